@@ -1,0 +1,33 @@
+"""FP64 CPU oracle for the even-odd Wilson/clover solver path.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously correct
+definition that the CUDA library is checked against.  Only the test suite,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference legs of
+``bench.py`` may import it.  The product library never calls it and shares no
+code with it.
+
+Contents (each function cites the passage of the paper it follows; where the
+paper is silent, the docstring states the reading taken):
+
+* ``lattice``  -- site indexing, parity and neighbour maps with boundary phases;
+* ``gamma``    -- the gamma matrices (chiral basis) and sigma_{mu nu};
+* ``dirac``    -- hopping term H, Wilson D = 1 - kappa H, the clover term T,
+                  full D = T - kappa H (Sec. 2 of the paper);
+* ``evenodd``  -- the blocks D_ee, D_oo, D_eo, D_oe and the Schur operator
+                  D^(eo) = 1 - D_ee^-1 D_eo D_oo^-1 D_oe (Eq. 1), source
+                  preparation and odd-site reconstruction;
+* ``solvers``  -- BiCGStab (van der Vorst) as named in Sec. 3, dense matrices
+                  by their matrix elements and dense LU solves.
+
+Arrays are complex128 in the canonical layouts of ``synth``: spinors
+``(V, 4, 3)``, links ``(4, V, 3, 3)``, half-lattice vectors ``(V/2, 4, 3)``
+ordered by lexicographic index among the sites of one parity.
+
+Parity status: every function here is pinned by a CPU test against a closed
+form, an invariant or a library routine (see tests/test_oracle_pins.py);
+none is marked "parity unpinned" except the overall sign/normalisation of the
+clover term, which is a convention the paper does not state (the abelian-flux
+closed form pins the reading taken, not the paper).
+"""
+
+from . import lattice, gamma, dirac, evenodd, solvers  # noqa: F401

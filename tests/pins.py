@@ -1,0 +1,250 @@
+"""Checks that pin the oracle to mathematics other than itself.
+
+Each function returns an error measure; tests/test_oracle_pins.py asserts it
+is at rounding level for the oracle as written, and tests/test_oracle_mutations.py
+asserts it is large once a plausible mistake is planted in the oracle.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+import synth
+from oracle import dirac, evenodd, gamma, solvers
+from oracle.lattice import Lattice
+
+
+def rel(a, b) -> float:
+    d = np.linalg.norm(np.asarray(a) - np.asarray(b))
+    n = np.linalg.norm(np.asarray(b))
+    return float(d / n) if n > 0 else float(d)
+
+
+# --- free field: plane waves are eigenvectors of D_W with a closed-form eigenvalue ---
+
+
+def plane_wave(lat: Lattice, n, u):
+    """psi(x) = exp(i p.x) u with p_k = 2 pi n_k / L_k and p_t = (2 n_t + 1) pi / L_t."""
+    L = lat.dims
+    p = [2 * np.pi * n[k] / L[k] for k in range(3)] + [(2 * n[3] + 1) * np.pi / L[3]]
+    phase = np.exp(1j * sum(p[mu] * lat.coords[mu] for mu in range(4)))
+    return phase[:, None, None] * u[None], p
+
+
+def free_field_symbol(p, kappa):
+    """The closed form D_W(p) = 1 - 2 kappa sum cos p_mu + 2 i kappa sum gamma_mu sin p_mu."""
+    M = (1 - 2 * kappa * sum(np.cos(q) for q in p)) * np.eye(4, dtype=np.complex128)
+    for mu in range(4):
+        M = M + 2j * kappa * np.sin(p[mu]) * PINNED_GAMMA[mu]
+    return M
+
+
+def _pinned_gamma():
+    """The chiral basis, typed here independently of oracle.gamma."""
+    s = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]])]
+    z = np.zeros((2, 2))
+    e = np.eye(2)
+    g = [np.block([[z, -1j * s[k]], [1j * s[k], z]]) for k in range(3)]
+    g.append(np.block([[z, e], [e, z]]))
+    return [x.astype(np.complex128) for x in g]
+
+
+PINNED_GAMMA = _pinned_gamma()
+
+
+def free_field_error(dims=(4, 6, 4, 8), kappa=0.12, modes=((0, 0, 0, 0), (1, 2, 3, 1), (3, 5, 1, 6)), seed=7):
+    lat = Lattice(dims)
+    U = synth.unit_gauge(dims)
+    gen = np.random.default_rng(seed)
+    err = 0.0
+    for n in modes:
+        u = gen.standard_normal((4, 3)) + 1j * gen.standard_normal((4, 3))
+        psi, p = plane_wave(lat, n, u)
+        got = dirac.wilson(U, psi, lat, kappa)
+        want = np.einsum("st,ntc->nsc", free_field_symbol(p, kappa), psi)
+        err = max(err, rel(got, want))
+    return err
+
+
+def free_field_inverse_error(dims=(4, 4, 4, 8), kappa=0.12, n=(1, 0, 2, 3), seed=3):
+    """BiCGStab on D_W applied to a plane wave reproduces the closed-form inverse."""
+    lat = Lattice(dims)
+    U = synth.unit_gauge(dims)
+    gen = np.random.default_rng(seed)
+    u = gen.standard_normal((4, 3)) + 1j * gen.standard_normal((4, 3))
+    b, p = plane_wave(lat, n, u)
+    x, info = solvers.bicgstab(lambda v: dirac.wilson(U, v, lat, kappa), b, tol=1e-13)
+    Minv = np.linalg.inv(free_field_symbol(p, kappa))
+    want = np.einsum("st,ntc->nsc", Minv, b)
+    return rel(x, want)
+
+
+# --- gamma_5 hermiticity -----------------------------------------------------------
+
+
+def gamma5_hermiticity_error(dims=(4, 4, 6, 4), kappa=0.13, csw=1.3, eps=0.4, seed=11):
+    """<phi, g5 D g5 psi> = <D phi, psi> for random fields."""
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    phi = synth.gaussian_spinor(dims, seed, field_id=5)
+    psi = synth.gaussian_spinor(dims, seed, field_id=6)
+    g5 = np.diag([1, 1, -1, -1]).astype(np.complex128)
+    g5v = lambda v: np.einsum("st,ntc->nsc", g5, v)  # noqa: E731
+    lhs = np.vdot(phi, g5v(dirac.dirac(U, g5v(psi), lat, kappa, csw)))
+    rhs = np.vdot(dirac.dirac(U, phi, lat, kappa, csw), psi)
+    return abs(lhs - rhs) / (np.linalg.norm(phi) * np.linalg.norm(psi))
+
+
+# --- gauge covariance --------------------------------------------------------------
+
+
+def random_su3(n, gen):
+    z = gen.standard_normal((n, 3, 3)) + 1j * gen.standard_normal((n, 3, 3))
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r, axis1=-2, axis2=-1)
+    q = q * (d / np.abs(d))[:, None, :]
+    det = np.linalg.det(q)
+    return q / (det ** (1 / 3))[:, None, None]
+
+
+def gauge_transform(U, lat: Lattice, Om):
+    """U_mu(x) -> Om(x) U_mu(x) Om(x + mu)^dagger."""
+    out = np.empty_like(U)
+    x = np.arange(lat.V)
+    for mu in range(4):
+        y, _ = lat.neighbor(x, mu, +1)
+        out[mu] = Om @ U[mu] @ np.conj(np.swapaxes(Om[y], -1, -2))
+    return out
+
+
+def covariance_error(dims=(4, 6, 4, 4), kappa=0.12, csw=1.1, eps=0.5, seed=21):
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    gen = np.random.default_rng(seed)
+    Om = random_su3(lat.V, gen)
+    Ug = gauge_transform(U, lat, Om)
+    psi = synth.gaussian_spinor(dims, seed, field_id=4)
+    rot = lambda v: np.einsum("nab,nsb->nsa", Om, v)  # noqa: E731
+    lhs = dirac.dirac(Ug, rot(psi), lat, kappa, csw)
+    rhs = rot(dirac.dirac(U, psi, lat, kappa, csw))
+    return rel(lhs, rhs)
+
+
+# --- abelian flux: F_{mu nu} known exactly ----------------------------------------
+
+
+def abelian_flux_links(lat: Lattice, mu, nu, n_flux, a, b):
+    """U_mu = exp(-i phi x_nu D), U_nu = exp(i phi L_nu x_mu D) on the last nu slice.
+
+    Every plaquette in the (mu, nu) plane then equals exp(i phi D) with
+    phi = 2 pi n / (L_mu L_nu) and D = diag(a, b, -a-b); all other planes are flat.
+    """
+    L = lat.dims
+    phi = 2 * np.pi * n_flux / (L[mu] * L[nu])
+    D = np.array([a, b, -a - b], dtype=float)
+    U = synth.unit_gauge(lat.dims)
+    xm, xn = lat.coords[mu], lat.coords[nu]
+    U[mu] = np.einsum("nk,kl->nkl", np.exp(-1j * phi * xn[:, None] * D[None]), np.eye(3))
+    last = xn == L[nu] - 1
+    ph = np.where(last[:, None], np.exp(1j * phi * L[nu] * xm[:, None] * D[None]), 1.0)
+    U[nu] = np.einsum("nk,kl->nkl", ph, np.eye(3))
+    return U, phi, D
+
+
+def abelian_flux_error(dims=(4, 6, 4, 8), kappa=0.11, csw=1.7):
+    """F and T from the oracle against sin(phi D) minus its trace, in every plane."""
+    lat = Lattice(dims)
+    err = 0.0
+    x = np.arange(lat.V)
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            U, phi, D = abelian_flux_links(lat, mu, nu, 1, 1, 2)
+            f = np.sin(phi * D)
+            f = f - f.sum() / 3
+            for r in range(4):
+                for s in range(r + 1, 4):
+                    F = dirac.field_strength(U, lat, x, r, s)
+                    want = np.diag(f) if (r, s) == (mu, nu) else np.zeros((3, 3))
+                    err = max(err, float(np.max(np.abs(F - want[None]))))
+            T = dirac.clover_term(U, lat, kappa, csw, x)
+            sig = 0.5j * (PINNED_GAMMA[mu] @ PINNED_GAMMA[nu] - PINNED_GAMMA[nu] @ PINNED_GAMMA[mu])
+            Twant = np.eye(12) - kappa * csw * np.kron(sig, np.diag(f))
+            err = max(err, float(np.max(np.abs(T - Twant[None]))))
+    return err
+
+
+# --- even-odd algebra (Eq. 1) -----------------------------------------------------
+
+
+def schur_dense_error(dims=(2, 2, 2, 2), kappa=0.12, csw=1.0, eps=0.6, seed=31):
+    """D^(eo) from the blocks equals T_ee^-1 (T_ee - D_eo T_oo^-1 D_oe) from the dense matrix."""
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    M = solvers.dense_dirac(U, lat, kappa, csw)
+    e = np.concatenate([np.arange(12 * s, 12 * s + 12) for s in lat.even])
+    o = np.concatenate([np.arange(12 * s, 12 * s + 12) for s in lat.odd])
+    Mee, Meo, Moe, Moo = M[np.ix_(e, e)], M[np.ix_(e, o)], M[np.ix_(o, e)], M[np.ix_(o, o)]
+    S = np.linalg.solve(Mee, Mee - Meo @ np.linalg.solve(Moo, Moe))
+    eo = evenodd.EvenOdd(U, lat, kappa, csw)
+    n = 12 * len(lat.even)
+    Sb = solvers.dense_matrix(lambda v: eo.schur(v.reshape(-1, 4, 3)).reshape(-1), n)
+    return rel(Sb, S)
+
+
+def dense_vs_stencil_error(dims=(2, 2, 2, 4), kappa=0.13, csw=0.9, eps=0.5, seed=41):
+    """The stencil D equals the matrix filled from its matrix elements."""
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    M = solvers.dense_dirac(U, lat, kappa, csw)
+    Mb = solvers.dense_matrix(lambda v: dirac.dirac(U, v.reshape(-1, 4, 3), lat, kappa, csw).reshape(-1), 12 * lat.V)
+    return rel(Mb, M)
+
+
+def lu_vs_bicgstab_error(dims=(2, 2, 2, 2), kappa=0.12, csw=1.0, eps=0.5, seed=51, evenodd_solve=False, maxiter=100000):
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    b = synth.gaussian_spinor(dims, seed)
+    M = solvers.dense_dirac(U, lat, kappa, csw)
+    x_lu = solvers.lu_solve(M, b.reshape(-1)).reshape(b.shape)
+    if evenodd_solve:
+        eo = evenodd.EvenOdd(U, lat, kappa, csw)
+        xe, info = solvers.bicgstab(eo.schur, eo.prepare(b), tol=1e-14, maxiter=maxiter)
+        x = eo.reconstruct(xe, b)
+    else:
+        x, info = solvers.bicgstab(lambda v: dirac.dirac(U, v, lat, kappa, csw), b, tol=1e-14, maxiter=maxiter)
+    return rel(x, x_lu)
+
+
+def evenodd_vs_full_error(dims=(4, 4, 4, 4), kappa=0.12, csw=1.0, eps=0.3, seed=61):
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    b = synth.gaussian_spinor(dims, seed)
+    T = dirac.clover_term(U, lat, kappa, csw)
+    x_full, _ = solvers.bicgstab(lambda v: dirac.dirac(U, v, lat, kappa, csw, T=T), b, tol=1e-13)
+    eo = evenodd.EvenOdd(U, lat, kappa, csw)
+    xe, _ = solvers.bicgstab(eo.schur, eo.prepare(b), tol=1e-13)
+    x_eo = eo.reconstruct(xe, b)
+    return rel(x_eo, x_full)
+
+
+def blocks_vs_full_error(dims=(4, 2, 6, 4), kappa=0.12, csw=1.2, eps=0.4, seed=71):
+    """The 2x2 block form of Eq. 1 reassembles the full operator."""
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    psi = synth.gaussian_spinor(dims, seed)
+    eo = evenodd.EvenOdd(U, lat, kappa, csw)
+    return rel(eo.full(psi), dirac.dirac(U, psi, lat, kappa, csw))
+
+
+def gamma_algebra_error():
+    err = 0.0
+    G = gamma.GAMMA
+    for mu in range(4):
+        err = max(err, np.abs(G[mu] - G[mu].conj().T).max())
+        for nu in range(4):
+            anti = G[mu] @ G[nu] + G[nu] @ G[mu]
+            err = max(err, np.abs(anti - 2 * (mu == nu) * np.eye(4)).max())
+    err = max(err, np.abs(gamma.gamma5() - np.diag([1, 1, -1, -1])).max())
+    for mu in range(4):
+        err = max(err, np.abs(G[mu] - PINNED_GAMMA[mu]).max())
+    return float(err)

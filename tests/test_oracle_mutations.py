@@ -1,0 +1,70 @@
+"""Planted mistakes in the oracle must fail a pin.
+
+Each case edits one line of the oracle's own source (a sign, a dropped term,
+a transposed operand, a wrong index), loads the edited module, swaps its
+functions in for the originals and checks that the named pin now reports a
+large error.  This shows the pins in tests/pins.py can tell a wrong oracle
+from a right one; nothing here touches a GPU.
+"""
+
+import importlib
+import inspect
+
+import pytest
+
+import oracle
+from tests import pins
+
+MUTANTS = [
+    # (module, original text, planted text, pin, threshold above every tolerance the pins use)
+    ("dirac", "_spin(_g.I4 - g,", "_spin(_g.I4 + g,", pins.free_field_error, 1e-10),
+    ("dirac", "_colour(_dag(U[mu][j]), phase * psi[j])", "_colour(U[mu][j], phase * psi[j])", pins.covariance_error, 1e-10),
+    ("dirac", "phase = np.where(wraps, bc[mu], 1.0)[:, None, None]\n        out += _spin(_g.I4 - g",
+     "phase = 1.0\n        out += _spin(_g.I4 - g", pins.free_field_error, 1e-10),
+    ("dirac", "_colour(U[mu][sites], phase * psi[j])", "_colour(np.swapaxes(U[mu][sites], -1, -2), phase * psi[j])",
+     pins.covariance_error, 1e-10),
+    ("dirac", "j, wraps = lat.neighbor(sites, mu, -1)", "j, wraps = lat.neighbor(sites, mu, +1)", pins.free_field_error, 1e-10),
+    ("dirac", "F = (Q - _dag(Q)) / 8j", "F = (Q - _dag(Q)) / 4j", pins.abelian_flux_error, 1e-10),
+    ("dirac", "return F - (tr / 3.0)[:, None, None] * np.eye(3)", "return F", pins.abelian_flux_error, 1e-10),
+    ("dirac", "q = q + Un[x] @ _dag(Um[xmm_pn]) @ _dag(Un[xmm]) @ Um[xmm]",
+     "q = q + _dag(Um[xmm]) @ Un[xmm] @ Um[xmm_pn] @ _dag(Un[x])", pins.abelian_flux_error, 1e-10),
+    ("dirac", "T -= kappa * csw", "T += kappa * csw", pins.abelian_flux_error, 1e-10),
+    ("dirac", '"st,nab->nsatb"', '"st,nab->nastb"', pins.abelian_flux_error, 1e-10),
+    ("gamma", "np.block([[Z2, -1j * PAULI[k]], [1j * PAULI[k], Z2]])",
+     "np.block([[Z2, 1j * PAULI[k]], [-1j * PAULI[k], Z2]])", pins.free_field_error, 1e-10),
+    ("evenodd", "return x_e - self.D_pp_inv(0, self.D_hop(0, t))", "return x_e - self.D_pp(0, self.D_hop(0, t))",
+     pins.schur_dense_error, 1e-10),
+    ("evenodd", "b_e - self.D_hop(0, self.D_pp_inv(1, b_o))", "b_e + self.D_hop(0, self.D_pp_inv(1, b_o))",
+     lambda: pins.lu_vs_bicgstab_error(evenodd_solve=True, maxiter=400), 1e-10),
+    ("evenodd", "x[lat.odd] = self.D_pp_inv(1, b[lat.odd] - self.D_hop(1, x_e))",
+     "x[lat.odd] = self.D_pp_inv(1, b[lat.odd] + self.D_hop(1, x_e))",
+     lambda: pins.lu_vs_bicgstab_error(evenodd_solve=True, maxiter=400), 1e-10),
+    ("solvers", "x = x + alpha * p + omega * s", "x = x + alpha * p", lambda: pins.lu_vs_bicgstab_error(maxiter=400), 1e-10),
+    ("solvers", "r = s - omega * t", "r = s + omega * t", lambda: pins.lu_vs_bicgstab_error(maxiter=400), 1e-10),
+    ("solvers", "np.kron(_g.I4 + g, U[mu][y].conj().T)", "np.kron(_g.I4 + g, U[mu][y].conj())", pins.dense_vs_stencil_error, 1e-10),
+]
+
+
+def _load_mutant(modname, old, new):
+    mod = importlib.import_module(f"oracle.{modname}")
+    src = inspect.getsource(mod)
+    assert src.count(old) >= 1, f"mutation anchor not found in oracle/{modname}.py: {old!r}"
+    ns = {"__name__": f"oracle.{modname}_mutant", "__package__": "oracle"}
+    exec(compile(src.replace(old, new, 1), f"oracle/{modname}.py(mutant)", "exec"), ns)
+    return mod, ns
+
+
+@pytest.mark.parametrize("case", range(len(MUTANTS)), ids=[f"{m[0]}:{m[2][:40]}" for m in MUTANTS])
+def test_planted_mistake_is_caught(case, monkeypatch):
+    modname, old, new, pin, threshold = MUTANTS[case]
+    mod, ns = _load_mutant(modname, old, new)
+    for name, obj in ns.items():
+        if not name.startswith("__") and hasattr(mod, name) and (inspect.isfunction(obj) or inspect.isclass(obj) or name == "GAMMA"):
+            monkeypatch.setattr(mod, name, obj)
+    assert pin() > threshold
+
+
+def test_unmutated_oracle_passes_every_pin_used_above():
+    for _, _, _, pin, _ in MUTANTS:
+        assert pin() < 1e-10
+    assert oracle is not None
