@@ -1,0 +1,246 @@
+/*
+ * libbridge -- GPU (sm_103a) even-odd Wilson/clover Dirac operator and
+ * mixed-precision BiCGStab solver, the fermion-propagator path of
+ * "Bridge++ 2.0: Benchmark results on supercomputer Fugaku" (Sec. 2, Eq. 1,
+ * Sec. 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: extents dims = {Lx, Ly, Lz, Lt}, all even and >= 2; site index
+ *   i = x + Lx*(y + Ly*(z + Lz*t)); parity (x+y+z+t) mod 2, even = 0.
+ * Canonical spinor layout (FP64): [rhs][t][z][y][x][spin 4][colour 3][re,im],
+ *   i.e. 24 doubles per site.  A half-lattice vector holds the V/2 sites of
+ *   one parity in increasing lexicographic order (site i sits at i/2).
+ * Canonical link layout (FP64): [mu][t][z][y][x][row 3][col 3][re,im],
+ *   mu = x, y, z, t; U_mu(x) connects x to x + mu.
+ * Gamma matrices: chiral basis gamma_k = [[0, -i s_k], [i s_k, 0]] (k = x, y,
+ *   z), gamma_t = [[0, 1], [1, 0]], gamma_5 = diag(1, 1, -1, -1).  (The paper
+ *   uses the QWS convention and converts at its call boundary; the basis is
+ *   not printed there.)
+ * Operator: D = T - kappa H with
+ *   (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *              + (1 + gamma_mu) U_mu(x-mu)^dagger psi(x-mu),
+ *   a boundary phase bc[mu] (+1 periodic, -1 antiperiodic) on every hop that
+ *   wraps, and T = 1 (Wilson) or T = 1 - kappa c_sw sum_{mu<nu} sigma_{mu nu}
+ *   F_{mu nu} (clover; F from the four-leaf clover, made traceless).
+ * Even-odd form (Eq. 1): D_ee = T_e, D_oo = T_o, D_eo = -kappa H_eo,
+ *   D_oe = -kappa H_oe, D^(eo) = 1 - D_ee^-1 D_eo D_oo^-1 D_oe.
+ *
+ * Memory: pointer arguments named *_dev are device pointers (cudaMalloc,
+ * cudaMallocAsync or a framework allocator on the current device); all
+ * others are host pointers.  The library copies every input it keeps; the
+ * caller owns every buffer it passes.  Device buffers must be 16-byte
+ * aligned.
+ *
+ * Errors: every function returns BRIDGE_OK (0) or a negative status and never
+ * aborts; bridge_last_error() gives a one-line description of the most recent
+ * failure on the calling thread.  A lattice handle may be used from one host
+ * thread at a time (calls are serialised by an internal lock); the request
+ * API (bridge_submit .. bridge_request_release) is thread-safe.
+ *
+ * There is no CPU fallback: without a CUDA device of compute capability 10.3
+ * bridge_lattice_create returns BRIDGE_ECUDA.
+ */
+#ifndef BRIDGE_H
+#define BRIDGE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bridge_lattice_s* bridge_lattice;  /* opaque, library-owned */
+typedef struct bridge_field_s* bridge_field;      /* opaque, library-owned */
+typedef struct bridge_request_s* bridge_request_h; /* opaque, library-owned */
+
+enum bridge_status {
+  BRIDGE_OK = 0,
+  BRIDGE_PENDING = 1,
+  BRIDGE_EINVAL = -1,     /* bad argument (null pointer, odd extent, unknown enum) */
+  BRIDGE_ENOMEM = -2,     /* device allocation failed or request exceeds the memory budget */
+  BRIDGE_ENOCONV = -3,    /* solver hit its iteration limit above tolerance */
+  BRIDGE_EBREAKDOWN = -4, /* BiCGStab breakdown that restarts could not cure */
+  BRIDGE_ETIMEDOUT = -5,  /* bridge_wait ran out of time (request still running) */
+  BRIDGE_ECUDA = -6,      /* CUDA error (text in bridge_last_error) */
+  BRIDGE_ESTATE = -7      /* call out of order (e.g. operator before gauge upload) */
+};
+
+/* Storage precision of a field or of an operator application.  F64 computes
+ * in FP64; F32 stores and computes in FP32; F16/BF16 store spinors as 16-bit
+ * values times a per-site FP32 scale (max |component|), links and clover
+ * blocks as plain 16-bit values, and compute in FP32. */
+enum bridge_prec { BRIDGE_F64 = 0, BRIDGE_F32 = 1, BRIDGE_F16 = 2, BRIDGE_BF16 = 3 };
+
+enum bridge_kind { BRIDGE_WILSON = 0, BRIDGE_CLOVER = 1 };
+
+/* Site subset of a field: one parity (half lattice) or the full lattice. */
+enum bridge_subset { BRIDGE_EVEN = 0, BRIDGE_ODD = 1, BRIDGE_FULL = 2 };
+
+/* Operator selector for bridge_apply. */
+enum bridge_apply_op {
+  BRIDGE_APPLY_D = 0,    /* full D, FULL -> FULL */
+  BRIDGE_APPLY_DEO = 1,  /* D_eo = -kappa H_eo, ODD -> EVEN */
+  BRIDGE_APPLY_DOE = 2,  /* D_oe = -kappa H_oe, EVEN -> ODD */
+  BRIDGE_APPLY_DHAT = 3  /* D^(eo) of Eq. 1, EVEN -> EVEN */
+};
+
+typedef struct {
+  int kind;     /* bridge_kind */
+  double kappa; /* hopping parameter */
+  double csw;   /* clover coefficient (ignored for WILSON) */
+  int bc[4];    /* boundary phase per direction, +1 or -1; {1,1,1,-1} usual */
+} bridge_op;
+
+typedef struct {
+  double tol;        /* stop when ||b - D x|| <= tol ||b|| (FP64 true residual) */
+  int max_iter;      /* limit on inner BiCGStab iterations, summed over restarts */
+  int inner_prec;    /* bridge_prec of the inner solver (mixed = 1) */
+  double inner_tol;  /* inner relative tolerance; <= 0 picks 1e-5 (F32), 2e-3 (F16/BF16) */
+  int mixed;         /* 1: FP64 defect correction around an inner_prec solver; 0: plain FP64 */
+  int check_every;   /* iterations between host convergence polls (<= 0: 16) */
+  int use_graph;     /* 1: replay iteration batches as CUDA graphs */
+  int max_outer;     /* limit on defect-correction passes (<= 0: 50) */
+} bridge_solver;
+
+typedef struct {
+  int status;               /* BRIDGE_OK, BRIDGE_ENOCONV or BRIDGE_EBREAKDOWN */
+  int outer_iters;          /* defect-correction passes (true-residual evaluations - 1) */
+  int inner_iters;          /* BiCGStab iterations summed over passes */
+  int restarts;             /* inner solves that ended in breakdown */
+  double true_rel_residual; /* ||b - D x|| / ||b|| in FP64 on the GPU */
+  double seconds;           /* wall time of the solve */
+} bridge_info;
+
+typedef struct {
+  const char* name;  /* kernel class */
+  long launches;
+  double bytes;      /* algorithmic bytes (each input read once, output written once) */
+  double flops;      /* stated flop count (hop 1320 + 24 per site, clover 504, ...) */
+  double ms;         /* event-timed milliseconds (only while profiling) */
+} bridge_kstat;
+
+/* ---- lattice ------------------------------------------------------------ */
+
+/* Create a lattice handle on the current CUDA device.  dims: 4 even extents
+ * >= 2 with V/2 < 2^31.  Allocates the handle and a CUDA stream; no field
+ * memory yet.  Errors: EINVAL (dims), ECUDA (no sm_103 device). */
+int bridge_lattice_create(const int dims[4], bridge_lattice* out);
+int bridge_lattice_destroy(bridge_lattice lat);
+/* The cudaStream_t (as void*) on which all work of this lattice is ordered. */
+void* bridge_lattice_stream(bridge_lattice lat);
+/* Block the host until all work queued on the lattice stream is done. */
+int bridge_sync(bridge_lattice lat);
+
+/* Upload a gauge field (Sec. 2: the operators act on a given SU(3) field).
+ * U: canonical FP64 links, 4*V*18 doubles, host (or device for _dev).  The
+ * links are copied and stored as FP64 18-real planes; FP32/F16/BF16 12-real
+ * copies and, for CLOVER, the clover term T and T^-1 (built in FP64 on the
+ * GPU for kappa*c_sw of op) are made on first use.  op may be NULL. */
+int bridge_gauge_upload(bridge_lattice lat, const double* U, const bridge_op* op);
+int bridge_gauge_upload_dev(bridge_lattice lat, const double* U_dev, const bridge_op* op);
+
+/* ---- operators on canonical FP64 buffers ----------------------------------- */
+
+/* out = D in on the full lattice (Sec. 2: Wilson/clover multiplication),
+ * computed in precision prec; in/out hold nrhs canonical full spinors
+ * (nrhs*V*24 doubles).  nrhs = 0 is a no-op.  Synchronous. */
+int bridge_mult_D(bridge_lattice lat, const bridge_op* op, int prec, const double* in, double* out, int nrhs);
+/* Half-lattice hopping block (Eq. 1): out_parity 0 gives D_eo in (in odd,
+ * out even), 1 gives D_oe in; D_eo = -kappa H_eo.  in/out: nrhs canonical
+ * half-lattice vectors (nrhs*V/2*24 doubles).  Synchronous. */
+int bridge_mult_Deo(bridge_lattice lat, const bridge_op* op, int prec, int out_parity, const double* in, double* out,
+                    int nrhs);
+/* Schur operator D^(eo) = 1 - D_ee^-1 D_eo D_oo^-1 D_oe of Eq. 1 on even
+ * half-lattice vectors.  Synchronous. */
+int bridge_mult_Dhat(bridge_lattice lat, const bridge_op* op, int prec, const double* in, double* out, int nrhs);
+/* Same three, with device buffers; work is queued on the lattice stream and
+ * the call returns without waiting (use bridge_sync or the stream). */
+int bridge_mult_D_dev(bridge_lattice lat, const bridge_op* op, int prec, const double* in_dev, double* out_dev, int nrhs);
+int bridge_mult_Deo_dev(bridge_lattice lat, const bridge_op* op, int prec, int out_parity, const double* in_dev,
+                        double* out_dev, int nrhs);
+int bridge_mult_Dhat_dev(bridge_lattice lat, const bridge_op* op, int prec, const double* in_dev, double* out_dev,
+                         int nrhs);
+
+/* ---- solver ------------------------------------------------------------------ */
+
+/* Solve D x = b for nrhs right-hand sides (Sec. 3: BiCGStab for the clover
+ * operator; mixed-precision BiCGStab for propagators).  Even-odd
+ * preconditioned BiCGStab on D^(eo) (Eq. 1) inside an FP64 defect-correction
+ * loop on the true residual.  b, x: canonical full spinors, nrhs*V*24
+ * doubles each; x holds the initial guess on entry (zeros for none) and the
+ * solution on return.  info: array of nrhs records (may be NULL).
+ * Returns OK when every right-hand side reached tol, else ENOCONV or
+ * EBREAKDOWN (x then holds the best iterate).  Synchronous. */
+int bridge_solve(bridge_lattice lat, const bridge_op* op, const bridge_solver* s, const double* b, double* x, int nrhs,
+                 bridge_info* info);
+int bridge_solve_dev(bridge_lattice lat, const bridge_op* op, const bridge_solver* s, const double* b_dev,
+                     double* x_dev, int nrhs, bridge_info* info);
+/* Defaults: tol 1e-10, max_iter 20000, F32 inner, mixed, poll every 16, graphs on. */
+void bridge_solver_defaults(bridge_solver* s);
+
+/* ---- fields in the GPU layout (resident data) ------------------------------- */
+
+/* A library-owned device field of nrhs spinors in the GPU site layout of
+ * precision prec over subset (bridge_subset). */
+int bridge_field_create(bridge_lattice lat, int prec, int subset, int nrhs, bridge_field* out);
+int bridge_field_destroy(bridge_field f);
+/* Fill from / copy to canonical FP64 (full or half-lattice per the field's
+ * subset); src/dst on the device if on_device != 0, else on the host.
+ * Device-side copies are queued on the lattice stream; host-side ones block. */
+int bridge_field_import(bridge_field f, const double* src, int on_device);
+int bridge_field_export(bridge_field f, double* dst, int on_device);
+/* out = op(in) in the fields' precision (both fields must share it); queued
+ * on the lattice stream.  See bridge_apply_op for the subsets required. */
+int bridge_apply(bridge_lattice lat, const bridge_op* op, int which, bridge_field out, bridge_field in);
+
+/* ---- serving: continuous batching of solve requests ------------------------- */
+
+/* Limits of the request engine: total device bytes that admitted requests
+ * may hold (0 = 80% of free memory at first use) and the maximum number of
+ * requests on the GPU at once (<= 0: 16).  Call before the first submit. */
+int bridge_engine_config(size_t memory_budget_bytes, int max_active);
+/* Queue a solve of D x = b (as bridge_solve, x0 = 0).  b is copied; the
+ * request is admitted when memory and a slot are free and then advances
+ * concurrently with the other admitted requests, each on its own stream.
+ * The lattice must outlive the request.  Errors: EINVAL, ENOMEM (request
+ * larger than the whole budget). */
+int bridge_submit(bridge_lattice lat, const bridge_op* op, const bridge_solver* s, const double* b, int nrhs,
+                  bridge_request_h* out);
+/* PENDING while running; else the request's final status, with x_out
+ * (nrhs*V*24 doubles, may be NULL) and info[nrhs] (may be NULL) filled. */
+int bridge_poll(bridge_request_h h, double* x_out, bridge_info* info);
+/* As bridge_poll, blocking up to timeout_ms (< 0: forever); ETIMEDOUT if
+ * the request is still running. */
+int bridge_wait(bridge_request_h h, int timeout_ms, double* x_out, bridge_info* info);
+/* Free a finished request; a running one is cancelled first. */
+int bridge_request_release(bridge_request_h h);
+/* Timestamps (seconds, monotonic clock) of submit, admission and completion. */
+int bridge_request_times(bridge_request_h h, double* t_submit, double* t_admit, double* t_done);
+
+/* ---- diagnostics --------------------------------------------------------- */
+
+const char* bridge_strerror(int status);
+const char* bridge_last_error(void);
+/* Kernel statistics of this lattice since the last reset: out[k] for the
+ * first min(n, count) classes; returns the number of classes. */
+int bridge_stats(bridge_lattice lat, bridge_kstat* out, int n);
+int bridge_stats_reset(bridge_lattice lat);
+/* While enabled, every kernel launch of this lattice is bracketed by CUDA
+ * events on its stream and graphs are not used; bridge_stats then reports
+ * event-timed milliseconds per class. */
+int bridge_profile(bridge_lattice lat, int enable);
+/* Number of kernels this library launched in this process (graph nodes
+ * count once per replay). */
+long bridge_launch_count(void);
+/* Neighbour map of the GPU layout, computed on the host with the same code
+ * the kernels use: out[2*mu + 0/1] = half-lattice index of x + mu / x - mu
+ * for half-lattice site ih of the given parity; wraps[mu*2 + 0/1] = 1 when
+ * that hop crosses the boundary.  For tests of the index arithmetic. */
+int bridge_debug_neighbours(const int dims[4], int parity, long ih, long out[8], int wraps[8]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BRIDGE_H */

@@ -1,0 +1,342 @@
+"""Python binding of libbridge: the C-ABI entry points under the same names.
+
+Argument marshalling only -- every step of the operator and the solver runs
+in the CUDA kernels of libbridge.so.  Host arrays are numpy complex128 in the
+canonical layouts of include/bridge.h (spinors ``(V, 4, 3)`` or
+``(nrhs, V, 4, 3)``, links ``(4, V, 3, 3)``); device arrays are torch CUDA
+complex128 tensors of the same shapes, which route to the ``*_dev`` entry
+points.  PyTorch is used for device memory and streams only.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, byref, c_double, c_int, c_long, c_void_p
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _abi
+from ._abi import BRIDGE_CLOVER, BRIDGE_WILSON, bridge_info, bridge_kstat, bridge_op, bridge_solver, check
+
+PRECISIONS = {"f64": _abi.BRIDGE_F64, "f32": _abi.BRIDGE_F32, "f16": _abi.BRIDGE_F16, "bf16": _abi.BRIDGE_BF16}
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def make_op(kind="wilson", kappa=0.12, csw=0.0, bc=(1, 1, 1, -1)) -> bridge_op:
+    k = {"wilson": BRIDGE_WILSON, "clover": BRIDGE_CLOVER}.get(kind, kind)
+    return bridge_op(int(k), float(kappa), float(csw), (c_int * 4)(*[int(b) for b in bc]))
+
+
+def make_solver(**kw) -> bridge_solver:
+    s = bridge_solver()
+    _abi.load().bridge_solver_defaults(byref(s))
+    for k, v in kw.items():
+        if k == "inner_prec":
+            v = _prec(v)
+        setattr(s, k, v)
+    return s
+
+
+def _is_torch_cuda(a) -> bool:
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(a, torch.Tensor) and a.is_cuda
+
+
+def _host(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+def _torch_sync():
+    import torch
+
+    torch.cuda.current_stream().synchronize()
+
+
+# --- lattice ------------------------------------------------------------------
+
+
+def bridge_lattice_create(dims) -> int:
+    lib = _abi.load()
+    h = c_void_p()
+    check(lib.bridge_lattice_create((c_int * 4)(*[int(d) for d in dims]), byref(h)), "bridge_lattice_create")
+    return h.value
+
+
+def bridge_lattice_destroy(lat) -> None:
+    check(_abi.load().bridge_lattice_destroy(lat), "bridge_lattice_destroy")
+
+
+def bridge_lattice_stream(lat) -> int:
+    return _abi.load().bridge_lattice_stream(lat) or 0
+
+
+def bridge_sync(lat) -> None:
+    check(_abi.load().bridge_sync(lat), "bridge_sync")
+
+
+def bridge_gauge_upload(lat, U, op: bridge_op | None = None) -> None:
+    lib = _abi.load()
+    opp = byref(op) if op is not None else None
+    if _is_torch_cuda(U):
+        _torch_sync()
+        check(lib.bridge_gauge_upload_dev(lat, c_void_p(U.contiguous().data_ptr()), opp), "bridge_gauge_upload_dev")
+    else:
+        U = _host(U)
+        check(lib.bridge_gauge_upload(lat, _dptr(U), opp), "bridge_gauge_upload")
+
+
+# --- operators ------------------------------------------------------------------
+
+
+def _mult(name, lat, op, prec, psi, *extra):
+    lib = _abi.load()
+    nrhs = 1 if psi.ndim == 3 else psi.shape[0]
+    if _is_torch_cuda(psi):
+        import torch
+
+        src = psi.contiguous()
+        out = torch.empty_like(src)
+        _torch_sync()
+        fn = getattr(lib, name + "_dev")
+        check(fn(lat, byref(op), _prec(prec), *extra, c_void_p(src.data_ptr()), c_void_p(out.data_ptr()), nrhs), name)
+        bridge_sync(lat)
+        return out
+    src = _host(psi)
+    out = np.empty_like(src)
+    fn = getattr(lib, name)
+    check(fn(lat, byref(op), _prec(prec), *extra, _dptr(src), _dptr(out), nrhs), name)
+    return out
+
+
+def bridge_mult_D(lat, op, prec, psi):
+    """D psi on the full lattice."""
+    return _mult("bridge_mult_D", lat, op, prec, psi)
+
+
+def bridge_mult_Deo(lat, op, prec, out_parity, psi_half):
+    """D_eo psi_o (out_parity 0) or D_oe psi_e (out_parity 1) on half-lattice vectors."""
+    return _mult("bridge_mult_Deo", lat, op, prec, psi_half, int(out_parity))
+
+
+def bridge_mult_Dhat(lat, op, prec, psi_even):
+    """The Schur operator of Eq. 1 on even half-lattice vectors."""
+    return _mult("bridge_mult_Dhat", lat, op, prec, psi_even)
+
+
+# --- solver -----------------------------------------------------------------------
+
+
+def _infos(arr, n):
+    return [
+        dict(
+            status=arr[k].status,
+            outer_iters=arr[k].outer_iters,
+            inner_iters=arr[k].inner_iters,
+            restarts=arr[k].restarts,
+            true_rel_residual=arr[k].true_rel_residual,
+            seconds=arr[k].seconds,
+        )
+        for k in range(n)
+    ]
+
+
+def bridge_solve(lat, op, solver, b, x0=None, raise_on_fail=True):
+    """Solve D x = b; returns (x, per-rhs info dicts)."""
+    lib = _abi.load()
+    nrhs = 1 if b.ndim == 3 else b.shape[0]
+    info = (bridge_info * nrhs)()
+    if _is_torch_cuda(b):
+        import torch
+
+        bb = b.contiguous()
+        x = torch.zeros_like(bb) if x0 is None else x0.contiguous().clone()
+        _torch_sync()
+        st = lib.bridge_solve_dev(lat, byref(op), byref(solver), c_void_p(bb.data_ptr()), c_void_p(x.data_ptr()), nrhs, info)
+    else:
+        bb = _host(b)
+        x = np.zeros_like(bb) if x0 is None else _host(x0).copy()
+        st = lib.bridge_solve(lat, byref(op), byref(solver), _dptr(bb), _dptr(x), nrhs, info)
+    if raise_on_fail:
+        check(st, "bridge_solve")
+    return x, _infos(info, nrhs)
+
+
+# --- fields -------------------------------------------------------------------------
+
+
+def bridge_field_create(lat, prec, subset, nrhs=1) -> int:
+    h = c_void_p()
+    check(_abi.load().bridge_field_create(lat, _prec(prec), int(subset), int(nrhs), byref(h)), "bridge_field_create")
+    return h.value
+
+
+def bridge_field_destroy(f) -> None:
+    check(_abi.load().bridge_field_destroy(f), "bridge_field_destroy")
+
+
+def bridge_field_import(f, src) -> None:
+    if _is_torch_cuda(src):
+        _torch_sync()
+        check(_abi.load().bridge_field_import(f, c_void_p(src.contiguous().data_ptr()), 1), "bridge_field_import")
+    else:
+        a = _host(src)
+        check(_abi.load().bridge_field_import(f, c_void_p(a.ctypes.data), 0), "bridge_field_import")
+
+
+def bridge_field_export(f, dst) -> None:
+    if _is_torch_cuda(dst):
+        check(_abi.load().bridge_field_export(f, c_void_p(dst.data_ptr()), 1), "bridge_field_export")
+    else:
+        assert dst.flags.c_contiguous and dst.dtype == np.complex128
+        check(_abi.load().bridge_field_export(f, c_void_p(dst.ctypes.data), 0), "bridge_field_export")
+
+
+def bridge_apply(lat, op, which, out, inp) -> None:
+    check(_abi.load().bridge_apply(lat, byref(op), int(which), out, inp), "bridge_apply")
+
+
+# --- serving --------------------------------------------------------------------------
+
+
+def bridge_engine_config(budget_bytes=0, max_active=0) -> None:
+    check(_abi.load().bridge_engine_config(int(budget_bytes), int(max_active)), "bridge_engine_config")
+
+
+@dataclass
+class Request:
+    handle: int
+    shape: tuple
+    nrhs: int
+    _b: np.ndarray = field(repr=False, default=None)
+
+
+def bridge_submit(lat, op, solver, b) -> Request:
+    bb = _host(b)
+    nrhs = 1 if bb.ndim == 3 else bb.shape[0]
+    h = c_void_p()
+    check(_abi.load().bridge_submit(lat, byref(op), byref(solver), _dptr(bb), nrhs, byref(h)), "bridge_submit")
+    return Request(h.value, bb.shape, nrhs, bb)
+
+
+def bridge_poll(req: Request):
+    """None while pending, else (status, x, infos)."""
+    x = np.empty(req.shape, dtype=np.complex128)
+    info = (bridge_info * req.nrhs)()
+    st = _abi.load().bridge_poll(req.handle, _dptr(x), info)
+    if st == _abi.BRIDGE_PENDING:
+        return None
+    return st, x, _infos(info, req.nrhs)
+
+
+def bridge_wait(req: Request, timeout_ms=-1):
+    x = np.empty(req.shape, dtype=np.complex128)
+    info = (bridge_info * req.nrhs)()
+    st = _abi.load().bridge_wait(req.handle, int(timeout_ms), _dptr(x), info)
+    if st == _abi.BRIDGE_ETIMEDOUT:
+        return None
+    return st, x, _infos(info, req.nrhs)
+
+
+def bridge_request_times(req: Request):
+    a, b, c = c_double(), c_double(), c_double()
+    check(_abi.load().bridge_request_times(req.handle, byref(a), byref(b), byref(c)), "bridge_request_times")
+    return a.value, b.value, c.value
+
+
+def bridge_request_release(req: Request) -> None:
+    check(_abi.load().bridge_request_release(req.handle), "bridge_request_release")
+
+
+# --- diagnostics ------------------------------------------------------------------------
+
+
+def bridge_stats(lat):
+    arr = (bridge_kstat * 32)()
+    n = _abi.load().bridge_stats(lat, arr, 32)
+    check(n, "bridge_stats")
+    return {
+        arr[k].name.decode(): dict(launches=arr[k].launches, bytes=arr[k].bytes, flops=arr[k].flops, ms=arr[k].ms)
+        for k in range(n)
+    }
+
+
+def bridge_stats_reset(lat) -> None:
+    check(_abi.load().bridge_stats_reset(lat), "bridge_stats_reset")
+
+
+def bridge_profile(lat, enable=True) -> None:
+    check(_abi.load().bridge_profile(lat, 1 if enable else 0), "bridge_profile")
+
+
+def bridge_launch_count() -> int:
+    return int(_abi.load().bridge_launch_count())
+
+
+def bridge_debug_neighbours(dims, parity, ih):
+    out = (c_long * 8)()
+    wr = (c_int * 8)()
+    check(
+        _abi.load().bridge_debug_neighbours((c_int * 4)(*[int(d) for d in dims]), int(parity), int(ih), out, wr),
+        "bridge_debug_neighbours",
+    )
+    return list(out), list(wr)
+
+
+def bridge_strerror(status: int) -> str:
+    return _abi.load().bridge_strerror(int(status)).decode()
+
+
+# --- convenience ---------------------------------------------------------------------------
+
+
+class Lattice:
+    """Owning wrapper of a lattice handle."""
+
+    def __init__(self, dims):
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        self.handle = bridge_lattice_create(self.dims)
+
+    def close(self):
+        if self.handle:
+            bridge_lattice_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload(self, U, op=None):
+        bridge_gauge_upload(self.handle, U, op)
+
+    def D(self, op, psi, prec="f64"):
+        return bridge_mult_D(self.handle, op, prec, psi)
+
+    def Deo(self, op, psi, out_parity=0, prec="f64"):
+        return bridge_mult_Deo(self.handle, op, prec, out_parity, psi)
+
+    def Dhat(self, op, psi, prec="f64"):
+        return bridge_mult_Dhat(self.handle, op, prec, psi)
+
+    def solve(self, op, b, solver=None, x0=None, raise_on_fail=True):
+        return bridge_solve(self.handle, op, solver or make_solver(), b, x0, raise_on_fail)
+
+    @property
+    def stream(self):
+        import torch
+
+        return torch.cuda.ExternalStream(bridge_lattice_stream(self.handle))

@@ -1,0 +1,431 @@
+// Device-side building blocks shared by the kernels of libbridge:
+// complex arithmetic, the GPU site layout, per-precision field access and
+// the even-odd lattice geometry.
+//
+// GPU layout (the A64FX layout of the paper, Sec. 2 / Fig. 1, is prior art;
+// this is the sm_103a counterpart):
+//   * a half-lattice field holds the Vh = V/2 sites of one parity, ordered by
+//     ih = (lexicographic index) >> 1, which is the order of the canonical
+//     half-lattice vectors at the C-ABI;
+//   * structure of arrays: each 16-byte plane p stores the same 16 bytes of
+//     every site, addressed base + (p * Vh + ih) * 16, so a warp reads 512
+//     contiguous bytes per plane (real and imaginary parts stay adjacent);
+//   * spinor planes: F64 12 x double2, F32 6 x float4, F16/BF16 3 x 8 halves
+//     plus one float per site (the per-site scale, max |component|);
+//   * links U_mu(x) stored at the site x they start from, per parity and
+//     direction: F64 all 18 reals (9 x double2); F32/F16/BF16 only rows 0, 1
+//     (12 reals), row 2 = conj(row0 x row1) rebuilt in registers;
+//   * clover blocks: the site term is block diagonal in the chiral basis,
+//     two Hermitian 6x6 blocks per site stored packed as 6 real diagonal
+//     entries and 15 complex lower-triangle entries (72 reals per site).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bridge {
+
+enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
+
+#define BR_HD __host__ __device__ __forceinline__
+#define BR_D __device__ __forceinline__
+
+// ---------------------------------------------------------------- complex
+template <class R>
+struct cx {
+  R r, i;
+};
+template <class R>
+BR_HD cx<R> operator+(cx<R> a, cx<R> b) { return {a.r + b.r, a.i + b.i}; }
+template <class R>
+BR_HD cx<R> operator-(cx<R> a, cx<R> b) { return {a.r - b.r, a.i - b.i}; }
+template <class R>
+BR_HD cx<R> operator*(cx<R> a, cx<R> b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+template <class R>
+BR_HD cx<R> operator*(R s, cx<R> a) { return {s * a.r, s * a.i}; }
+template <class R>
+BR_HD cx<R> conj(cx<R> a) { return {a.r, -a.i}; }
+template <class R>
+BR_HD cx<R> times_i(cx<R> a) { return {-a.i, a.r}; }  // i * a
+template <class R>
+BR_HD cx<R> times_mi(cx<R> a) { return {a.i, -a.r}; }  // -i * a
+template <class R>
+BR_HD cx<R> cmul_conj(cx<R> a, cx<R> b) {  // conj(a) * b
+  return {a.r * b.r + a.i * b.i, a.r * b.i - a.i * b.r};
+}
+template <class R>
+BR_HD cx<R> czero() { return {R(0), R(0)}; }
+
+// ------------------------------------------------------------ precision
+template <int P>
+struct Tr;
+template <>
+struct Tr<P_F64> {
+  using R = double;
+  static constexpr int spinor_planes = 12;
+  static constexpr int link_reals = 18;
+  static constexpr bool half = false;
+  static constexpr long spinor_bytes = 192;  // per site
+  static constexpr long link_bytes = 144;
+  static constexpr long clover_bytes = 576;
+};
+template <>
+struct Tr<P_F32> {
+  using R = float;
+  static constexpr int spinor_planes = 6;
+  static constexpr int link_reals = 12;
+  static constexpr bool half = false;
+  static constexpr long spinor_bytes = 96;
+  static constexpr long link_bytes = 48;
+  static constexpr long clover_bytes = 288;
+};
+template <>
+struct Tr<P_F16> {
+  using R = float;
+  static constexpr int spinor_planes = 3;
+  static constexpr int link_reals = 12;
+  static constexpr bool half = true;
+  static constexpr long spinor_bytes = 52;
+  static constexpr long link_bytes = 24;
+  static constexpr long clover_bytes = 144;
+};
+template <>
+struct Tr<P_BF16> {
+  using R = float;
+  static constexpr int spinor_planes = 3;
+  static constexpr int link_reals = 12;
+  static constexpr bool half = true;
+  static constexpr long spinor_bytes = 52;
+  static constexpr long link_bytes = 24;
+  static constexpr long clover_bytes = 144;
+};
+
+// Bytes of one half-lattice block (one parity, one right-hand side), padded
+// to 256 bytes so that every block of a multi-RHS field stays aligned.
+BR_HD long pad256(long b) { return (b + 255) & ~255L; }
+BR_HD long spinor_block_bytes(int prec, long vh) {
+  long b = prec == P_F64 ? 192 * vh : prec == P_F32 ? 96 * vh : 52 * vh;
+  return pad256(b);
+}
+BR_HD long link_block_bytes(int prec, long vh) {  // one parity, one direction
+  long b = prec == P_F64 ? 144 * vh : prec == P_F32 ? 48 * vh : 24 * vh;
+  return pad256(b);
+}
+BR_HD long clover_block_bytes(int prec, long vh) {  // one parity
+  long b = prec == P_F64 ? 576 * vh : prec == P_F32 ? 288 * vh : 144 * vh;
+  return pad256(b);
+}
+
+// ------------------------------------------------------- 16-bit helpers
+template <int P>
+struct H16;
+template <>
+struct H16<P_F16> {
+  BR_D float2 to2(uint32_t w) { return __half22float2(*reinterpret_cast<const __half2*>(&w)); }
+  BR_D uint32_t from2(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+};
+template <>
+struct H16<P_BF16> {
+  BR_D float2 to2(uint32_t w) { return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w)); }
+  BR_D uint32_t from2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+};
+
+// ------------------------------------------------------- spinor access
+// s[k] with k = spin * 3 + colour.
+template <int P, bool NC = true>
+BR_D void load_spinor(const char* base, long vh, uint32_t i, cx<typename Tr<P>::R> s[12]) {
+  if constexpr (P == P_F64) {
+    const double2* p = reinterpret_cast<const double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 v = NC ? __ldg(p + k * vh + i) : p[k * vh + i];
+      s[k] = {v.x, v.y};
+    }
+  } else if constexpr (P == P_F32) {
+    const float4* p = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float4 v = NC ? __ldg(p + k * vh + i) : p[k * vh + i];
+      s[2 * k] = {v.x, v.y};
+      s[2 * k + 1] = {v.z, v.w};
+    }
+  } else {
+    const uint4* p = reinterpret_cast<const uint4*>(base);
+    const float* sc = reinterpret_cast<const float*>(base + 48 * vh);
+    float scale = NC ? __ldg(sc + i) : sc[i];
+    H16<P> h;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 v = NC ? __ldg(p + k * vh + i) : p[k * vh + i];
+      float2 a = h.to2(v.x), b = h.to2(v.y), c = h.to2(v.z), d = h.to2(v.w);
+      s[4 * k + 0] = {a.x * scale, a.y * scale};
+      s[4 * k + 1] = {b.x * scale, b.y * scale};
+      s[4 * k + 2] = {c.x * scale, c.y * scale};
+      s[4 * k + 3] = {d.x * scale, d.y * scale};
+    }
+  }
+}
+
+template <int P>
+BR_D void store_spinor(char* base, long vh, uint32_t i, const cx<typename Tr<P>::R> s[12]) {
+  if constexpr (P == P_F64) {
+    double2* p = reinterpret_cast<double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k * vh + i] = make_double2(s[k].r, s[k].i);
+  } else if constexpr (P == P_F32) {
+    float4* p = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[k * vh + i] = make_float4(s[2 * k].r, s[2 * k].i, s[2 * k + 1].r, s[2 * k + 1].i);
+  } else {
+    // per-site scale = max |component|; stored values are component / scale
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(s[k].r), fabsf(s[k].i)));
+    float inv = m > 0.f ? 1.0f / m : 0.f;
+    uint4* p = reinterpret_cast<uint4*>(base);
+    float* sc = reinterpret_cast<float*>(base + 48 * vh);
+    H16<P> h;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 v;
+      v.x = h.from2(s[4 * k + 0].r * inv, s[4 * k + 0].i * inv);
+      v.y = h.from2(s[4 * k + 1].r * inv, s[4 * k + 1].i * inv);
+      v.z = h.from2(s[4 * k + 2].r * inv, s[4 * k + 2].i * inv);
+      v.w = h.from2(s[4 * k + 3].r * inv, s[4 * k + 3].i * inv);
+      p[k * vh + i] = v;
+    }
+    sc[i] = m;
+  }
+}
+
+// --------------------------------------------------------- link access
+template <class R>
+struct Link {
+  cx<R> m[3][3];
+};
+
+template <class R>
+BR_D void recon_row2(Link<R>& u) {
+  u.m[2][0] = conj(u.m[0][1] * u.m[1][2] - u.m[0][2] * u.m[1][1]);
+  u.m[2][1] = conj(u.m[0][2] * u.m[1][0] - u.m[0][0] * u.m[1][2]);
+  u.m[2][2] = conj(u.m[0][0] * u.m[1][1] - u.m[0][1] * u.m[1][0]);
+}
+
+// base points at the block of one (parity, direction).
+template <int P>
+BR_D void load_link(const char* base, long vh, uint32_t i, Link<typename Tr<P>::R>& u) {
+  if constexpr (P == P_F64) {
+    const double2* p = reinterpret_cast<const double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double2 v = __ldg(p + k * vh + i);
+      u.m[k / 3][k % 3] = {v.x, v.y};
+    }
+  } else if constexpr (P == P_F32) {
+    const float4* p = reinterpret_cast<const float4*>(base);
+    float4 a = __ldg(p + i), b = __ldg(p + vh + i), c = __ldg(p + 2 * vh + i);
+    u.m[0][0] = {a.x, a.y};
+    u.m[0][1] = {a.z, a.w};
+    u.m[0][2] = {b.x, b.y};
+    u.m[1][0] = {b.z, b.w};
+    u.m[1][1] = {c.x, c.y};
+    u.m[1][2] = {c.z, c.w};
+    recon_row2(u);
+  } else {
+    const uint2* p = reinterpret_cast<const uint2*>(base);
+    uint2 a = __ldg(p + i), b = __ldg(p + vh + i), c = __ldg(p + 2 * vh + i);
+    H16<P> h;
+    float2 t;
+    t = h.to2(a.x); u.m[0][0] = {t.x, t.y};
+    t = h.to2(a.y); u.m[0][1] = {t.x, t.y};
+    t = h.to2(b.x); u.m[0][2] = {t.x, t.y};
+    t = h.to2(b.y); u.m[1][0] = {t.x, t.y};
+    t = h.to2(c.x); u.m[1][1] = {t.x, t.y};
+    t = h.to2(c.y); u.m[1][2] = {t.x, t.y};
+    recon_row2(u);
+  }
+}
+
+// ------------------------------------------------------- clover access
+// Packed Hermitian 6x6 per chiral block b (spins 2b, 2b+1): reals
+// [36 b + 0 .. 36 b + 5] diagonal, then 15 complex (row, col) pairs with
+// row > col in row-major order.  F16/BF16 store the 72 reals as 9 planes of
+// 8 halves (block 0 = halves 0..35, block 1 = halves 36..71).
+template <int P>
+BR_D void load_clover_block(const char* base, long vh, uint32_t i, int b, typename Tr<P>::R a[36]) {
+  if constexpr (P == P_F64) {
+    const double2* p = reinterpret_cast<const double2*>(base) + 18 * b * vh;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+      double2 v = __ldg(p + k * vh + i);
+      a[2 * k] = v.x;
+      a[2 * k + 1] = v.y;
+    }
+  } else if constexpr (P == P_F32) {
+    const float4* p = reinterpret_cast<const float4*>(base) + 9 * b * vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      float4 v = __ldg(p + k * vh + i);
+      a[4 * k] = v.x;
+      a[4 * k + 1] = v.y;
+      a[4 * k + 2] = v.z;
+      a[4 * k + 3] = v.w;
+    }
+  } else {
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(base);
+    H16<P> h;
+    // 18 words of 2 halves; word w of the 72-half row lives in plane w / 4, lane w % 4
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+      const int w = 18 * b + k;
+      float2 t = h.to2(__ldg(p + ((w >> 2) * vh + i) * 4 + (w & 3)));
+      a[2 * k] = t.x;
+      a[2 * k + 1] = t.y;
+    }
+  }
+}
+
+template <class R>
+BR_D void hermitian6_apply(const R a[36], const cx<R> x[6], cx<R> y[6]) {
+  const R* o = a + 6;
+#pragma unroll
+  for (int r = 0; r < 6; ++r) y[r] = a[r] * x[r];
+  int k = 0;
+#pragma unroll
+  for (int r = 1; r < 6; ++r) {
+#pragma unroll
+    for (int c = 0; c < r; ++c) {
+      cx<R> arc = {o[2 * k], o[2 * k + 1]};
+      y[r] = y[r] + arc * x[c];
+      y[c] = y[c] + cmul_conj(arc, x[r]);
+      ++k;
+    }
+  }
+}
+
+// y = A x with A the packed site term at site i (x and y must not alias).
+template <int P>
+BR_D void clover_apply(const char* base, long vh, uint32_t i, const cx<typename Tr<P>::R> x[12],
+                       cx<typename Tr<P>::R> y[12]) {
+  using R = typename Tr<P>::R;
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    R a[36];
+    load_clover_block<P>(base, vh, i, b, a);
+    hermitian6_apply<R>(a, x + 6 * b, y + 6 * b);
+  }
+}
+
+// -------------------------------------------------------------- geometry
+// Division by an invariant 32-bit divisor (Granlund and Montgomery, PLDI
+// 1994, unsigned case): q = (umulhi(n, m) + n) >> l with l = ceil(log2 d)
+// and m = floor(2^32 (2^l - d) / d) + 1; exact for every 32-bit n.
+struct FastDiv {
+  uint32_t d, m, l;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  uint64_t m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+  return FastDiv{d, (uint32_t)m, l};
+}
+BR_HD uint32_t fdiv(uint32_t n, FastDiv f) {
+#ifdef __CUDA_ARCH__
+  uint32_t hi = __umulhi(n, f.m);
+#else
+  uint32_t hi = (uint32_t)(((uint64_t)n * f.m) >> 32);
+#endif
+  return (uint32_t)(((uint64_t)hi + n) >> f.l);
+}
+
+struct Geom {
+  int L[4];      // Lx, Ly, Lz, Lt
+  uint32_t Lxh;  // Lx / 2
+  uint32_t vh;   // V / 2
+  uint32_t s[4]; // half-lattice index strides for y, z, t (s[0] unused)
+  FastDiv dLxh, dLy, dLz;
+};
+
+inline Geom make_geom(const int dims[4]) {
+  Geom g;
+  for (int k = 0; k < 4; ++k) g.L[k] = dims[k];
+  g.Lxh = dims[0] / 2;
+  g.vh = (uint32_t)((long)dims[0] * dims[1] * dims[2] * dims[3] / 2);
+  g.s[0] = 1;
+  g.s[1] = g.Lxh;
+  g.s[2] = g.Lxh * dims[1];
+  g.s[3] = g.Lxh * dims[1] * dims[2];
+  g.dLxh = make_fastdiv(g.Lxh);
+  g.dLy = make_fastdiv(dims[1]);
+  g.dLz = make_fastdiv(dims[2]);
+  return g;
+}
+
+// Coordinates of half-lattice site ih of parity p; returns x/2 in xh.
+BR_HD void site_coords(const Geom& g, uint32_t ih, int p, int c[4], uint32_t& xh) {
+  uint32_t r = fdiv(ih, g.dLxh);
+  xh = ih - r * g.Lxh;
+  uint32_t r2 = fdiv(r, g.dLy);
+  c[1] = (int)(r - r2 * (uint32_t)g.L[1]);
+  uint32_t r3 = fdiv(r2, g.dLz);
+  c[2] = (int)(r2 - r3 * (uint32_t)g.L[2]);
+  c[3] = (int)r3;
+  c[0] = 2 * (int)xh + ((p + c[1] + c[2] + c[3]) & 1);
+}
+
+// Half-lattice index of the neighbours x + mu and x - mu (opposite parity)
+// and whether each hop wraps around the lattice.
+template <int MU>
+BR_HD void neighbours(const Geom& g, uint32_t ih, const int c[4], uint32_t xh, uint32_t& fwd, uint32_t& bwd,
+                      bool& wf, bool& wb) {
+  if (MU == 0) {
+    int xp = c[0] + 1, xm = c[0] - 1;
+    wf = (xp == g.L[0]);
+    wb = (c[0] == 0);
+    if (wf) xp = 0;
+    if (wb) xm = g.L[0] - 1;
+    uint32_t row = ih - xh;
+    fwd = row + ((uint32_t)xp >> 1);
+    bwd = row + ((uint32_t)xm >> 1);
+  } else {
+    const uint32_t s = g.s[MU];
+    const int L = g.L[MU];
+    wf = (c[MU] == L - 1);
+    wb = (c[MU] == 0);
+    fwd = wf ? ih - (uint32_t)(L - 1) * s : ih + s;
+    bwd = wb ? ih + (uint32_t)(L - 1) * s : ih - s;
+  }
+}
+
+// Runtime-direction form used by host-side checks and the clover builder.
+BR_HD uint32_t neighbour_rt(const Geom& g, uint32_t ih, const int c[4], uint32_t xh, int mu, int step) {
+  uint32_t f, b;
+  bool wf, wb;
+  switch (mu) {
+    case 0: neighbours<0>(g, ih, c, xh, f, b, wf, wb); break;
+    case 1: neighbours<1>(g, ih, c, xh, f, b, wf, wb); break;
+    case 2: neighbours<2>(g, ih, c, xh, f, b, wf, wb); break;
+    default: neighbours<3>(g, ih, c, xh, f, b, wf, wb); break;
+  }
+  return step > 0 ? f : b;
+}
+
+// ------------------------------------------------------ solver scalars
+// Complex BiCGStab scalars of one right-hand side, kept on the device so
+// that no iteration needs the host.
+struct BiCGScalars {
+  double rho_r, rho_i, alpha_r, alpha_i, omega_r, omega_i, beta_r, beta_i;
+  double r2, b2, tol2, rhat2;
+  int iter, done, max_iter, pad;
+};
+enum Done { RUNNING = 0, CONVERGED = 1, BREAKDOWN = 2, MAXITER = 3 };
+
+}  // namespace bridge

@@ -1,0 +1,251 @@
+// The Wilson/clover hopping stencil and its fused epilogues.
+//
+// Operator (Sec. 2 of the paper implements the Wilson and clover fermion
+// operators and their even-odd blocks, Eq. 1; the formula is the standard
+// one, with the chiral gamma basis):
+//   (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu)
+//              + (1 + gamma_mu) U_mu(x-mu)^dagger psi(x-mu),
+// boundary phase bc[mu] on every hop that wraps around the lattice.
+//
+// One thread computes one output site of one right-hand side.  Each of the
+// eight hops projects the neighbour spinor onto its two independent spin
+// components (a half spinor), multiplies by the link, and reconstructs the
+// other two, so only 2 x (3x3 complex matrix times 3-vector) per hop.  The
+// result of the hop term is combined in registers:
+//
+//   out = s1 * M(self) + E( beta * H(in) + caux * aux )
+//
+// with M in {1, T} (F_SELF, F_SELF_CLOV) and E in {1, T^-1} (F_E_CLOV); this
+// single kernel covers D_eo / D_oe, the full operator T - kappa H, both
+// passes of the Schur operator of Eq. 1, the even-odd source preparation and
+// solution reconstruction, and the FP64 residual b - D x.  Optional fused
+// reductions: |out|^2, <a, out>, or (<out, self>, |out|^2).
+#pragma once
+
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace bridge {
+
+enum HopFlags { F_SELF = 1, F_SELF_CLOV = 2, F_E_CLOV = 4, F_AUX = 8 };
+enum RedMode { R_NONE = 0, R_NORM = 1, R_DOT_A = 2, R_TS = 3 };
+
+struct HopArgs {
+  Geom g;
+  int out_parity;
+  int nrhs;
+  int nblk;  // site blocks per right-hand side (grid = nblk * nrhs)
+  double beta, s1, caux;
+  double bc[4];
+  // Field pointers address the block of the right parity for rhs 0; *_rs is
+  // the byte stride between right-hand sides.
+  char* out;
+  long out_rs;
+  const char* in;
+  long in_rs;
+  const char* self;
+  long self_rs;
+  const char* aux;
+  long aux_rs;
+  const char* avec;
+  long avec_rs;
+  const char* gauge;  // [parity][mu] link blocks
+  const char* clovE;  // [parity] clover blocks (T^-1)
+  const char* clovM;  // [parity] clover blocks (T)
+  RedArgs red;
+};
+
+template <class R, int MU, bool FWD>
+BR_D void project(const cx<R> p[12], cx<R> h[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cx<R> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+    if (MU == 0) {
+      h[0][c] = FWD ? p0 + times_i(p3) : p0 - times_i(p3);
+      h[1][c] = FWD ? p1 + times_i(p2) : p1 - times_i(p2);
+    } else if (MU == 1) {
+      h[0][c] = FWD ? p0 + p3 : p0 - p3;
+      h[1][c] = FWD ? p1 - p2 : p1 + p2;
+    } else if (MU == 2) {
+      h[0][c] = FWD ? p0 + times_i(p2) : p0 - times_i(p2);
+      h[1][c] = FWD ? p1 - times_i(p3) : p1 + times_i(p3);
+    } else {
+      h[0][c] = FWD ? p0 - p2 : p0 + p2;
+      h[1][c] = FWD ? p1 - p3 : p1 + p3;
+    }
+  }
+}
+
+template <class R, int MU, bool FWD>
+BR_D void reconstruct(const cx<R> u[2][3], cx<R> acc[12]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cx<R> u0 = u[0][c], u1 = u[1][c];
+    acc[c] = acc[c] + u0;
+    acc[3 + c] = acc[3 + c] + u1;
+    if (MU == 0) {
+      acc[6 + c] = FWD ? acc[6 + c] + times_mi(u1) : acc[6 + c] + times_i(u1);
+      acc[9 + c] = FWD ? acc[9 + c] + times_mi(u0) : acc[9 + c] + times_i(u0);
+    } else if (MU == 1) {
+      acc[6 + c] = FWD ? acc[6 + c] - u1 : acc[6 + c] + u1;
+      acc[9 + c] = FWD ? acc[9 + c] + u0 : acc[9 + c] - u0;
+    } else if (MU == 2) {
+      acc[6 + c] = FWD ? acc[6 + c] + times_mi(u0) : acc[6 + c] + times_i(u0);
+      acc[9 + c] = FWD ? acc[9 + c] + times_i(u1) : acc[9 + c] + times_mi(u1);
+    } else {
+      acc[6 + c] = FWD ? acc[6 + c] - u0 : acc[6 + c] + u0;
+      acc[9 + c] = FWD ? acc[9 + c] - u1 : acc[9 + c] + u1;
+    }
+  }
+}
+
+// One hop: psi at half-lattice site nb of the input, link block lb at index li.
+template <int P, int MU, bool FWD>
+BR_D void hop_one(const char* in, const char* lb, long vh, uint32_t nb, uint32_t li, bool wraps, double bc,
+                  cx<typename Tr<P>::R> acc[12]) {
+  using R = typename Tr<P>::R;
+  cx<R> h[2][3];
+  {
+    cx<R> psi[12];
+    load_spinor<P>(in, vh, nb, psi);
+    project<R, MU, FWD>(psi, h);
+  }
+  if (wraps) {
+    const R ph = (R)bc;
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) h[k][c] = ph * h[k][c];
+  }
+  Link<R> U;
+  load_link<P>(lb, vh, li, U);
+  cx<R> u[2][3];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (FWD)
+        u[k][r] = U.m[r][0] * h[k][0] + U.m[r][1] * h[k][1] + U.m[r][2] * h[k][2];
+      else
+        u[k][r] = cmul_conj(U.m[0][r], h[k][0]) + cmul_conj(U.m[1][r], h[k][1]) + cmul_conj(U.m[2][r], h[k][2]);
+    }
+  reconstruct<R, MU, FWD>(u, acc);
+}
+
+template <int P, int MU>
+BR_D void hop_dir(const HopArgs& a, const char* in, const char* g_out, const char* g_in, long lbb, uint32_t ih,
+                  const int c[4], uint32_t xh, cx<typename Tr<P>::R> acc[12]) {
+  uint32_t f, b;
+  bool wf, wb;
+  neighbours<MU>(a.g, ih, c, xh, f, b, wf, wb);
+  // forward: link U_mu(x) lives at x (output parity); backward: U_mu(x - mu) at x - mu.
+  hop_one<P, MU, true>(in, g_out + MU * lbb, a.g.vh, f, ih, wf, a.bc[MU], acc);
+  hop_one<P, MU, false>(in, g_in + MU * lbb, a.g.vh, b, b, wb, a.bc[MU], acc);
+}
+
+template <int P, int FL, int RED>
+__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
+  using R = typename Tr<P>::R;
+  const int nrhs = a.nrhs;
+  const int rhs = blockIdx.x % nrhs;
+  const int sb = blockIdx.x / nrhs;
+  const long vh = a.g.vh;
+  constexpr int NV = RED == R_NORM ? 1 : RED == R_DOT_A ? 2 : 3;
+  double rv[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) rv[k] = 0.0;
+  const bool skip = a.red.check_done && a.red.sc != nullptr && a.red.sc[rhs].done != RUNNING;
+  if (!skip) {
+    const int p = a.out_parity;
+    const long lbb = link_block_bytes(P, vh), cbb = clover_block_bytes(P, vh);
+    const char* g_out = a.gauge + (long)p * 4 * lbb;
+    const char* g_in = a.gauge + (long)(1 - p) * 4 * lbb;
+    const char* in = a.in + rhs * a.in_rs;
+    const uint32_t stride = (uint32_t)a.nblk * blockDim.x;
+    for (uint32_t ih = sb * blockDim.x + threadIdx.x; ih < (uint32_t)vh; ih += stride) {
+      int c[4];
+      uint32_t xh;
+      site_coords(a.g, ih, p, c, xh);
+      cx<R> acc[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = czero<R>();
+      hop_dir<P, 0>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+      hop_dir<P, 1>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+      hop_dir<P, 2>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+      hop_dir<P, 3>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+      const R beta = (R)a.beta;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = beta * acc[k];
+      if (FL & F_AUX) {
+        cx<R> x[12];
+        load_spinor<P>(a.aux + rhs * a.aux_rs, vh, ih, x);
+        const R ca = (R)a.caux;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = acc[k] + ca * x[k];
+      }
+      cx<R> v[12];
+      if (FL & F_E_CLOV) {
+        clover_apply<P>(a.clovE + p * cbb, vh, ih, acc, v);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = acc[k];
+      }
+      cx<R> s[12];
+      if (FL & F_SELF) {
+        load_spinor<P>(a.self + rhs * a.self_rs, vh, ih, s);
+        const R s1 = (R)a.s1;
+        if (FL & F_SELF_CLOV) {
+          cx<R> ms[12];
+          clover_apply<P>(a.clovM + p * cbb, vh, ih, s, ms);
+#pragma unroll
+          for (int k = 0; k < 12; ++k) v[k] = v[k] + s1 * ms[k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < 12; ++k) v[k] = v[k] + s1 * s[k];
+        }
+      }
+      store_spinor<P>(a.out + rhs * a.out_rs, vh, ih, v);
+      if (RED == R_NORM) {
+        R n = 0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) n += v[k].r * v[k].r + v[k].i * v[k].i;
+        rv[0] += (double)n;
+      } else if (RED == R_DOT_A) {
+        cx<R> w[12];
+        load_spinor<P>(a.avec + rhs * a.avec_rs, vh, ih, w);
+        cx<R> d = czero<R>();
+#pragma unroll
+        for (int k = 0; k < 12; ++k) d = d + cmul_conj(w[k], v[k]);
+        rv[0] += (double)d.r;
+        rv[1] += (double)d.i;
+      } else if (RED == R_TS) {
+        cx<R> d = czero<R>();
+        R n = 0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          d = d + cmul_conj(v[k], s[k]);
+          n += v[k].r * v[k].r + v[k].i * v[k].i;
+        }
+        rv[0] += (double)d.r;
+        rv[1] += (double)d.i;
+        rv[2] += (double)n;
+      }
+    }
+  }
+  if (RED != R_NONE) reduce_finalize<NV>(a.red, rhs, sb, a.nblk, nrhs, rv);
+}
+
+// Launch with the given block size on a stream; returns false for a
+// (flags, reduction) pair that is not instantiated.
+template <int P>
+bool launch_hop(int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+template <>
+bool launch_hop<P_F64>(int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+template <>
+bool launch_hop<P_F32>(int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+template <>
+bool launch_hop<P_F16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+template <>
+bool launch_hop<P_BF16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+
+}  // namespace bridge

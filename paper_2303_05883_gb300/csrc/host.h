@@ -1,0 +1,182 @@
+// Host-side runtime of libbridge: lattice handles, device fields, operator
+// application and launch bookkeeping.  Everything here is plain C++ around
+// the CUDA runtime; no PyTorch types appear.
+#pragma once
+
+#include <atomic>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/bridge.h"
+#include "kernels.h"
+
+namespace bridge {
+
+// ------------------------------------------------------------ errors
+struct Error {
+  int code;
+  std::string msg;
+};
+void set_error(int code, const std::string& msg);
+#define BR_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) throw ::bridge::Error{BRIDGE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+#define BR_CHECK(cond, code, msg) \
+  do {                            \
+    if (!(cond)) throw ::bridge::Error{(code), (msg)}; \
+  } while (0)
+
+// ------------------------------------------------------- kernel stats
+enum KClass {
+  K_HOP = 0,     // D_eo / D_oe
+  K_FULLD,       // full operator, one parity
+  K_DHAT1,       // Schur pass 1: T^-1 D_oe
+  K_DHAT2,       // Schur pass 2 (+ fused dot products)
+  K_PREP,        // even-odd prepare / reconstruct
+  K_RESID,       // FP64 residual b - D x with |r|^2
+  K_BLAS_INIT,
+  K_BLAS_S,
+  K_BLAS_XR,
+  K_BLAS_P,
+  K_CONVERT,
+  K_NORM,
+  K_CLOVER,
+  K_SETUP,
+  K_NCLASS
+};
+const char* kclass_name(int k);
+
+struct KStat {
+  long launches = 0;
+  double bytes = 0, flops = 0, ms = 0;
+};
+
+// --------------------------------------------------------- device memory
+struct DevBuf {
+  char* ptr = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  explicit DevBuf(size_t n);
+  ~DevBuf();
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// A spinor field in the GPU layout: nrhs x (1 or 2 parity blocks).
+struct Field {
+  int prec = P_F32;
+  int subset = BRIDGE_FULL;  // BRIDGE_EVEN, BRIDGE_ODD, BRIDGE_FULL
+  int nrhs = 1;
+  long vh = 0;
+  long block = 0;  // bytes of one parity block
+  long rs = 0;     // bytes between right-hand sides
+  std::shared_ptr<DevBuf> buf;
+  char* ptr(int parity) const {  // block of this parity for rhs 0
+    return buf->ptr + ((subset == BRIDGE_FULL && parity == 1) ? block : 0);
+  }
+};
+Field make_field(int prec, int subset, int nrhs, long vh);
+
+// ----------------------------------------------------------- tuning
+// Launch shapes picked per (kernel class, precision, flags, lattice, nrhs).
+struct LaunchShape {
+  int block = 256;
+  int nblk = 0;  // site blocks per rhs; 0 -> cover the lattice once
+};
+
+struct Stats {
+  std::mutex mu;
+  KStat k[K_NCLASS];
+  // optional per-launch event timing
+  bool profiling = false;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+}  // namespace bridge
+
+// ------------------------------------------------------------- lattice
+struct bridge_lattice_s {
+  int dims[4];
+  long V, vh;
+  bridge::Geom g;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  // links per precision; [0] (F64, 18 reals) is the master copy
+  std::unique_ptr<bridge::DevBuf> gauge[4];
+  bool have_gauge = false;
+  // clover: T and T^-1 per precision, built for kcsw = kappa * c_sw
+  double kcsw = 0.0;
+  bool have_clover = false;
+  std::unique_ptr<bridge::DevBuf> T[4], Tinv[4];
+  // reduction scratch for the operator entry points
+  std::unique_ptr<bridge::DevBuf> red_partials, red_result;
+  std::unique_ptr<bridge::DevBuf> red_counter;
+  double* red_result_host = nullptr;  // pinned
+  // staging for canonical fields of the host-pointer entry points
+  std::unique_ptr<bridge::DevBuf> stage_in, stage_out;
+  std::map<std::string, bridge::LaunchShape> tuned;
+  std::map<std::string, bridge::Field> ws;  // reusable fields of the operator entry points
+  bridge::Stats stats;
+  std::mutex api_mu;  // serialises host entry points on one lattice
+};
+
+namespace bridge {
+
+// launch bookkeeping (called at each launch site)
+void note_launch(bridge_lattice_s* L, int cls, double bytes, double flops, cudaStream_t st, bool begin);
+LaunchShape shape_for(bridge_lattice_s* L, const std::string& key, long vh, int nrhs);
+int sm_count();
+
+// gauge / clover on demand
+const char* gauge_ptr(bridge_lattice_s* L, int prec);
+const char* clover_ptr(bridge_lattice_s* L, int prec, bool inverse, double kcsw);
+
+// ------------------------------------------------------- operators
+// Apply one hop-kernel variant (see dslash.cuh).  Field pointers are the
+// parity blocks of rhs 0; strides are per right-hand side.
+struct HopCall {
+  int prec, flags = 0, red = R_NONE, out_parity = 0, nrhs = 1, cls = K_HOP;
+  double beta = 0, s1 = 0, caux = 0;
+  int bc[4] = {1, 1, 1, -1};
+  char* out = nullptr;
+  long out_rs = 0;
+  const char *in = nullptr, *self = nullptr, *aux = nullptr, *avec = nullptr;
+  long in_rs = 0, self_rs = 0, aux_rs = 0, avec_rs = 0;
+  double kcsw = 0;
+  RedArgs redargs{};
+};
+void run_hop(bridge_lattice_s* L, HopCall c, cudaStream_t st);
+
+// Operator entry points on fields (asynchronous on st).
+void apply_deo(bridge_lattice_s* L, const bridge_op& op, int out_parity, const Field& out, const Field& in, cudaStream_t st);
+void apply_d(bridge_lattice_s* L, const bridge_op& op, const Field& out, const Field& in, cudaStream_t st);
+void apply_dhat(bridge_lattice_s* L, const bridge_op& op, const Field& out, const Field& in, const Field& tmp_odd,
+                cudaStream_t st);
+
+// Canonical FP64 (device) <-> field.  full: canonical holds whole lattices.
+void canon_to_field(bridge_lattice_s* L, const double* canon, const Field& f, cudaStream_t st, const int* mask = nullptr);
+void field_to_canon(bridge_lattice_s* L, const Field& f, double* canon, cudaStream_t st);
+void convert_field(bridge_lattice_s* L, const Field& src, const Field& dst, int parity, cudaStream_t st, const int* mask);
+void accumulate64(bridge_lattice_s* L, const Field& src, int src_parity, const Field& dst64, int dst_parity, cudaStream_t st,
+                  const int* mask);
+void norm2_field(bridge_lattice_s* L, const Field& f, int parity, RedArgs red, cudaStream_t st);
+void clover_site(bridge_lattice_s* L, int prec, bool inverse, double kcsw, int parity, const Field& src, int sp,
+                 const Field& dst, int dp, int nrhs, cudaStream_t st);
+
+// Reusable field of this lattice (allocated on first use).
+Field& workspace(bridge_lattice_s* L, const std::string& name, int prec, int subset, int nrhs);
+
+bool op_is_clover(const bridge_op& op);
+double op_kcsw(const bridge_op& op);
+
+}  // namespace bridge

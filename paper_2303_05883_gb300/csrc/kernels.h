@@ -1,0 +1,64 @@
+// Host-visible declarations of the kernel launchers (implemented in the .cu
+// translation units) used by the lattice, operator and solver code.
+#pragma once
+
+#include "dslash.cuh"
+
+namespace bridge {
+
+// ---------------------------------------------------------------- hop
+bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+
+// ----------------------------------------------------- BiCGStab vectors
+enum BlasOp { B_INIT = 0, B_S = 1, B_XR = 2, B_P = 3 };
+struct BlasArgs {
+  uint32_t vh;
+  int nrhs, nblk;
+  char* x;  // precision px
+  long x_rs;
+  char *r, *p, *v, *s, *t, *rhat;
+  long r_rs, p_rs, v_rs, s_rs, t_rs, rhat_rs;
+  const char* b;
+  long b_rs;
+  RedArgs red;
+};
+// B_INIT: x = 0, r = rhat = p = b, |b|^2 -> FIN_INIT
+// B_S:    s = r - alpha v
+// B_XR:   x += alpha p + omega s, r = s - omega t, (<rhat, r>, |r|^2) -> FIN_RHO
+// B_P:    p = r + beta (p - omega v)
+bool launch_blas(int op, int prec, int px, const BlasArgs& a, int block, cudaStream_t st);
+
+// ------------------------------------------------------------ layout
+struct CopyArgs {
+  uint32_t vh;
+  int nrhs, nblk;
+  int parity;   // parity of the half-lattice block (full-canonical conversions)
+  Geom g;
+  long V;       // full volume (canonical full-lattice strides)
+  const double* canon;  // canonical FP64 (re, im) pairs
+  double* canon_out;
+  int canon_full;       // 1: canonical is a full-lattice field, 0: a half-lattice one
+  const char* src;
+  long src_rs;
+  char* dst;
+  long dst_rs;
+  const int* mask;      // per rhs; 0 -> write zeros (may be null)
+  RedArgs red;          // norm of the source (FIN_STORE) when red.partials != null
+};
+bool launch_canon_to_field(int prec, const CopyArgs& a, int block, cudaStream_t st);
+bool launch_field_to_canon(int prec, const CopyArgs& a, int block, cudaStream_t st);
+bool launch_convert(int ps, int pd, const CopyArgs& a, int block, cudaStream_t st);   // dst = mask ? src : 0
+bool launch_accumulate64(int ps, const CopyArgs& a, int block, cudaStream_t st);      // dst(F64) += src
+bool launch_norm2(int prec, const CopyArgs& a, int block, cudaStream_t st);           // |src|^2 -> FIN_STORE
+bool launch_clover_site(int prec, const CopyArgs& a, const char* clov, int block, cudaStream_t st);  // dst = A src
+
+// ------------------------------------------------------- gauge, clover
+// Canonical FP64 links (4, V, 3, 3) -> internal F64 blocks [parity][mu].
+void launch_gauge_from_canon(const double* U, const Geom& g, char* g64, cudaStream_t st);
+// Internal F64 links -> internal links of another precision.
+bool launch_gauge_convert(int prec, const Geom& g, const char* g64, char* gp, cudaStream_t st);
+// Clover term T = 1 - kcsw * sum sigma F and its inverse, packed FP64 [parity].
+void launch_clover_build(const Geom& g, const char* g64, double kcsw, char* T64, char* Tinv64, cudaStream_t st);
+bool launch_clover_convert(int prec, const Geom& g, const char* c64, char* cp, cudaStream_t st);
+
+}  // namespace bridge

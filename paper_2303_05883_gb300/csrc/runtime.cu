@@ -1,0 +1,420 @@
+// Host runtime: device buffers, fields, gauge and clover storage, operator
+// application, launch statistics and launch shapes.
+#include <cstring>
+#include <string>
+
+#include "host.h"
+
+namespace bridge {
+
+static thread_local std::string tl_last_error;
+void set_error(int code, const std::string& msg) {
+  (void)code;
+  tl_last_error = msg;
+}
+const char* last_error_text() { return tl_last_error.c_str(); }
+
+std::atomic<long> g_launches{0};
+
+const char* kclass_name(int k) {
+  static const char* names[K_NCLASS] = {"hop_deo",   "dirac_full", "schur_pass1", "schur_pass2", "evenodd_prep",
+                                        "residual64", "blas_init",  "blas_s",      "blas_xr",     "blas_p",
+                                        "convert",   "norm",       "clover_site", "setup"};
+  return (k >= 0 && k < K_NCLASS) ? names[k] : "?";
+}
+
+DevBuf::DevBuf(size_t n) {
+  if (n == 0) return;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ptr), n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+    throw Error{BRIDGE_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e)};
+  }
+  bytes = n;
+}
+DevBuf::~DevBuf() {
+  if (ptr) cudaFree(ptr);
+}
+
+Field make_field(int prec, int subset, int nrhs, long vh) {
+  Field f;
+  f.prec = prec;
+  f.subset = subset;
+  f.nrhs = nrhs;
+  f.vh = vh;
+  f.block = spinor_block_bytes(prec, vh);
+  f.rs = (subset == BRIDGE_FULL ? 2 : 1) * f.block;
+  f.buf = std::make_shared<DevBuf>((size_t)(f.rs * (nrhs > 0 ? nrhs : 1)));
+  return f;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// ----------------------------------------------------------- statistics
+void note_launch(bridge_lattice_s* L, int cls, double bytes, double flops, cudaStream_t st, bool begin) {
+  Stats& S = L->stats;
+  std::lock_guard<std::mutex> lk(S.mu);
+  if (begin) {
+    g_launches.fetch_add(1);
+    S.k[cls].launches += 1;
+    S.k[cls].bytes += bytes;
+    S.k[cls].flops += flops;
+    if (S.profiling) {
+      Stats::Rec r;
+      r.cls = cls;
+      if (S.pool.size() < 2) {
+        cudaEvent_t e;
+        for (int i = 0; i < 64; ++i) {
+          cudaEventCreate(&e);
+          S.pool.push_back(e);
+        }
+      }
+      r.a = S.pool.back();
+      S.pool.pop_back();
+      r.b = S.pool.back();
+      S.pool.pop_back();
+      cudaEventRecord(r.a, st);
+      S.recs.push_back(r);
+    }
+  } else if (S.profiling && !S.recs.empty()) {
+    cudaEventRecord(S.recs.back().b, st);
+  }
+}
+
+// Launch shape: block size and the number of site blocks per right-hand
+// side.  The autotuner (tune.cu) fills L->tuned; the default covers the
+// half lattice once with 128-thread blocks.
+LaunchShape shape_for(bridge_lattice_s* L, const std::string& key, long vh, int nrhs) {
+  (void)nrhs;
+  auto it = L->tuned.find(key);
+  LaunchShape s;
+  if (it != L->tuned.end()) s = it->second;
+  else s.block = 128;
+  long cover = (vh + s.block - 1) / s.block;
+  if (s.nblk <= 0 || s.nblk > cover) s.nblk = (int)cover;
+  return s;
+}
+
+static void ensure_red_scratch(bridge_lattice_s* L, long n_partials, int nrhs) {
+  size_t need = (size_t)n_partials * 4 * sizeof(double);
+  if (!L->red_partials || L->red_partials->bytes < need) L->red_partials.reset(new DevBuf(need));
+  size_t rneed = (size_t)(nrhs > 0 ? nrhs : 1) * 4 * sizeof(double);
+  if (!L->red_result || L->red_result->bytes < rneed) L->red_result.reset(new DevBuf(rneed < 4096 ? 4096 : rneed));
+  if (!L->red_counter) {
+    L->red_counter.reset(new DevBuf(256));
+    BR_CUDA(cudaMemsetAsync(L->red_counter->ptr, 0, 256, L->stream));
+  }
+}
+
+// ------------------------------------------------------- gauge / clover
+bool op_is_clover(const bridge_op& op) { return op.kind == BRIDGE_CLOVER && op.csw != 0.0 && op.kappa != 0.0; }
+double op_kcsw(const bridge_op& op) { return op_is_clover(op) ? op.kappa * op.csw : 0.0; }
+
+const char* gauge_ptr(bridge_lattice_s* L, int prec) {
+  BR_CHECK(L->have_gauge, BRIDGE_ESTATE, "no gauge field uploaded");
+  if (!L->gauge[prec]) {
+    L->gauge[prec].reset(new DevBuf((size_t)(8 * link_block_bytes(prec, L->vh))));
+    note_launch(L, K_SETUP, 0, 0, L->stream, true);
+    BR_CHECK(launch_gauge_convert(prec, L->g, L->gauge[P_F64]->ptr, L->gauge[prec]->ptr, L->stream), BRIDGE_EINVAL,
+             "gauge precision");
+    note_launch(L, K_SETUP, 0, 0, L->stream, false);
+    BR_CUDA(cudaGetLastError());
+  }
+  return L->gauge[prec]->ptr;
+}
+
+const char* clover_ptr(bridge_lattice_s* L, int prec, bool inverse, double kcsw) {
+  BR_CHECK(L->have_gauge, BRIDGE_ESTATE, "no gauge field uploaded");
+  if (!L->have_clover || L->kcsw != kcsw) {
+    for (int p = 0; p < 4; ++p) {
+      if (p != P_F64) {
+        L->T[p].reset();
+        L->Tinv[p].reset();
+      }
+    }
+    size_t n = (size_t)(2 * clover_block_bytes(P_F64, L->vh));
+    if (!L->T[P_F64]) L->T[P_F64].reset(new DevBuf(n));
+    if (!L->Tinv[P_F64]) L->Tinv[P_F64].reset(new DevBuf(n));
+    note_launch(L, K_SETUP, 0, 0, L->stream, true);
+    launch_clover_build(L->g, L->gauge[P_F64]->ptr, kcsw, L->T[P_F64]->ptr, L->Tinv[P_F64]->ptr, L->stream);
+    note_launch(L, K_SETUP, 0, 0, L->stream, false);
+    BR_CUDA(cudaGetLastError());
+    L->kcsw = kcsw;
+    L->have_clover = true;
+  }
+  std::unique_ptr<DevBuf>* arr = inverse ? L->Tinv : L->T;
+  if (!arr[prec]) {
+    arr[prec].reset(new DevBuf((size_t)(2 * clover_block_bytes(prec, L->vh))));
+    note_launch(L, K_SETUP, 0, 0, L->stream, true);
+    BR_CHECK(launch_clover_convert(prec, L->g, arr[P_F64]->ptr, arr[prec]->ptr, L->stream), BRIDGE_EINVAL,
+             "clover precision");
+    note_launch(L, K_SETUP, 0, 0, L->stream, false);
+    BR_CUDA(cudaGetLastError());
+  }
+  return arr[prec]->ptr;
+}
+
+// ------------------------------------------------------------ operators
+static long spinor_site_bytes(int prec) { return prec == P_F64 ? 192 : prec == P_F32 ? 96 : 52; }
+static long link_site_bytes(int prec) { return prec == P_F64 ? 144 : prec == P_F32 ? 48 : 24; }
+static long clover_site_bytes(int prec) { return prec == P_F64 ? 576 : prec == P_F32 ? 288 : 144; }
+
+static std::string dims_key(const bridge_lattice_s* L) {
+  return std::to_string(L->dims[0]) + "x" + std::to_string(L->dims[1]) + "x" + std::to_string(L->dims[2]) + "x" +
+         std::to_string(L->dims[3]);
+}
+
+void run_hop(bridge_lattice_s* L, HopCall c, cudaStream_t st) {
+  HopArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = L->g;
+  a.out_parity = c.out_parity;
+  a.nrhs = c.nrhs;
+  a.beta = c.beta;
+  a.s1 = c.s1;
+  a.caux = c.caux;
+  for (int k = 0; k < 4; ++k) a.bc[k] = (double)c.bc[k];
+  a.out = c.out;
+  a.out_rs = c.out_rs;
+  a.in = c.in;
+  a.in_rs = c.in_rs;
+  a.self = c.self;
+  a.self_rs = c.self_rs;
+  a.aux = c.aux;
+  a.aux_rs = c.aux_rs;
+  a.avec = c.avec;
+  a.avec_rs = c.avec_rs;
+  a.gauge = gauge_ptr(L, c.prec);
+  a.clovE = (c.flags & F_E_CLOV) ? clover_ptr(L, c.prec, true, c.kcsw) : nullptr;
+  a.clovM = (c.flags & F_SELF_CLOV) ? clover_ptr(L, c.prec, false, c.kcsw) : nullptr;
+  const std::string key = "hop/" + std::to_string(c.prec) + "/" + std::to_string(c.flags) + "/" +
+                          std::to_string(c.red) + "/" + dims_key(L) + "/" + std::to_string(c.nrhs);
+  LaunchShape sh = shape_for(L, key, L->vh, c.nrhs);
+  a.nblk = sh.nblk;
+  a.red = c.redargs;
+  if (c.red != R_NONE && a.red.partials == nullptr) {
+    ensure_red_scratch(L, (long)sh.nblk * c.nrhs, c.nrhs);
+    a.red.partials = reinterpret_cast<double*>(L->red_partials->ptr);
+    a.red.counter = reinterpret_cast<unsigned*>(L->red_counter->ptr);
+    a.red.result = reinterpret_cast<double*>(L->red_result->ptr);
+    if (a.red.fin == FIN_NONE) a.red.fin = FIN_STORE;
+  }
+  const long S = spinor_site_bytes(c.prec);
+  long per_rhs = 2 * S;  // one input read, one output written
+  if (c.flags & F_SELF) per_rhs += S;
+  if (c.flags & F_AUX) per_rhs += S;
+  if (c.red == R_DOT_A) per_rhs += S;
+  long shared = 8 * link_site_bytes(c.prec);
+  if (c.flags & F_E_CLOV) shared += clover_site_bytes(c.prec);
+  if (c.flags & F_SELF_CLOV) shared += clover_site_bytes(c.prec);
+  const double bytes = (double)L->vh * ((double)per_rhs * c.nrhs + (double)shared);
+  double fl = 1320 + 24;
+  if (c.flags & F_E_CLOV) fl += 504;
+  if (c.flags & F_SELF_CLOV) fl += 504;
+  if (c.flags & F_SELF) fl += 48;
+  if (c.flags & F_AUX) fl += 48;
+  if (c.red != R_NONE) fl += 48;
+  const double flops = (double)L->vh * c.nrhs * fl;
+  note_launch(L, c.cls, bytes, flops, st, true);
+  BR_CHECK(launch_hop_any(c.prec, c.flags, c.red, a, sh.block, st), BRIDGE_EINVAL, "hop variant not instantiated");
+  note_launch(L, c.cls, bytes, flops, st, false);
+  BR_CUDA(cudaGetLastError());
+}
+
+void apply_deo(bridge_lattice_s* L, const bridge_op& op, int q, const Field& out, const Field& in, cudaStream_t st) {
+  HopCall c;
+  c.prec = in.prec;
+  c.flags = 0;
+  c.cls = K_HOP;
+  c.out_parity = q;
+  c.nrhs = in.nrhs;
+  c.beta = -op.kappa;
+  for (int k = 0; k < 4; ++k) c.bc[k] = op.bc[k];
+  c.out = out.ptr(q);
+  c.out_rs = out.rs;
+  c.in = in.ptr(1 - q);
+  c.in_rs = in.rs;
+  run_hop(L, c, st);
+}
+
+void apply_d(bridge_lattice_s* L, const bridge_op& op, const Field& out, const Field& in, cudaStream_t st) {
+  const bool clov = op_is_clover(op);
+  for (int q = 0; q < 2; ++q) {
+    HopCall c;
+    c.prec = in.prec;
+    c.flags = F_SELF | (clov ? F_SELF_CLOV : 0);
+    c.cls = K_FULLD;
+    c.out_parity = q;
+    c.nrhs = in.nrhs;
+    c.beta = -op.kappa;
+    c.s1 = 1.0;
+    c.kcsw = op_kcsw(op);
+    for (int k = 0; k < 4; ++k) c.bc[k] = op.bc[k];
+    c.out = out.ptr(q);
+    c.out_rs = out.rs;
+    c.in = in.ptr(1 - q);
+    c.in_rs = in.rs;
+    c.self = in.ptr(q);
+    c.self_rs = in.rs;
+    run_hop(L, c, st);
+  }
+}
+
+void apply_dhat(bridge_lattice_s* L, const bridge_op& op, const Field& out, const Field& in, const Field& tmp,
+                cudaStream_t st) {
+  const bool clov = op_is_clover(op);
+  HopCall c;
+  c.prec = in.prec;
+  c.nrhs = in.nrhs;
+  c.kcsw = op_kcsw(op);
+  for (int k = 0; k < 4; ++k) c.bc[k] = op.bc[k];
+  // pass 1: tmp_o = T_oo^-1 (-kappa H_oe in_e)
+  c.flags = clov ? F_E_CLOV : 0;
+  c.cls = K_DHAT1;
+  c.out_parity = 1;
+  c.beta = -op.kappa;
+  c.out = tmp.ptr(1);
+  c.out_rs = tmp.rs;
+  c.in = in.ptr(0);
+  c.in_rs = in.rs;
+  run_hop(L, c, st);
+  // pass 2: out_e = in_e - T_ee^-1 (-kappa H_eo tmp_o)
+  c.flags = F_SELF | (clov ? F_E_CLOV : 0);
+  c.cls = K_DHAT2;
+  c.out_parity = 0;
+  c.beta = op.kappa;
+  c.s1 = 1.0;
+  c.out = out.ptr(0);
+  c.out_rs = out.rs;
+  c.in = tmp.ptr(1);
+  c.in_rs = tmp.rs;
+  c.self = in.ptr(0);
+  c.self_rs = in.rs;
+  run_hop(L, c, st);
+}
+
+// ------------------------------------------------------------ layouts
+static CopyArgs copy_args(bridge_lattice_s* L, const Field& f, int parity) {
+  CopyArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.vh = (uint32_t)L->vh;
+  a.nrhs = f.nrhs;
+  a.parity = parity;
+  a.g = L->g;
+  a.V = L->V;
+  const int block = 256;
+  a.nblk = (int)((L->vh + block - 1) / block);
+  return a;
+}
+
+void canon_to_field(bridge_lattice_s* L, const double* canon, const Field& f, cudaStream_t st, const int* mask) {
+  const int lo = f.subset == BRIDGE_FULL ? 0 : f.subset, hi = f.subset == BRIDGE_FULL ? 1 : f.subset;
+  for (int p = lo; p <= hi; ++p) {
+    CopyArgs a = copy_args(L, f, p);
+    a.canon = canon;
+    a.canon_full = f.subset == BRIDGE_FULL;
+    a.dst = f.ptr(p);
+    a.dst_rs = f.rs;
+    a.mask = mask;
+    const double bytes = (double)L->vh * f.nrhs * (192 + spinor_site_bytes(f.prec));
+    note_launch(L, K_CONVERT, bytes, 0, st, true);
+    launch_canon_to_field(f.prec, a, 256, st);
+    note_launch(L, K_CONVERT, bytes, 0, st, false);
+  }
+  BR_CUDA(cudaGetLastError());
+}
+
+void field_to_canon(bridge_lattice_s* L, const Field& f, double* canon, cudaStream_t st) {
+  const int lo = f.subset == BRIDGE_FULL ? 0 : f.subset, hi = f.subset == BRIDGE_FULL ? 1 : f.subset;
+  for (int p = lo; p <= hi; ++p) {
+    CopyArgs a = copy_args(L, f, p);
+    a.canon_out = canon;
+    a.canon_full = f.subset == BRIDGE_FULL;
+    a.src = f.ptr(p);
+    a.src_rs = f.rs;
+    const double bytes = (double)L->vh * f.nrhs * (192 + spinor_site_bytes(f.prec));
+    note_launch(L, K_CONVERT, bytes, 0, st, true);
+    launch_field_to_canon(f.prec, a, 256, st);
+    note_launch(L, K_CONVERT, bytes, 0, st, false);
+  }
+  BR_CUDA(cudaGetLastError());
+}
+
+void convert_field(bridge_lattice_s* L, const Field& src, const Field& dst, int parity, cudaStream_t st, const int* mask) {
+  CopyArgs a = copy_args(L, src, parity);
+  a.src = src.ptr(parity);
+  a.src_rs = src.rs;
+  a.dst = dst.ptr(parity);
+  a.dst_rs = dst.rs;
+  a.mask = mask;
+  const double bytes = (double)L->vh * src.nrhs * (spinor_site_bytes(src.prec) + spinor_site_bytes(dst.prec));
+  note_launch(L, K_CONVERT, bytes, 0, st, true);
+  launch_convert(src.prec, dst.prec, a, 256, st);
+  note_launch(L, K_CONVERT, bytes, 0, st, false);
+  BR_CUDA(cudaGetLastError());
+}
+
+void accumulate64(bridge_lattice_s* L, const Field& src, int sp, const Field& dst, int dp, cudaStream_t st,
+                  const int* mask) {
+  CopyArgs a = copy_args(L, src, sp);
+  a.src = src.ptr(sp);
+  a.src_rs = src.rs;
+  a.dst = dst.ptr(dp);
+  a.dst_rs = dst.rs;
+  a.mask = mask;
+  const double bytes = (double)L->vh * src.nrhs * (spinor_site_bytes(src.prec) + 2 * 192);
+  note_launch(L, K_CONVERT, bytes, (double)L->vh * src.nrhs * 24, st, true);
+  launch_accumulate64(src.prec, a, 256, st);
+  note_launch(L, K_CONVERT, bytes, 0, st, false);
+  BR_CUDA(cudaGetLastError());
+}
+
+void norm2_field(bridge_lattice_s* L, const Field& f, int parity, RedArgs red, cudaStream_t st) {
+  CopyArgs a = copy_args(L, f, parity);
+  a.src = f.ptr(parity);
+  a.src_rs = f.rs;
+  a.red = red;
+  const double bytes = (double)L->vh * f.nrhs * spinor_site_bytes(f.prec);
+  note_launch(L, K_NORM, bytes, (double)L->vh * f.nrhs * 48, st, true);
+  launch_norm2(f.prec, a, 256, st);
+  note_launch(L, K_NORM, bytes, 0, st, false);
+  BR_CUDA(cudaGetLastError());
+}
+
+void clover_site(bridge_lattice_s* L, int prec, bool inverse, double kcsw, int parity, const Field& src, int sp,
+                 const Field& dst, int dp, int nrhs, cudaStream_t st) {
+  const char* cl = clover_ptr(L, prec, inverse, kcsw) + (long)parity * clover_block_bytes(prec, L->vh);
+  CopyArgs a = copy_args(L, src, sp);
+  a.nrhs = nrhs;
+  a.src = src.ptr(sp);
+  a.src_rs = src.rs;
+  a.dst = dst.ptr(dp);
+  a.dst_rs = dst.rs;
+  const double bytes = (double)L->vh * (nrhs * 2.0 * spinor_site_bytes(prec) + clover_site_bytes(prec));
+  note_launch(L, K_CLOVER, bytes, (double)L->vh * nrhs * 504, st, true);
+  launch_clover_site(prec, a, cl, 256, st);
+  note_launch(L, K_CLOVER, bytes, 0, st, false);
+  BR_CUDA(cudaGetLastError());
+}
+
+bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st) {
+  switch (prec) {
+    case P_F64: return launch_hop<P_F64>(flags, red, a, block, st);
+    case P_F32: return launch_hop<P_F32>(flags, red, a, block, st);
+    case P_F16: return launch_hop<P_F16>(flags, red, a, block, st);
+    case P_BF16: return launch_hop<P_BF16>(flags, red, a, block, st);
+  }
+  return false;
+}
+
+}  // namespace bridge

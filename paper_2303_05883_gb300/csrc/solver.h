@@ -1,0 +1,85 @@
+// Even-odd preconditioned BiCGStab inside an FP64 defect-correction loop,
+// written as a resumable state machine so that one code path serves both
+// the blocking bridge_solve and the request engine (which interleaves many
+// solves, each on its own stream).
+#pragma once
+
+#include <chrono>
+#include <vector>
+
+#include "host.h"
+
+namespace bridge {
+
+struct PinnedBuf {
+  void* ptr = nullptr;
+  explicit PinnedBuf(size_t n);
+  ~PinnedBuf();
+  PinnedBuf(const PinnedBuf&) = delete;
+  PinnedBuf& operator=(const PinnedBuf&) = delete;
+};
+
+// Device bytes a solve of nrhs right-hand sides will hold (used for admission).
+size_t solve_footprint(const bridge_lattice_s* L, const bridge_solver& prm, int nrhs);
+
+class SolveState {
+ public:
+  // b_dev / x_dev: canonical FP64 full-lattice fields on the device (nrhs of
+  // each).  x_dev holds the initial guess and receives the solution.
+  SolveState(bridge_lattice_s* L, const bridge_op& op, const bridge_solver& prm, int nrhs, cudaStream_t st,
+             const double* b_dev, double* x_dev);
+  ~SolveState();
+
+  // Queue whatever can be queued without blocking; true once finished.
+  bool advance();
+  // Event the caller may block on when advance() returned false.
+  cudaEvent_t wait_event() const { return pending_; }
+  const std::vector<bridge_info>& info() const { return info_; }
+  int status() const;
+
+ private:
+  enum State { ST_START, ST_BNORM, ST_RESID, ST_INNER, ST_FINISH, ST_DONE };
+
+  void enqueue_residual();
+  void begin_inner();
+  void enqueue_batch();
+  void enqueue_iteration();
+  void finish_inner();
+  void launch_blas(int op, int cls, double bytes_per_site, double flops_per_site, int fin);
+  void capture_batch();
+  RedArgs red(int fin, int slot = 0);
+
+  bridge_lattice_s* L_;
+  bridge_op op_;
+  bridge_solver prm_;
+  int nrhs_;
+  cudaStream_t st_;
+  const double* b_dev_;
+  double* x_dev_;
+  int P_, PX_;
+  bool clover_;
+  double kcsw_;
+
+  Field b64_, x64_, r64_, rin_, bh_, r_, rhat_, p_, v_, s_, t_, xin_, xinp_, tmp_, eo_;
+  std::unique_ptr<DevBuf> scal_, partials_, counter_, result_, mask_;
+  std::unique_ptr<PinnedBuf> h_sc_[2], h_result_, h_mask_, h_init_;
+  cudaEvent_t ev_[2] = {nullptr, nullptr};
+  cudaEvent_t ev_misc_ = nullptr;
+  cudaEvent_t pending_ = nullptr;
+
+  cudaGraphExec_t graph_ = nullptr;
+  KStat graph_delta_[K_NCLASS];
+  long graph_launches_ = 0;
+
+  State state_ = ST_START;
+  int outer_ = 0;
+  long batches_launched_ = 0, batches_checked_ = 0;
+  int batch_iters_ = 16;
+  long inner_total_ = 0;
+  std::vector<double> b2_, r2_;
+  std::vector<int> active_, failed_, stall_;
+  std::vector<bridge_info> info_;
+  std::chrono::steady_clock::time_point t0_;
+};
+
+}  // namespace bridge

@@ -1,0 +1,206 @@
+"""GPU solves against the FP64 oracle.
+
+Every solver configuration (plain FP64 BiCGStab; FP32, FP16 and BF16 inner
+solvers inside the FP64 defect-correction loop) must return x within 1e-10
+relative L2 of the oracle's solution of D x = b, with the oracle solved to a
+residual tight enough that its own error is far below that bar.  Edge cases:
+zero sources, an exact initial guess, iteration limits, 12 point sources,
+graph replay vs direct launches.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dirac, evenodd, solvers
+from oracle.lattice import Lattice
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_2303_05883_gb300 import api
+
+    return api
+
+
+def oracle_solve(U, lat, kappa, csw, b, bc=(1, 1, 1, -1), tol=1e-14):
+    eo = evenodd.EvenOdd(U, lat, kappa, csw, bc)
+    xe, info = solvers.bicgstab(eo.schur, eo.prepare(b), tol=tol)
+    x = eo.reconstruct(xe, b)
+    T = dirac.clover_term(U, lat, kappa, csw)
+    r = b - dirac.dirac(U, x, lat, kappa, csw, bc, T=T)
+    return x, float(np.linalg.norm(r) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def wilson8(api):
+    """8^4 Wilson, kappa 0.12, links exp(0.3 i A), Gaussian source (seed 1)."""
+    w = synth.WORKLOADS["wilson_8x8x8x8"]
+    lat = Lattice(w.dims)
+    U = w.gauge()
+    b = w.sources()[0]
+    x, res = oracle_solve(U, lat, w.kappa, 0.0, b)
+    assert res < 1e-13
+    L = api.Lattice(w.dims)
+    op = api.make_op("wilson", w.kappa)
+    L.upload(U, op)
+    yield dict(L=L, op=op, U=U, b=b, x=x, lat=lat, w=w)
+    L.close()
+
+
+@pytest.fixture(scope="module")
+def clover_odd(api):
+    """Non-cubic clover case with a ragged last thread block."""
+    dims, kappa, csw = (4, 6, 8, 10), 0.125, 1.0
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, 0.2, 7)
+    b = synth.gaussian_spinor(dims, 7)
+    x, res = oracle_solve(U, lat, kappa, csw, b)
+    assert res < 1e-13
+    L = api.Lattice(dims)
+    op = api.make_op("clover", kappa, csw)
+    L.upload(U, op)
+    yield dict(L=L, op=op, U=U, b=b, x=x, lat=lat, kappa=kappa, csw=csw)
+    L.close()
+
+
+@pytest.mark.parametrize(
+    "mode", [dict(mixed=0), dict(mixed=1, inner_prec="f32"), dict(mixed=1, inner_prec="f16"), dict(mixed=1, inner_prec="bf16")]
+)
+def test_wilson_8x8x8x8_solve(wilson8, api, mode):
+    s = api.make_solver(tol=1e-12, **mode)
+    x, info = wilson8["L"].solve(wilson8["op"], wilson8["b"], s)
+    assert info[0]["status"] == 0
+    assert info[0]["true_rel_residual"] <= 1e-12
+    assert rel(x, wilson8["x"]) < 1e-10
+
+
+@pytest.mark.parametrize(
+    "mode", [dict(mixed=0), dict(mixed=1, inner_prec="f32"), dict(mixed=1, inner_prec="f16"), dict(mixed=1, inner_prec="bf16")]
+)
+def test_clover_noncubic_solve(clover_odd, api, mode):
+    s = api.make_solver(tol=1e-12, **mode)
+    x, info = clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], s)
+    assert info[0]["status"] == 0 and info[0]["true_rel_residual"] <= 1e-12
+    assert rel(x, clover_odd["x"]) < 1e-10
+
+
+def test_dense_lu_2x2x2x2(api):
+    dims, kappa, csw = (2, 2, 2, 2), 0.12, 1.0
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, 0.5, 51)
+    b = synth.gaussian_spinor(dims, 51)
+    M = solvers.dense_dirac(U, lat, kappa, csw)
+    x_lu = solvers.lu_solve(M, b.reshape(-1)).reshape(b.shape)
+    L = api.Lattice(dims)
+    op = api.make_op("clover", kappa, csw)
+    L.upload(U, op)
+    for mode in (dict(mixed=0), dict(mixed=1, inner_prec="f32")):
+        x, info = L.solve(op, b, api.make_solver(tol=1e-13, **mode))
+        assert rel(x, x_lu) < 1e-11
+    L.close()
+
+
+def test_free_field_inverse_on_gpu(api):
+    from tests import pins
+
+    dims, kappa = (4, 4, 4, 8), 0.12
+    lat = Lattice(dims)
+    gen = np.random.default_rng(3)
+    u = gen.standard_normal((4, 3)) + 1j * gen.standard_normal((4, 3))
+    b, p = pins.plane_wave(lat, (1, 0, 2, 3), u)
+    want = np.einsum("st,ntc->nsc", np.linalg.inv(pins.free_field_symbol(p, kappa)), b)
+    L = api.Lattice(dims)
+    op = api.make_op("wilson", kappa)
+    L.upload(synth.unit_gauge(dims), op)
+    x, info = L.solve(op, b, api.make_solver(tol=1e-13))
+    assert rel(x, want) < 1e-11
+    L.close()
+
+
+def test_twelve_point_sources_f16(api):
+    """12 spin-colour point sources at the origin, FP16 inner solver, all at once."""
+    dims, kappa, csw = (4, 4, 4, 8), 0.125, 1.0
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, 0.2, 3)
+    B = synth.point_sources(dims)
+    eo = evenodd.EvenOdd(U, lat, kappa, csw)
+    L = api.Lattice(dims)
+    op = api.make_op("clover", kappa, csw)
+    L.upload(U, op)
+    X, info = L.solve(op, B, api.make_solver(tol=1e-12, inner_prec="f16"))
+    assert len(info) == 12
+    for k in range(12):
+        xe, _ = solvers.bicgstab(eo.schur, eo.prepare(B[k]), tol=1e-14)
+        xk = eo.reconstruct(xe, B[k])
+        assert info[k]["status"] == 0 and info[k]["true_rel_residual"] <= 1e-12
+        assert rel(X[k], xk) < 1e-10, k
+    L.close()
+
+
+def test_multi_rhs_equals_single_rhs(clover_odd, api):
+    """Right-hand sides solved together give the same answer as alone (within the bar)."""
+    b2 = np.stack([clover_odd["b"], synth.gaussian_spinor((4, 6, 8, 10), 8)])
+    s = api.make_solver(tol=1e-12)
+    X, info = clover_odd["L"].solve(clover_odd["op"], b2, s)
+    x0, _ = clover_odd["L"].solve(clover_odd["op"], b2[0], s)
+    assert rel(X[0], x0) < 1e-10 and rel(X[0], clover_odd["x"]) < 1e-10
+
+
+def test_zero_source_and_zero_column(clover_odd, api):
+    s = api.make_solver(tol=1e-12)
+    z = np.zeros_like(clover_odd["b"])
+    guess = synth.gaussian_spinor((4, 6, 8, 10), 9)
+    x, info = clover_odd["L"].solve(clover_odd["op"], z, s, x0=guess)
+    assert np.abs(x).max() == 0 and info[0]["status"] == 0
+    B = np.stack([z, clover_odd["b"]])
+    X, info = clover_odd["L"].solve(clover_odd["op"], B, s)
+    assert np.abs(X[0]).max() == 0 and rel(X[1], clover_odd["x"]) < 1e-10
+
+
+def test_exact_initial_guess_needs_no_iterations(clover_odd, api):
+    s = api.make_solver(tol=1e-10)
+    x, info = clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], s, x0=clover_odd["x"])
+    assert info[0]["inner_iters"] == 0 and info[0]["true_rel_residual"] <= 1e-10
+
+
+def test_iteration_limit_reports_enoconv(clover_odd, api):
+    from paper_2303_05883_gb300 import _abi
+
+    s = api.make_solver(tol=1e-12, max_iter=3, check_every=1)
+    x, info = clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], s, raise_on_fail=False)
+    assert info[0]["status"] == _abi.BRIDGE_ENOCONV
+    assert info[0]["true_rel_residual"] > 1e-12
+
+
+def test_graph_replay_is_bit_identical_to_direct_launches(clover_odd, api):
+    a, _ = clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], api.make_solver(tol=1e-11, use_graph=1))
+    b, _ = clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], api.make_solver(tol=1e-11, use_graph=0))
+    assert np.array_equal(a, b)
+
+
+def test_repeat_solve_is_bit_identical(clover_odd, api):
+    s = api.make_solver(tol=1e-11, inner_prec="f16")
+    a, _ = clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], s)
+    b, _ = clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], s)
+    assert np.array_equal(a, b)
+
+
+def test_profile_stats_report_event_times(clover_odd, api):
+    h = clover_odd["L"].handle
+    api.bridge_stats_reset(h)
+    api.bridge_profile(h, True)
+    clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], api.make_solver(tol=1e-10))
+    api.bridge_profile(h, False)
+    st = api.bridge_stats(h)
+    assert st["schur_pass2"]["launches"] > 0 and st["schur_pass2"]["ms"] > 0
+    assert st["residual64"]["launches"] >= 4
