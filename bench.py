@@ -1,0 +1,555 @@
+#!/usr/bin/env python
+"""Benchmark of the even-odd Wilson/clover solver path on one GB300.
+
+Workload (default): even-odd clover operator on a 32^3 x 64 lattice,
+c_sw = 1.0, kappa = 0.125, links exp(0.2 i A) (seed 2), one Gaussian source;
+FP32 inner BiCGStab inside FP64 defect correction, solved to a true FP64
+relative residual of 1e-10.
+
+A step is one complete solve (setup excluded: gauge field and clover term are
+resident).  value = algorithmic bytes moved by all kernels of the step (each
+input read once, each output written once, as counted per launch by the
+library) / step time -- the whole-job HBM throughput of the solve, to be read
+against the HBM peak.  Beside it the line reports:
+
+* roofline: the dominant kernel of the step, timed with CUDA events on the
+  library stream in an event-profiled extra step;
+* deo: the plain D_eo hopping kernel alone on resident FP32 fields;
+* solve: the mixed solve against a plain FP64 BiCGStab solve of the same system;
+* serving: p50/p99 latency of a short Poisson stream of requests through the
+  continuous-batching engine;
+* e2e: the same solve through bridge_solve with pinned host buffers
+  (host->device copies of b and x0 and the device->host copy of x timed);
+* cpu_baseline: the FP64 numpy oracle on a bounded sample of the workload.
+
+``--impl reference`` times only the oracle (the reference for this path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D_eo GB/s vs HBM peak; mixed vs FP64 solve time to 1e-10; p50/p99 solve latency"
+UNIT = "GB/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="clover_32x32x32x64")
+    ap.add_argument("--serving-requests", type=int, default=40)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--oracle-sites", type=int, default=16384, help="sites per oracle sample")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------- helpers
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of the SM clock and throttle reasons while running."""
+
+    FIELDS = (
+        "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+        "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+        "clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+            )
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        return {
+            "sm_mhz": statistics.median(r[0] for r in rows),
+            "sm_max_mhz": max(r[1] for r in rows),
+            "power_w_max": max(r[2] for r in rows),
+            "samples": len(rows),
+            "reasons": reasons,
+        }
+
+
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def kernel_source_hash() -> str:
+    d = hashlib.sha256()
+    for f in ("common.cuh", "dslash.cuh", "reduce.cuh"):
+        d.update(open(os.path.join(ROOT, "paper_2303_05883_gb300", "csrc", f), "rb").read())
+    return d.hexdigest()[:16]
+
+
+def cpu_cores_used(fn):
+    t0, c0 = time.perf_counter(), os.times()
+    r = fn()
+    t1, c1 = time.perf_counter(), os.times()
+    cpu = (c1.user - c0.user) + (c1.system - c0.system)
+    return r, t1 - t0, max(1, round(cpu / max(t1 - t0, 1e-9)))
+
+
+# oracle sample: the FP64 clover operator at randomly drawn sites of the workload
+FP64_D_BYTES_PER_SITE = 192 + 8 * 144 + 576 + 192  # spinor in, 8 links, T, spinor out
+
+
+def oracle_sample(w, U, b, nsites, seed):
+    from oracle import dirac
+    from oracle.lattice import Lattice
+
+    lat = Lattice(w.dims)
+    sites = np.sort(np.random.default_rng(seed).choice(lat.V, nsites, replace=False))
+    csw = w.csw if w.kind == "clover" else 0.0
+
+    def run():
+        return dirac.dirac(U, b, lat, w.kappa, csw, w.bc, sites=sites)
+
+    _, secs, cores = cpu_cores_used(run)
+    return nsites * FP64_D_BYTES_PER_SITE / secs / 1e9, secs, cores
+
+
+# ------------------------------------------------------------------- serving
+
+
+def serving_sample(api, n_requests, main_lattice, main_U, seed=5):
+    """Poisson stream through the request engine; returns latency stats."""
+    import synth
+
+    rng = np.random.default_rng(seed)
+    sizes = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48), (32, 32, 32, 64)]
+    pool = {}
+    for dims in sizes:
+        for eps in (0.1, 0.3):
+            if dims == main_lattice["dims"] and eps == 0.3:
+                continue
+            L = api.Lattice(dims)
+            L.upload(synth.gauge_field(dims, eps, seed + len(pool)))
+            pool[(dims, eps)] = L
+    pool[(main_lattice["dims"], 0.2)] = main_lattice["L"]
+    keys = list(pool)
+
+    def make(i):
+        dims, eps = keys[rng.integers(len(keys))]
+        kappa = float(rng.uniform(0.11, 0.13))
+        kind = "clover" if rng.integers(2) else "wilson"
+        nrhs = int(rng.integers(1, 13))
+        op = api.make_op(kind, kappa, 1.0 if kind == "clover" else 0.0)
+        b = synth.gaussian_spinor(dims, 1000 + i, nrhs=nrhs)
+        return pool[(dims, eps)], op, b
+
+    reqs = [make(i) for i in range(n_requests)]
+    # near-critical kappa on smooth fields can need tens of thousands of
+    # iterations; a per-request cap bounds latency and is reported
+    solver = api.make_solver(tol=1e-10, max_iter=4000)
+    # saturated throughput from a burst of the first requests
+    burst = reqs[: max(4, n_requests // 4)]
+    t0 = time.perf_counter()
+    hs = [api.bridge_submit(L.handle, op, solver, b) for L, op, b in burst]
+    for h in hs:
+        api.bridge_wait(h)
+        api.bridge_request_release(h)
+    sat = len(burst) / (time.perf_counter() - t0)
+    # Poisson arrivals at 0.9x the saturated rate
+    lam = 0.9 * sat
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_requests))
+    handles = []
+    start = time.perf_counter()
+    for (L, op, b), ta in zip(reqs, arrivals):
+        delay = start + ta - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        handles.append((api.bridge_submit(L.handle, op, solver, b), b.shape[0]))
+    lat_ms, lat_ok, ok, nrhs_total, statuses = [], [], 0, 0, {}
+    for h, nr in handles:
+        st, _, info = api.bridge_wait(h)
+        ts, _, td = api.bridge_request_times(h)
+        lat_ms.append((td - ts) * 1e3)
+        if st == 0:
+            lat_ok.append((td - ts) * 1e3)
+        ok += st == 0
+        statuses[api.bridge_strerror(st)] = statuses.get(api.bridge_strerror(st), 0) + 1
+        nrhs_total += nr
+        api.bridge_request_release(h)
+    wall = time.perf_counter() - start
+    for k, L in pool.items():
+        if L is not main_lattice["L"]:
+            L.close()
+    return {
+        "requests": n_requests,
+        "ok": ok,
+        "arrival_rate_per_s": lam,
+        "saturated_solves_per_s": sat,
+        "solves_per_s": n_requests / wall,
+        "statuses": statuses,
+        "max_iter_per_request": 4000,
+        "p50_ms": float(np.percentile(lat_ms, 50)),
+        "p99_ms": float(np.percentile(lat_ms, 99)),
+        "p50_ms_converged": float(np.percentile(lat_ok, 50)) if lat_ok else None,
+        "p99_ms_converged": float(np.percentile(lat_ok, 99)) if lat_ok else None,
+        "rhs_solved": nrhs_total,
+        "lattices": ["x".join(map(str, d)) for d in sizes],
+        "kappa": [0.11, 0.13],
+        "nrhs": [1, 12],
+    }
+
+
+# ----------------------------------------------------------------------- main
+
+
+def aggregate_ranks(ms: float, nbytes: float, device="cpu"):
+    """Whole-job view over ranks: the slowest rank's time and the sum of work."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, nbytes
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    b = torch.tensor([nbytes], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(b.item())
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores; rank 0 only."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import synth
+
+    w = synth.WORKLOADS[args.workload]
+    U = w.gauge()
+    b = w.sources()[0]
+    vals, secs_all, cores_all = [], [], []
+    for k in range(args.warmup + args.steps):
+        v, secs, cores = oracle_sample(w, U, b, args.oracle_sites, seed=k)
+        if k >= args.warmup:
+            vals.append(v)
+            secs_all.append(secs)
+            cores_all.append(cores)
+    value = float(np.mean(vals))
+    sample = f"FP64 numpy oracle: clover D at {args.oracle_sites} random sites of the {args.workload} lattice per step"
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(secs_all)),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "lattice": "x".join(map(str, w.dims)), "kappa": w.kappa, "csw": w.csw,
+                   "eps": w.eps, "sample_sites": args.oracle_sites},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": max(cores_all), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__ as g
+
+    if rank == 0:
+        g.build()
+    if world > 1:
+        dist.barrier()
+    import synth
+    from paper_2303_05883_gb300 import api
+
+    w = synth.WORKLOADS[args.workload]
+    U = w.gauge()
+    b_host = w.sources()[0]
+    kind = w.kind
+    op = api.make_op(kind, w.kappa, w.csw, w.bc)
+    L = api.Lattice(w.dims)
+    L.upload(U, op)
+    h = L.handle
+    solver = api.make_solver(tol=w.tol, inner_prec="f32", mixed=1)
+    stream = L.stream
+    b_dev = torch.from_numpy(b_host).to(f"cuda:{local}")
+    x_dev = torch.zeros_like(b_dev)
+
+    def solve_dev(prm):
+        x_dev.zero_()
+        torch.cuda.current_stream().synchronize()
+        from ctypes import byref, c_void_p
+
+        from paper_2303_05883_gb300 import _abi
+
+        info = (_abi.bridge_info * 1)()
+        st = _abi.load().bridge_solve_dev(h, byref(op), byref(prm), c_void_p(b_dev.data_ptr()),
+                                          c_void_p(x_dev.data_ptr()), 1, info)
+        _abi.check(st, "bridge_solve_dev")
+        return info[0]
+
+    api.bridge_tune(h, op, "f32", 1)
+    if not args.no_fp64:
+        api.bridge_tune(h, op, "f64", 1)
+    for _ in range(args.warmup):
+        solve_dev(solver)
+    torch.cuda.synchronize()
+    api.bridge_stats_reset(h)
+    l0 = api.bridge_launch_count()
+    infos = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(solve_dev(solver))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    ms = e0.elapsed_time(e1)
+    launches = api.bridge_launch_count() - l0
+    st = api.bridge_stats(h)
+    total_bytes = sum(v["bytes"] for v in st.values())
+    ms, total_bytes = aggregate_ranks(ms, total_bytes, device=f"cuda:{local}")
+    value = total_bytes / (ms * 1e-3) / 1e9
+    res = max(i.true_rel_residual for i in infos)
+    iters = statistics.median(i.inner_iters for i in infos)
+
+    # ---- one event-profiled step: per-kernel times for the roofline
+    api.bridge_stats_reset(h)
+    api.bridge_profile(h, True)
+    solve_dev(solver)
+    torch.cuda.synchronize()
+    api.bridge_profile(h, False)
+    pst = api.bridge_stats(h)
+    step_ms_prof = sum(v["ms"] for v in pst.values())
+    dom = max(pst, key=lambda k: pst[k]["ms"])
+    d = pst[dom]
+    peak, peak_kind = peaks()
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    roofline = {
+        "bound": "hbm",
+        "kernel": dom,
+        "achieved": achieved,
+        "peak": peak,
+        "peak_source": peak_kind,
+        "unit": "GB/s",
+        "frac": achieved / peak,
+        "traffic": traffic_for(dom, args.workload),
+        "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
+        "launches": d["launches"],
+        "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
+        "share_of_step": d["ms"] / step_ms_prof if step_ms_prof else None,
+    }
+    shares = {k: round(v["ms"] / step_ms_prof, 4) for k, v in pst.items() if v["ms"] > 0}
+
+    # ---- the plain D_eo hop kernel alone on resident FP32 fields
+    lat_half = b_host.reshape(-1, 4, 3)
+    fo = api.bridge_field_create(h, "f32", 1, 1)
+    fe = api.bridge_field_create(h, "f32", 0, 1)
+    from oracle.lattice import Lattice as _OL  # index order only: odd sites of the lattice
+
+    odd = _OL(w.dims).odd
+    api.bridge_field_import(fo, np.ascontiguousarray(lat_half[odd]))
+    api.bridge_sync(h)
+    for _ in range(3):
+        api.bridge_apply(h, op, 1, fe, fo)
+    reps = 50
+    api.bridge_stats_reset(h)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        api.bridge_apply(h, op, 1, fe, fo)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    deo_ms = a0.elapsed_time(a1) / reps
+    deo_bytes = api.bridge_stats(h)["hop_deo"]["bytes"] / reps
+    deo = {"kernel": "hop_deo", "prec": "f32", "gbs": deo_bytes / (deo_ms * 1e-3) / 1e9, "us_per_launch": deo_ms * 1e3,
+           "bytes_per_launch": deo_bytes, "frac": deo_bytes / (deo_ms * 1e-3) / 1e9 / peak,
+           "gflops": w.volume / 2 * 1344 / (deo_ms * 1e-3) / 1e9}
+    api.bridge_field_destroy(fo)
+    api.bridge_field_destroy(fe)
+
+    # ---- plain FP64 BiCGStab on the same system
+    solve = {"mixed_ms": ms / args.steps, "mixed_inner_iters": iters, "mixed_true_rel_residual": res}
+    if not args.no_fp64:
+        s64 = api.make_solver(tol=w.tol, mixed=0)
+        t0 = time.perf_counter()
+        i64 = solve_dev(s64)
+        t64 = time.perf_counter() - t0
+        solve.update({"fp64_ms": t64 * 1e3, "fp64_inner_iters": i64.inner_iters,
+                      "fp64_true_rel_residual": i64.true_rel_residual, "speedup": t64 * 1e3 / (ms / args.steps)})
+
+    # ---- end to end through bridge_solve with pinned host buffers
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    x_pin = torch.zeros_like(b_pin).pin_memory()
+    bn, xn = b_pin.numpy(), x_pin.numpy()
+    import ctypes
+
+    from paper_2303_05883_gb300 import _abi
+
+    lib = _abi.load()
+    info = (_abi.bridge_info * 1)()
+    dp = ctypes.POINTER(ctypes.c_double)
+    bp, xp = ctypes.cast(b_pin.data_ptr(), dp), ctypes.cast(x_pin.data_ptr(), dp)
+    e2e_t = []
+    for k in range(args.steps):
+        xn[...] = 0
+        t0 = time.perf_counter()
+        _abi.check(lib.bridge_solve(h, ctypes.byref(op), ctypes.byref(solver), bp, xp, 1, info), "bridge_solve")
+        e2e_t.append(time.perf_counter() - t0)
+    nbytes = b_host.nbytes
+    e2e = {"value": (total_bytes / args.steps) / statistics.median(e2e_t) / 1e9 if world == 1 else None,
+           "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes,
+           "ms_per_step": 1e3 * statistics.median(e2e_t)}
+
+    # ---- serving sample
+    serving = None
+    if args.serving_requests > 0 and rank == 0:
+        serving = serving_sample(api, args.serving_requests, {"dims": w.dims, "L": L}, U)
+
+    # ---- CPU oracle baseline (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1:
+        v, secs, cores = oracle_sample(w, U, b_host, 4 * args.oracle_sites, seed=0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"FP64 numpy oracle: clover D at {4 * args.oracle_sites} random sites of the "
+                         f"{args.workload} lattice ({secs:.1f} s)"}
+
+    if rank == 0:
+        working_set = (4 * w.volume * 48 + w.volume * 288 + 12 * w.volume / 2 * 96 + 3 * w.volume * 192) / 1e9
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {
+                "workload": args.workload,
+                "lattice": "x".join(map(str, w.dims)),
+                "operator": f"{kind}, kappa={w.kappa}, c_sw={w.csw}, bc={list(w.bc)}",
+                "links": f"exp({w.eps} i A), seed {w.seed}",
+                "source": "gaussian",
+                "solver": "even-odd BiCGStab, f32 inner, f64 defect correction",
+                "tol": w.tol,
+                "l2": f"inputs larger than L2 (solve working set ~{working_set:.1f} GB)",
+                "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            },
+            "roofline": roofline,
+            "kernel_shares": shares,
+            "deo": deo,
+            "solve": solve,
+            "serving": serving,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "inner_iters": iters,
+            "true_rel_residual": res,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    L.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -179,6 +179,18 @@ int bridge_solve_dev(bridge_lattice lat, const bridge_op* op, const bridge_solve
 /* Defaults: tol 1e-10, max_iter 20000, F32 inner, mixed, poll every 16, graphs on. */
 void bridge_solver_defaults(bridge_solver* s);
 
+/* Autotune (the GPU counterpart of the paper's site-tile study, Sec. 3 /
+ * Fig. 5): time the hop and vector kernels a solve with this operator,
+ * inner precision prec and nrhs right-hand sides will launch, over block
+ * sizes and grid shapes, on scratch buffers, and keep the fastest shape per
+ * kernel for this lattice.  With the environment variable BRIDGE_TUNE_CACHE
+ * naming a file, results are appended there and loaded by later
+ * bridge_lattice_create calls on the same device model.  Synchronous. */
+int bridge_tune(bridge_lattice lat, const bridge_op* op, int prec, int nrhs);
+/* The current shape table as text ("key block nblk" per line) in out[n];
+ * returns the full length. */
+int bridge_tune_table(bridge_lattice lat, char* out, int n);
+
 /* ---- fields in the GPU layout (resident data) ------------------------------- */
 
 /* A library-owned device field of nrhs spinors in the GPU site layout of

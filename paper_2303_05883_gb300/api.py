@@ -294,6 +294,20 @@ def bridge_debug_neighbours(dims, parity, ih):
     return list(out), list(wr)
 
 
+def bridge_tune(lat, op, prec="f32", nrhs=1) -> None:
+    check(_abi.load().bridge_tune(lat, byref(op), _prec(prec), int(nrhs)), "bridge_tune")
+
+
+def bridge_tune_table(lat) -> dict:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _abi.load().bridge_tune_table(lat, buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        k, b, n = line.split()
+        out[k] = (int(b), int(n))
+    return out
+
+
 def bridge_strerror(status: int) -> str:
     return _abi.load().bridge_strerror(int(status)).decode()
 

@@ -11,6 +11,7 @@ using namespace bridge;
 namespace bridge {
 const char* last_error_text();
 extern std::atomic<long> g_launches;
+void tune_cache_load(bridge_lattice_s* L);
 int engine_submit(bridge_lattice_s* L, const bridge_op& op, const bridge_solver& s, const double* b, int nrhs,
                   bridge_request_h* out);
 
@@ -190,6 +191,7 @@ int bridge_lattice_create(const int dims[4], bridge_lattice* out) {
     delete L;
     throw Error{BRIDGE_ECUDA, cudaGetErrorString(se)};
   }
+  tune_cache_load(L);
   *out = L;
   BR_API_END
 }
@@ -234,12 +236,13 @@ static int gauge_upload(bridge_lattice L, const double* U, const bridge_op* op, 
     BR_CUDA(cudaMemcpyAsync(d, U, n, cudaMemcpyHostToDevice, L->stream));
     src = reinterpret_cast<const double*>(d);
   }
-  for (int p = 0; p < 4; ++p) {
-    L->gauge[p].reset();
-    L->T[p].reset();
-    L->Tinv[p].reset();
+  BR_CHECK(L->in_flight.load() == 0, BRIDGE_ESTATE, "requests on this lattice are still running");
+  BR_CUDA(cudaStreamSynchronize(L->stream));
+  for (int p = 0; p < 4; ++p) L->gauge[p].reset();
+  {
+    std::lock_guard<std::mutex> lk(L->clover_mu);
+    L->clovers.clear();
   }
-  L->have_clover = false;
   L->gauge[P_F64].reset(new DevBuf((size_t)(8 * link_block_bytes(P_F64, L->vh))));
   note_launch(L, K_SETUP, (double)n * 2, 0, L->stream, true);
   launch_gauge_from_canon(src, L->g, L->gauge[P_F64]->ptr, L->stream);

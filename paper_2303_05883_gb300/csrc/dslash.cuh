@@ -236,16 +236,17 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
 }
 
 // Launch with the given block size on a stream; returns false for a
-// (flags, reduction) pair that is not instantiated.
+// (flags, reduction) pair that is not instantiated.  With occ != null,
+// nothing is launched: *occ receives the resident blocks per SM instead.
 template <int P>
-bool launch_hop(int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+bool launch_hop(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ = nullptr);
 template <>
-bool launch_hop<P_F64>(int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+bool launch_hop<P_F64>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ);
 template <>
-bool launch_hop<P_F32>(int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+bool launch_hop<P_F32>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ);
 template <>
-bool launch_hop<P_F16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+bool launch_hop<P_F16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ);
 template <>
-bool launch_hop<P_BF16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+bool launch_hop<P_BF16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ);
 
 }  // namespace bridge

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <atomic>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -102,6 +103,16 @@ struct Stats {
   std::vector<cudaEvent_t> pool;
 };
 
+// Clover term T = 1 - kcsw sum sigma F and its inverse for one value of
+// kcsw = kappa c_sw: FP64 masters plus lazily converted copies.  Shared by
+// the solves that use it, so a solve keeps its set alive even after the
+// lattice cache has dropped it.
+struct CloverSet {
+  double kcsw = 0.0;
+  std::unique_ptr<DevBuf> T[4], Tinv[4];
+  std::mutex mu;
+};
+
 }  // namespace bridge
 
 // ------------------------------------------------------------- lattice
@@ -114,10 +125,10 @@ struct bridge_lattice_s {
   // links per precision; [0] (F64, 18 reals) is the master copy
   std::unique_ptr<bridge::DevBuf> gauge[4];
   bool have_gauge = false;
-  // clover: T and T^-1 per precision, built for kcsw = kappa * c_sw
-  double kcsw = 0.0;
-  bool have_clover = false;
-  std::unique_ptr<bridge::DevBuf> T[4], Tinv[4];
+  // clover sets for the most recently used values of kappa * c_sw
+  std::vector<std::shared_ptr<bridge::CloverSet>> clovers;
+  std::mutex clover_mu;
+  std::atomic<int> in_flight{0};  // engine requests currently holding this lattice
   // reduction scratch for the operator entry points
   std::unique_ptr<bridge::DevBuf> red_partials, red_result;
   std::unique_ptr<bridge::DevBuf> red_counter;
@@ -125,6 +136,7 @@ struct bridge_lattice_s {
   // staging for canonical fields of the host-pointer entry points
   std::unique_ptr<bridge::DevBuf> stage_in, stage_out;
   std::map<std::string, bridge::LaunchShape> tuned;
+  std::mutex tune_mu;
   std::map<std::string, bridge::Field> ws;  // reusable fields of the operator entry points
   bridge::Stats stats;
   std::mutex api_mu;  // serialises host entry points on one lattice
@@ -134,11 +146,24 @@ namespace bridge {
 
 // launch bookkeeping (called at each launch site)
 void note_launch(bridge_lattice_s* L, int cls, double bytes, double flops, cudaStream_t st, bool begin);
-LaunchShape shape_for(bridge_lattice_s* L, const std::string& key, long vh, int nrhs);
+// Launch shape for a kernel key: the tuned entry if there is one, else
+// `block` threads and a persistent grid of (resident blocks per SM x SM
+// count) blocks, computed by occ(block), capped at one site per thread.
+LaunchShape shape_for(bridge_lattice_s* L, const std::string& key, long vh, int nrhs,
+                      const std::function<int(int)>& occ);
+
+// Algorithmic cost of one hop launch: bytes and flops per right-hand side
+// (spinors) and shared by all right-hand sides (links, clover blocks).
+struct HopCost {
+  double rhs_bytes, shared_bytes, rhs_flops;
+};
+HopCost hop_cost(int prec, int flags, int red);
 int sm_count();
 
 // gauge / clover on demand
 const char* gauge_ptr(bridge_lattice_s* L, int prec);
+std::shared_ptr<CloverSet> clover_set(bridge_lattice_s* L, double kcsw);
+const char* clover_ptr(bridge_lattice_s* L, CloverSet& set, int prec, bool inverse);
 const char* clover_ptr(bridge_lattice_s* L, int prec, bool inverse, double kcsw);
 
 // ------------------------------------------------------- operators
@@ -153,6 +178,8 @@ struct HopCall {
   const char *in = nullptr, *self = nullptr, *aux = nullptr, *avec = nullptr;
   long in_rs = 0, self_rs = 0, aux_rs = 0, avec_rs = 0;
   double kcsw = 0;
+  CloverSet* clov = nullptr;  // optional: use this set instead of the cache lookup
+  bool count_work = true;     // false: count the launch only (work is credited by the caller)
   RedArgs redargs{};
 };
 void run_hop(bridge_lattice_s* L, HopCall c, cudaStream_t st);
@@ -171,7 +198,7 @@ void accumulate64(bridge_lattice_s* L, const Field& src, int src_parity, const F
                   const int* mask);
 void norm2_field(bridge_lattice_s* L, const Field& f, int parity, RedArgs red, cudaStream_t st);
 void clover_site(bridge_lattice_s* L, int prec, bool inverse, double kcsw, int parity, const Field& src, int sp,
-                 const Field& dst, int dp, int nrhs, cudaStream_t st);
+                 const Field& dst, int dp, int nrhs, cudaStream_t st, CloverSet* set = nullptr);
 
 // Reusable field of this lattice (allocated on first use).
 Field& workspace(bridge_lattice_s* L, const std::string& name, int prec, int subset, int nrhs);

@@ -7,7 +7,7 @@
 namespace bridge {
 
 // ---------------------------------------------------------------- hop
-bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st);
+bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ = nullptr);
 
 // ----------------------------------------------------- BiCGStab vectors
 enum BlasOp { B_INIT = 0, B_S = 1, B_XR = 2, B_P = 3 };
@@ -26,7 +26,7 @@ struct BlasArgs {
 // B_S:    s = r - alpha v
 // B_XR:   x += alpha p + omega s, r = s - omega t, (<rhat, r>, |r|^2) -> FIN_RHO
 // B_P:    p = r + beta (p - omega v)
-bool launch_blas(int op, int prec, int px, const BlasArgs& a, int block, cudaStream_t st);
+bool launch_blas(int op, int prec, int px, const BlasArgs& a, int block, cudaStream_t st, int* occ = nullptr);
 
 // ------------------------------------------------------------ layout
 struct CopyArgs {

@@ -111,8 +111,18 @@ __global__ void __launch_bounds__(256) k_blas_p(const BlasArgs a) {
 }
 
 template <int P, int PX>
-static bool blas_dispatch(int op, const BlasArgs& a, int block, cudaStream_t st) {
+static bool blas_dispatch(int op, const BlasArgs& a, int block, cudaStream_t st, int* occ) {
   const dim3 grid((unsigned)(a.nblk * a.nrhs));
+  if (occ) {
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (op) {
+      case B_INIT: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_blas_init<P, PX>, block, 0); break;
+      case B_S: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_blas_s<P>, block, 0); break;
+      case B_XR: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_blas_xr<P, PX>, block, 0); break;
+      case B_P: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_blas_p<P>, block, 0); break;
+    }
+    return e == cudaSuccess;
+  }
   switch (op) {
     case B_INIT: k_blas_init<P, PX><<<grid, block, 0, st>>>(a); return true;
     case B_S: k_blas_s<P><<<grid, block, 0, st>>>(a); return true;
@@ -122,11 +132,11 @@ static bool blas_dispatch(int op, const BlasArgs& a, int block, cudaStream_t st)
   return false;
 }
 
-bool launch_blas(int op, int prec, int px, const BlasArgs& a, int block, cudaStream_t st) {
-  if (prec == P_F64 && px == P_F64) return blas_dispatch<P_F64, P_F64>(op, a, block, st);
-  if (prec == P_F32 && px == P_F32) return blas_dispatch<P_F32, P_F32>(op, a, block, st);
-  if (prec == P_F16 && px == P_F32) return blas_dispatch<P_F16, P_F32>(op, a, block, st);
-  if (prec == P_BF16 && px == P_F32) return blas_dispatch<P_BF16, P_F32>(op, a, block, st);
+bool launch_blas(int op, int prec, int px, const BlasArgs& a, int block, cudaStream_t st, int* occ) {
+  if (prec == P_F64 && px == P_F64) return blas_dispatch<P_F64, P_F64>(op, a, block, st, occ);
+  if (prec == P_F32 && px == P_F32) return blas_dispatch<P_F32, P_F32>(op, a, block, st, occ);
+  if (prec == P_F16 && px == P_F32) return blas_dispatch<P_F16, P_F32>(op, a, block, st, occ);
+  if (prec == P_BF16 && px == P_F32) return blas_dispatch<P_BF16, P_F32>(op, a, block, st, occ);
   return false;
 }
 

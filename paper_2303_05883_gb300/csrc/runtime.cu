@@ -1,5 +1,6 @@
 // Host runtime: device buffers, fields, gauge and clover storage, operator
 // application, launch statistics and launch shapes.
+#include <algorithm>
 #include <cstring>
 #include <string>
 
@@ -91,16 +92,21 @@ void note_launch(bridge_lattice_s* L, int cls, double bytes, double flops, cudaS
   }
 }
 
-// Launch shape: block size and the number of site blocks per right-hand
-// side.  The autotuner (tune.cu) fills L->tuned; the default covers the
-// half lattice once with 128-thread blocks.
-LaunchShape shape_for(bridge_lattice_s* L, const std::string& key, long vh, int nrhs) {
-  (void)nrhs;
-  auto it = L->tuned.find(key);
+LaunchShape shape_for(bridge_lattice_s* L, const std::string& key, long vh, int nrhs,
+                      const std::function<int(int)>& occ) {
+  std::lock_guard<std::mutex> lk(L->tune_mu);
   LaunchShape s;
-  if (it != L->tuned.end()) s = it->second;
-  else s.block = 128;
-  long cover = (vh + s.block - 1) / s.block;
+  auto it = L->tuned.find(key);
+  if (it != L->tuned.end()) {
+    s = it->second;
+  } else {
+    s.block = 128;
+    const int per_sm = occ ? occ(s.block) : 0;
+    const long resident = (long)sm_count() * (per_sm > 0 ? per_sm : 4);
+    s.nblk = (int)std::max<long>(1, resident / std::max(1, nrhs));
+    L->tuned[key] = s;
+  }
+  const long cover = (vh + s.block - 1) / s.block;
   if (s.nblk <= 0 || s.nblk > cover) s.nblk = (int)cover;
   return s;
 }
@@ -133,26 +139,35 @@ const char* gauge_ptr(bridge_lattice_s* L, int prec) {
   return L->gauge[prec]->ptr;
 }
 
-const char* clover_ptr(bridge_lattice_s* L, int prec, bool inverse, double kcsw) {
+std::shared_ptr<CloverSet> clover_set(bridge_lattice_s* L, double kcsw) {
   BR_CHECK(L->have_gauge, BRIDGE_ESTATE, "no gauge field uploaded");
-  if (!L->have_clover || L->kcsw != kcsw) {
-    for (int p = 0; p < 4; ++p) {
-      if (p != P_F64) {
-        L->T[p].reset();
-        L->Tinv[p].reset();
-      }
+  std::lock_guard<std::mutex> lk(L->clover_mu);
+  for (size_t i = 0; i < L->clovers.size(); ++i) {
+    if (L->clovers[i]->kcsw == kcsw) {
+      auto s = L->clovers[i];
+      L->clovers.erase(L->clovers.begin() + i);
+      L->clovers.insert(L->clovers.begin(), s);
+      return s;
     }
-    size_t n = (size_t)(2 * clover_block_bytes(P_F64, L->vh));
-    if (!L->T[P_F64]) L->T[P_F64].reset(new DevBuf(n));
-    if (!L->Tinv[P_F64]) L->Tinv[P_F64].reset(new DevBuf(n));
-    note_launch(L, K_SETUP, 0, 0, L->stream, true);
-    launch_clover_build(L->g, L->gauge[P_F64]->ptr, kcsw, L->T[P_F64]->ptr, L->Tinv[P_F64]->ptr, L->stream);
-    note_launch(L, K_SETUP, 0, 0, L->stream, false);
-    BR_CUDA(cudaGetLastError());
-    L->kcsw = kcsw;
-    L->have_clover = true;
   }
-  std::unique_ptr<DevBuf>* arr = inverse ? L->Tinv : L->T;
+  auto s = std::make_shared<CloverSet>();
+  s->kcsw = kcsw;
+  const size_t n = (size_t)(2 * clover_block_bytes(P_F64, L->vh));
+  s->T[P_F64].reset(new DevBuf(n));
+  s->Tinv[P_F64].reset(new DevBuf(n));
+  note_launch(L, K_SETUP, 0, 0, L->stream, true);
+  launch_clover_build(L->g, L->gauge[P_F64]->ptr, kcsw, s->T[P_F64]->ptr, s->Tinv[P_F64]->ptr, L->stream);
+  note_launch(L, K_SETUP, 0, 0, L->stream, false);
+  BR_CUDA(cudaGetLastError());
+  L->clovers.insert(L->clovers.begin(), s);
+  const size_t keep = 4;  // sets still used by a solve stay alive through its reference
+  if (L->clovers.size() > keep) L->clovers.resize(keep);
+  return s;
+}
+
+const char* clover_ptr(bridge_lattice_s* L, CloverSet& set, int prec, bool inverse) {
+  std::lock_guard<std::mutex> lk(set.mu);
+  std::unique_ptr<DevBuf>* arr = inverse ? set.Tinv : set.T;
   if (!arr[prec]) {
     arr[prec].reset(new DevBuf((size_t)(2 * clover_block_bytes(prec, L->vh))));
     note_launch(L, K_SETUP, 0, 0, L->stream, true);
@@ -164,10 +179,33 @@ const char* clover_ptr(bridge_lattice_s* L, int prec, bool inverse, double kcsw)
   return arr[prec]->ptr;
 }
 
+const char* clover_ptr(bridge_lattice_s* L, int prec, bool inverse, double kcsw) {
+  auto s = clover_set(L, kcsw);
+  return clover_ptr(L, *s, prec, inverse);
+}
+
 // ------------------------------------------------------------ operators
 static long spinor_site_bytes(int prec) { return prec == P_F64 ? 192 : prec == P_F32 ? 96 : 52; }
 static long link_site_bytes(int prec) { return prec == P_F64 ? 144 : prec == P_F32 ? 48 : 24; }
 static long clover_site_bytes(int prec) { return prec == P_F64 ? 576 : prec == P_F32 ? 288 : 144; }
+
+HopCost hop_cost(int prec, int flags, int red) {
+  const double S = (double)spinor_site_bytes(prec);
+  double per_rhs = 2 * S;  // one input read, one output written
+  if (flags & F_SELF) per_rhs += S;
+  if (flags & F_AUX) per_rhs += S;
+  if (red == R_DOT_A) per_rhs += S;
+  double shared = 8.0 * link_site_bytes(prec);
+  if (flags & F_E_CLOV) shared += clover_site_bytes(prec);
+  if (flags & F_SELF_CLOV) shared += clover_site_bytes(prec);
+  double fl = 1320 + 24;  // hop (8 projected hops) and the scale by beta
+  if (flags & F_E_CLOV) fl += 504;
+  if (flags & F_SELF_CLOV) fl += 504;
+  if (flags & F_SELF) fl += 48;
+  if (flags & F_AUX) fl += 48;
+  if (red != R_NONE) fl += 48;
+  return HopCost{per_rhs, shared, fl};
+}
 
 static std::string dims_key(const bridge_lattice_s* L) {
   return std::to_string(L->dims[0]) + "x" + std::to_string(L->dims[1]) + "x" + std::to_string(L->dims[2]) + "x" +
@@ -195,11 +233,23 @@ void run_hop(bridge_lattice_s* L, HopCall c, cudaStream_t st) {
   a.avec = c.avec;
   a.avec_rs = c.avec_rs;
   a.gauge = gauge_ptr(L, c.prec);
-  a.clovE = (c.flags & F_E_CLOV) ? clover_ptr(L, c.prec, true, c.kcsw) : nullptr;
-  a.clovM = (c.flags & F_SELF_CLOV) ? clover_ptr(L, c.prec, false, c.kcsw) : nullptr;
+  if (c.flags & (F_E_CLOV | F_SELF_CLOV)) {
+    std::shared_ptr<CloverSet> keep;
+    CloverSet* cs = c.clov;
+    if (!cs) {
+      keep = clover_set(L, c.kcsw);
+      cs = keep.get();
+    }
+    a.clovE = (c.flags & F_E_CLOV) ? clover_ptr(L, *cs, c.prec, true) : nullptr;
+    a.clovM = (c.flags & F_SELF_CLOV) ? clover_ptr(L, *cs, c.prec, false) : nullptr;
+  }
   const std::string key = "hop/" + std::to_string(c.prec) + "/" + std::to_string(c.flags) + "/" +
                           std::to_string(c.red) + "/" + dims_key(L) + "/" + std::to_string(c.nrhs);
-  LaunchShape sh = shape_for(L, key, L->vh, c.nrhs);
+  LaunchShape sh = shape_for(L, key, L->vh, c.nrhs, [&](int block) {
+    int n = 0;
+    launch_hop_any(c.prec, c.flags, c.red, a, block, st, &n);
+    return n;
+  });
   a.nblk = sh.nblk;
   a.red = c.redargs;
   if (c.red != R_NONE && a.red.partials == nullptr) {
@@ -209,22 +259,9 @@ void run_hop(bridge_lattice_s* L, HopCall c, cudaStream_t st) {
     a.red.result = reinterpret_cast<double*>(L->red_result->ptr);
     if (a.red.fin == FIN_NONE) a.red.fin = FIN_STORE;
   }
-  const long S = spinor_site_bytes(c.prec);
-  long per_rhs = 2 * S;  // one input read, one output written
-  if (c.flags & F_SELF) per_rhs += S;
-  if (c.flags & F_AUX) per_rhs += S;
-  if (c.red == R_DOT_A) per_rhs += S;
-  long shared = 8 * link_site_bytes(c.prec);
-  if (c.flags & F_E_CLOV) shared += clover_site_bytes(c.prec);
-  if (c.flags & F_SELF_CLOV) shared += clover_site_bytes(c.prec);
-  const double bytes = (double)L->vh * ((double)per_rhs * c.nrhs + (double)shared);
-  double fl = 1320 + 24;
-  if (c.flags & F_E_CLOV) fl += 504;
-  if (c.flags & F_SELF_CLOV) fl += 504;
-  if (c.flags & F_SELF) fl += 48;
-  if (c.flags & F_AUX) fl += 48;
-  if (c.red != R_NONE) fl += 48;
-  const double flops = (double)L->vh * c.nrhs * fl;
+  const HopCost hc = hop_cost(c.prec, c.flags, c.red);
+  const double bytes = c.count_work ? (double)L->vh * (hc.rhs_bytes * c.nrhs + hc.shared_bytes) : 0.0;
+  const double flops = c.count_work ? (double)L->vh * c.nrhs * hc.rhs_flops : 0.0;
   note_launch(L, c.cls, bytes, flops, st, true);
   BR_CHECK(launch_hop_any(c.prec, c.flags, c.red, a, sh.block, st), BRIDGE_EINVAL, "hop variant not instantiated");
   note_launch(L, c.cls, bytes, flops, st, false);
@@ -384,6 +421,7 @@ void norm2_field(bridge_lattice_s* L, const Field& f, int parity, RedArgs red, c
   a.src = f.ptr(parity);
   a.src_rs = f.rs;
   a.red = red;
+  a.nblk = std::max(1, std::min(a.nblk, sm_count() * 8 / std::max(1, f.nrhs)));
   const double bytes = (double)L->vh * f.nrhs * spinor_site_bytes(f.prec);
   note_launch(L, K_NORM, bytes, (double)L->vh * f.nrhs * 48, st, true);
   launch_norm2(f.prec, a, 256, st);
@@ -392,8 +430,9 @@ void norm2_field(bridge_lattice_s* L, const Field& f, int parity, RedArgs red, c
 }
 
 void clover_site(bridge_lattice_s* L, int prec, bool inverse, double kcsw, int parity, const Field& src, int sp,
-                 const Field& dst, int dp, int nrhs, cudaStream_t st) {
-  const char* cl = clover_ptr(L, prec, inverse, kcsw) + (long)parity * clover_block_bytes(prec, L->vh);
+                 const Field& dst, int dp, int nrhs, cudaStream_t st, CloverSet* set) {
+  const char* cl = (set ? clover_ptr(L, *set, prec, inverse) : clover_ptr(L, prec, inverse, kcsw)) +
+                   (long)parity * clover_block_bytes(prec, L->vh);
   CopyArgs a = copy_args(L, src, sp);
   a.nrhs = nrhs;
   a.src = src.ptr(sp);
@@ -407,12 +446,12 @@ void clover_site(bridge_lattice_s* L, int prec, bool inverse, double kcsw, int p
   BR_CUDA(cudaGetLastError());
 }
 
-bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st) {
+bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ) {
   switch (prec) {
-    case P_F64: return launch_hop<P_F64>(flags, red, a, block, st);
-    case P_F32: return launch_hop<P_F32>(flags, red, a, block, st);
-    case P_F16: return launch_hop<P_F16>(flags, red, a, block, st);
-    case P_BF16: return launch_hop<P_BF16>(flags, red, a, block, st);
+    case P_F64: return launch_hop<P_F64>(flags, red, a, block, st, occ);
+    case P_F32: return launch_hop<P_F32>(flags, red, a, block, st, occ);
+    case P_F16: return launch_hop<P_F16>(flags, red, a, block, st, occ);
+    case P_BF16: return launch_hop<P_BF16>(flags, red, a, block, st, occ);
   }
   return false;
 }

@@ -85,6 +85,7 @@ struct Engine {
       r->st = nullptr;
     }
     used -= r->bytes;
+    r->L->in_flight.fetch_sub(1);
     r->status = status;
     r->error = err;
     r->state = RQ_DONE;
@@ -127,6 +128,7 @@ struct Engine {
           bridge_request_s* r = queue.front();
           queue.pop_front();
           r->state = RQ_ACTIVE;
+          r->L->in_flight.fetch_add(1);
           used += r->bytes;
           active.push_back(r);
           starting.push_back(r);

@@ -69,6 +69,11 @@ SolveState::SolveState(bridge_lattice_s* L, const bridge_op& op, const bridge_so
   if (prm_.max_iter <= 0) prm_.max_iter = 20000;
   if (prm_.inner_tol <= 0) prm_.inner_tol = prm_.mixed ? (P_ == P_F32 ? 1e-5 : 2e-3) : std::max(prm_.tol * 0.25, 1e-15);
   batch_iters_ = prm_.check_every;
+  if (L_->stats.profiling) {
+    // event-timed runs launch exactly the iterations that execute
+    batch_iters_ = 1;
+    inflight_ = 1;
+  }
   const long vh = L_->vh;
   b64_ = make_field(P_F64, BRIDGE_FULL, nrhs, vh);
   x64_ = make_field(P_F64, BRIDGE_FULL, nrhs, vh);
@@ -109,8 +114,9 @@ SolveState::SolveState(bridge_lattice_s* L, const bridge_op& op, const bridge_so
   gauge_ptr(L_, P_);
   gauge_ptr(L_, P_F64);
   if (clover_) {
-    clover_ptr(L_, P_, true, kcsw_);
-    clover_ptr(L_, P_F64, false, kcsw_);
+    clov_ = clover_set(L_, kcsw_);
+    clover_ptr(L_, *clov_, P_, true);
+    clover_ptr(L_, *clov_, P_F64, false);
   }
   if (st_ != L_->stream) BR_CUDA(cudaStreamSynchronize(L_->stream));
 }
@@ -154,6 +160,7 @@ void SolveState::enqueue_residual() {
     c.s1 = -1.0;
     c.caux = 1.0;
     c.kcsw = kcsw_;
+    c.clov = clov_.get();
     for (int k = 0; k < 4; ++k) c.bc[k] = op_.bc[k];
     c.out = r64_.ptr(q);
     c.out_rs = r64_.rs;
@@ -171,7 +178,7 @@ void SolveState::enqueue_residual() {
   pending_ = ev_misc_;
 }
 
-void SolveState::launch_blas(int op, int cls, double bytes_per_site, double flops_per_site, int fin) {
+void SolveState::launch_blas(int op, int cls, double bytes_per_site, double flops_per_site, int fin, bool count_work) {
   BlasArgs a;
   std::memset(&a, 0, sizeof(a));
   a.vh = (uint32_t)L_->vh;
@@ -195,9 +202,13 @@ void SolveState::launch_blas(int op, int cls, double bytes_per_site, double flop
   a.red = red(fin);
   const std::string key = "blas/" + std::to_string(op) + "/" + std::to_string(P_) + "/" + std::to_string(L_->vh) + "/" +
                           std::to_string(nrhs_);
-  LaunchShape sh = shape_for(L_, key, L_->vh, nrhs_);
+  LaunchShape sh = shape_for(L_, key, L_->vh, nrhs_, [&](int block) {
+    int n = 0;
+    bridge::launch_blas(op, P_, PX_, a, block, st_, &n);
+    return n;
+  });
   a.nblk = sh.nblk;
-  const double n = (double)L_->vh * nrhs_;
+  const double n = count_work ? (double)L_->vh * nrhs_ : 0.0;
   note_launch(L_, cls, n * bytes_per_site, n * flops_per_site, st_, true);
   BR_CHECK(bridge::launch_blas(op, P_, PX_, a, sh.block, st_), BRIDGE_EINVAL, "blas variant");
   note_launch(L_, cls, 0, 0, st_, false);
@@ -217,6 +228,7 @@ void SolveState::begin_inner() {
   c.prec = P_;
   c.nrhs = nrhs_;
   c.kcsw = kcsw_;
+  c.clov = clov_.get();
   for (int k = 0; k < 4; ++k) c.bc[k] = op_.bc[k];
   c.cls = K_PREP;
   c.out_parity = 0;
@@ -227,7 +239,7 @@ void SolveState::begin_inner() {
   c.aux = rin_.ptr(0);
   c.aux_rs = rin_.rs;
   if (clover_) {
-    clover_site(L_, P_, true, kcsw_, 1, rin_, 1, tmp_, 1, nrhs_, st_);
+    clover_site(L_, P_, true, kcsw_, 1, rin_, 1, tmp_, 1, nrhs_, st_, clov_.get());
     c.flags = F_AUX | F_E_CLOV;
     c.in = tmp_.ptr(1);
     c.in_rs = tmp_.rs;
@@ -249,8 +261,7 @@ void SolveState::begin_inner() {
   const double S = P_ == P_F64 ? 192 : P_ == P_F32 ? 96 : 52, SX = PX_ == P_F64 ? 192 : PX_ == P_F32 ? 96 : 52;
   launch_blas(B_INIT, K_BLAS_INIT, 4 * S + SX, 24, FIN_INIT);
   batches_launched_ = batches_checked_ = 0;
-  enqueue_batch();
-  enqueue_batch();
+  for (int k = 0; k < inflight_; ++k) enqueue_batch();
 }
 
 void SolveState::enqueue_iteration() {
@@ -259,6 +270,7 @@ void SolveState::enqueue_iteration() {
   c.prec = P_;
   c.nrhs = nrhs_;
   c.kcsw = kcsw_;
+  c.clov = clov_.get();
   for (int k = 0; k < 4; ++k) c.bc[k] = op_.bc[k];
   // pass 1 of D^: tmp_o = T_oo^-1 (-kappa H_oe in_e)
   HopCall p1 = c;
@@ -270,8 +282,10 @@ void SolveState::enqueue_iteration() {
   p1.out_rs = tmp_.rs;
   p1.redargs = red(FIN_NONE);
   p1.redargs.partials = nullptr;  // no reduction, but skip finished right-hand sides
+  p1.count_work = false;          // executed iterations are credited in finish_inner
   // pass 2 of D^: out_e = in_e + kappa T_ee^-1 H_eo tmp_o
   HopCall p2 = c;
+  p2.count_work = false;
   p2.flags = F_SELF | (clover_ ? F_E_CLOV : 0);
   p2.cls = K_DHAT2;
   p2.out_parity = 0;
@@ -293,7 +307,7 @@ void SolveState::enqueue_iteration() {
   p2.redargs = red(FIN_ALPHA);
   run_hop(L_, p2, st_);
   // s = r - alpha v
-  launch_blas(B_S, K_BLAS_S, 3 * S, 48, FIN_NONE);
+  launch_blas(B_S, K_BLAS_S, 3 * S, 48, FIN_NONE, false);
   // t = D^ s, omega = <t, s> / <t, t>
   p1.in = s_.ptr(0);
   p1.in_rs = s_.rs;
@@ -307,9 +321,9 @@ void SolveState::enqueue_iteration() {
   p2.redargs = red(FIN_OMEGA);
   run_hop(L_, p2, st_);
   // x += alpha p + omega s, r = s - omega t, beta, convergence
-  launch_blas(B_XR, K_BLAS_XR, 5 * S + 2 * SX, 192, FIN_RHO);
+  launch_blas(B_XR, K_BLAS_XR, 5 * S + 2 * SX, 192, FIN_RHO, false);
   // p = r + beta (p - omega v)
-  launch_blas(B_P, K_BLAS_P, 4 * S, 96, FIN_NONE);
+  launch_blas(B_P, K_BLAS_P, 4 * S, 96, FIN_NONE, false);
 }
 
 void SolveState::capture_batch() {
@@ -367,17 +381,45 @@ void SolveState::enqueue_batch() {
   ++batches_launched_;
 }
 
+// Algorithmic work of the iterations that ran (launched iterations past
+// convergence exit at once and move no data, so they are not counted).
+void SolveState::credit_iterations(const std::vector<long>& iters) {
+  long most = 0, sum = 0;
+  for (long n : iters) {
+    most = std::max(most, n);
+    sum += n;
+  }
+  if (most == 0) return;
+  const double vh = (double)L_->vh;
+  const double S = P_ == P_F64 ? 192 : P_ == P_F32 ? 96 : 52, SX = PX_ == P_F64 ? 192 : PX_ == P_F32 ? 96 : 52;
+  const int f1 = clover_ ? F_E_CLOV : 0, f2 = F_SELF | (clover_ ? F_E_CLOV : 0);
+  const HopCost h1 = hop_cost(P_, f1, R_NONE), ha = hop_cost(P_, f2, R_DOT_A), ht = hop_cost(P_, f2, R_TS);
+  std::lock_guard<std::mutex> lk(L_->stats.mu);
+  auto add = [&](int cls, double rhs_bytes, double shared_bytes, double rhs_flops) {
+    L_->stats.k[cls].bytes += vh * (rhs_bytes * sum + shared_bytes * most);
+    L_->stats.k[cls].flops += vh * rhs_flops * sum;
+  };
+  add(K_DHAT1, 2 * h1.rhs_bytes, 2 * h1.shared_bytes, 2 * h1.rhs_flops);
+  add(K_DHAT2, ha.rhs_bytes + ht.rhs_bytes, ha.shared_bytes + ht.shared_bytes, ha.rhs_flops + ht.rhs_flops);
+  add(K_BLAS_S, 3 * S, 0, 48);
+  add(K_BLAS_XR, 5 * S + 2 * SX, 0, 192);
+  add(K_BLAS_P, 4 * S, 0, 96);
+}
+
 void SolveState::finish_inner() {
   const BiCGScalars* sc = reinterpret_cast<const BiCGScalars*>(h_sc_[(batches_checked_ - 1) & 1]->ptr);
   long most = 0;
+  std::vector<long> iters(nrhs_, 0);
   for (int r = 0; r < nrhs_; ++r) {
     if (!active_[r]) continue;
     info_[r].inner_iters += sc[r].iter;
+    iters[r] = sc[r].iter;
     most = std::max<long>(most, sc[r].iter);
     if (sc[r].done == BREAKDOWN) info_[r].restarts += 1;
     stall_[r] = (sc[r].iter == 0) ? stall_[r] + 1 : 0;
   }
   inner_total_ += most;
+  credit_iterations(iters);
   const int* mask = reinterpret_cast<const int*>(mask_->ptr);
   // e_o = T_oo^-1 (r_o + kappa H_oe e_e)
   const Field* xe = &xin_;
@@ -389,6 +431,7 @@ void SolveState::finish_inner() {
   c.prec = P_;
   c.nrhs = nrhs_;
   c.kcsw = kcsw_;
+  c.clov = clov_.get();
   for (int k = 0; k < 4; ++k) c.bc[k] = op_.bc[k];
   c.cls = K_PREP;
   c.flags = F_AUX | (clover_ ? F_E_CLOV : 0);

@@ -45,7 +45,8 @@ class SolveState {
   void enqueue_batch();
   void enqueue_iteration();
   void finish_inner();
-  void launch_blas(int op, int cls, double bytes_per_site, double flops_per_site, int fin);
+  void launch_blas(int op, int cls, double bytes_per_site, double flops_per_site, int fin, bool count_work = true);
+  void credit_iterations(const std::vector<long>& iters);
   void capture_batch();
   RedArgs red(int fin, int slot = 0);
 
@@ -59,6 +60,7 @@ class SolveState {
   int P_, PX_;
   bool clover_;
   double kcsw_;
+  std::shared_ptr<CloverSet> clov_;
 
   Field b64_, x64_, r64_, rin_, bh_, r_, rhat_, p_, v_, s_, t_, xin_, xinp_, tmp_, eo_;
   std::unique_ptr<DevBuf> scal_, partials_, counter_, result_, mask_;
@@ -75,6 +77,7 @@ class SolveState {
   int outer_ = 0;
   long batches_launched_ = 0, batches_checked_ = 0;
   int batch_iters_ = 16;
+  int inflight_ = 2;  // batches kept queued ahead of the host check
   long inner_total_ = 0;
   std::vector<double> b2_, r2_;
   std::vector<int> active_, failed_, stall_;

@@ -24,6 +24,7 @@ field and the sources of one configuration are independent and reproducible.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -81,51 +82,90 @@ def rng(seed: int, field_id: int) -> np.random.Generator:
 
 
 def lie_gaussian(gen: np.random.Generator, n: int) -> np.ndarray:
-    """n traceless Hermitian matrices A = sum_a w_a l_a / 2 with w_a ~ N(0, 1)."""
+    """n traceless Hermitian matrices A = sum_a w_a l_a / 2 with w_a ~ N(0, 1), shape (n, 3, 3)."""
     w = gen.standard_normal((n, 8))
     return np.einsum("na,aij->nij", w, GELL_MANN) * 0.5
 
 
-def expi_hermitian(A: np.ndarray, eps: float) -> np.ndarray:
-    """exp(i*eps*A) for a batch of Hermitian A by scaling and squaring.
+def _mm(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Products of 3x3 matrices stored component-major, shape (3, 3, n)."""
+    return np.einsum("ikn,kjn->ijn", A, B)
 
-    The scaled argument has Frobenius norm <= 1/2, where the degree-16
-    Taylor polynomial is exact to below 1e-19; the result is squared back.
+
+def _expi_soa(A: np.ndarray, eps: float) -> np.ndarray:
+    """exp(i*eps*A) for Hermitian A in component-major form (3, 3, n).
+
+    Scaling and squaring: the argument is scaled to Frobenius norm <= 1/8,
+    where the degree-12 Taylor polynomial (Horner form) is exact to far below
+    1e-18, then squared back.
     """
     X = 1j * float(eps) * A
-    nrm = float(np.max(np.sqrt(np.sum(np.abs(X) ** 2, axis=(-2, -1))))) if len(X) else 0.0
-    s = max(0, int(math.ceil(math.log2(nrm / 0.5)))) if nrm > 0.5 else 0
+    n = X.shape[-1]
+    if n == 0:
+        return X
+    nrm = float(np.sqrt(np.max(np.sum(np.abs(X) ** 2, axis=(0, 1)))))
+    s = max(0, int(math.ceil(math.log2(nrm / 0.125)))) if nrm > 0.125 else 0
     X = X / (2.0**s)
-    eye = np.broadcast_to(np.eye(3, dtype=np.complex128), X.shape)
+    eye = np.zeros_like(X)
+    for k in range(3):
+        eye[k, k] = 1.0
     E = eye.copy()
-    for k in range(16, 0, -1):  # Horner: I + X/1 (I + X/2 (I + ...))
-        E = eye + (X @ E) / k
+    for k in range(12, 0, -1):  # I + X/1 (I + X/2 (I + ...))
+        E = eye + _mm(X, E) / k
     for _ in range(s):
-        E = E @ E
+        E = _mm(E, E)
     return E
 
 
+def _reunitarize_soa(U: np.ndarray) -> np.ndarray:
+    """Project (3, 3, n) matrices onto SU(3): Gram-Schmidt rows 1, 2; row 3 = conj(r1 x r2)."""
+    r1 = U[0] / np.sqrt(np.sum(np.abs(U[0]) ** 2, axis=0))
+    r2 = U[1] - np.sum(r1.conj() * U[1], axis=0) * r1
+    r2 = r2 / np.sqrt(np.sum(np.abs(r2) ** 2, axis=0))
+    r3 = np.stack(
+        [r1[1] * r2[2] - r1[2] * r2[1], r1[2] * r2[0] - r1[0] * r2[2], r1[0] * r2[1] - r1[1] * r2[0]]
+    ).conj()
+    return np.stack([r1, r2, r3])
+
+
+def expi_hermitian(A: np.ndarray, eps: float) -> np.ndarray:
+    """exp(i*eps*A) for a batch of Hermitian A of shape (n, 3, 3)."""
+    return np.ascontiguousarray(_expi_soa(np.transpose(A, (1, 2, 0)), eps).transpose(2, 0, 1))
+
+
 def reunitarize(U: np.ndarray) -> np.ndarray:
-    """Project onto SU(3): Gram-Schmidt on rows 1, 2; row 3 = conj(r1 x r2)."""
-    r1 = U[..., 0, :]
-    r1 = r1 / np.linalg.norm(r1, axis=-1, keepdims=True)
-    r2 = U[..., 1, :]
-    r2 = r2 - np.sum(r1.conj() * r2, axis=-1, keepdims=True) * r1
-    r2 = r2 / np.linalg.norm(r2, axis=-1, keepdims=True)
-    r3 = np.cross(r1, r2).conj()
-    return np.stack([r1, r2, r3], axis=-2)
+    """Project a batch (n, 3, 3) onto SU(3): Gram-Schmidt rows 1, 2; row 3 = conj(r1 x r2)."""
+    return np.ascontiguousarray(_reunitarize_soa(np.transpose(U, (1, 2, 0))).transpose(2, 0, 1))
 
 
-def gauge_field(dims, eps: float, seed: int, chunk: int = 1 << 20) -> np.ndarray:
-    """Links U_mu(x) = exp(i*eps*A_mu(x)), shape (4, V, 3, 3), complex128."""
+def gauge_field(dims, eps: float, seed: int, chunk: int = 1 << 18, threads: int | None = None) -> np.ndarray:
+    """Links U_mu(x) = exp(i*eps*A_mu(x)), shape (4, V, 3, 3), complex128.
+
+    The Lie-algebra draws are taken chunk by chunk in a fixed order from one
+    PCG64 stream; only the exponentiation runs on a thread pool, so the field
+    does not depend on the thread count.
+    """
+    from concurrent.futures import ThreadPoolExecutor
+
     V = volume(dims)
     n = 4 * V
     gen = rng(seed, FIELD_GAUGE)
     out = np.empty((n, 3, 3), dtype=np.complex128)
-    for lo in range(0, n, chunk):
-        hi = min(n, lo + chunk)
-        A = lie_gaussian(gen, hi - lo)
-        out[lo:hi] = reunitarize(expi_hermitian(A, eps))
+
+    def work(lo, w):
+        A = np.einsum("an,aij->ijn", w.T, GELL_MANN) * 0.5
+        out[lo : lo + w.shape[0]] = _reunitarize_soa(_expi_soa(A, eps)).transpose(2, 0, 1)
+
+    nt = threads or min(16, os.cpu_count() or 1)
+    with ThreadPoolExecutor(max_workers=nt) as ex:
+        futs = []
+        for lo in range(0, n, chunk):
+            hi = min(n, lo + chunk)
+            futs.append(ex.submit(work, lo, gen.standard_normal((hi - lo, 8))))
+            if len(futs) >= 2 * nt:
+                futs.pop(0).result()
+        for f in futs:
+            f.result()
     return out.reshape(4, V, 3, 3)
 
 
@@ -141,9 +181,7 @@ def gaussian_spinor(dims, seed: int, nrhs: int | None = None, field_id: int = FI
     V = volume(dims)
     shape = (V, 4, 3) if nrhs is None else (nrhs, V, 4, 3)
     gen = rng(seed, field_id)
-    re = gen.standard_normal(shape)
-    im = gen.standard_normal(shape)
-    return re + 1j * im
+    return gen.standard_normal(shape + (2,)).view(np.complex128)[..., 0]
 
 
 def point_sources(dims, site: int = 0) -> np.ndarray:
@@ -190,6 +228,8 @@ WORKLOADS = {
     "wilson_8x8x8x8": Workload("wilson_8x8x8x8", (8, 8, 8, 8), "wilson", 0.12, 0.0, 0.3, 1, 1, "gaussian", 1e-12),
     # Even-odd clover on 32^3x64: FP32 inner BiCGStab + FP64 defect correction vs plain FP64.
     "clover_32x32x32x64": Workload("clover_32x32x32x64", (32, 32, 32, 64), "clover", 0.125, 1.0, 0.2, 2, 1, "gaussian", 1e-10),
+    # Mid-size clover case (working set above L2, a few GB) for profiler captures.
+    "clover_24x24x24x48": Workload("clover_24x24x24x48", (24, 24, 24, 48), "clover", 0.125, 1.0, 0.2, 4, 1, "gaussian", 1e-10),
     # Twelve point sources on 48^3x96 clover with half-precision storage.
     "clover_48x48x48x96_12rhs": Workload(
         "clover_48x48x48x96_12rhs", (48, 48, 48, 96), "clover", 0.125, 1.0, 0.2, 3, 12, "point", 1e-10

@@ -204,3 +204,15 @@ def test_profile_stats_report_event_times(clover_odd, api):
     st = api.bridge_stats(h)
     assert st["schur_pass2"]["launches"] > 0 and st["schur_pass2"]["ms"] > 0
     assert st["residual64"]["launches"] >= 4
+
+
+def test_autotuned_shapes_keep_parity(clover_odd, api):
+    """Autotuning changes launch shapes (and reduction order) but not the answer."""
+    h = clover_odd["L"].handle
+    api.bridge_tune(h, clover_odd["op"], "f32", 1)
+    table = api.bridge_tune_table(h)
+    assert any(k.startswith("hop/1/") for k in table) and any(k.startswith("blas/") for k in table)
+    for block, nblk in table.values():
+        assert block in (64, 128, 256) and nblk >= 1
+    x, info = clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], api.make_solver(tol=1e-12))
+    assert info[0]["true_rel_residual"] <= 1e-12 and rel(x, clover_odd["x"]) < 1e-10
