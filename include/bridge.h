@@ -162,6 +162,37 @@ int bridge_mult_Deo_dev(bridge_lattice lat, const bridge_op* op, int prec, int o
 int bridge_mult_Dhat_dev(bridge_lattice lat, const bridge_op* op, int prec, const double* in_dev, double* out_dev,
                          int nrhs);
 
+/* ---- operator without device allocation ------------------------------------- */
+
+/* Size of the fixed device scratch array used by bridge_mult_Dhat_noalloc:
+ * 64 MiB, held on every GPU that loads the library until the process exits. */
+#define BRIDGE_NOALLOC_SCRATCH_BYTES (64L << 20)
+
+/* The Schur operator of bridge_mult_Dhat_dev, for callers that cannot call
+ * cudaMalloc while they apply the operator (for example an application that
+ * reserves all device memory for its own pool at start-up, or a
+ * latency-critical loop where an allocation, which may synchronize the
+ * device, is not allowed).  The paper has no counterpart: this is a
+ * deployment variant of the Eq. 1 operator.
+ *
+ * in_dev / out_dev: nrhs canonical FP64 even half-lattice vectors on the
+ * device (nrhs*V/2*24 doubles each), owned by the caller.  Its scratch (the
+ * input, the odd intermediate and the output in the GPU layout of precision
+ * prec: 3 * nrhs blocks of the half-lattice field size) lives in one fixed
+ * file-scope device array of BRIDGE_NOALLOC_SCRATCH_BYTES; larger requests
+ * return BRIDGE_EINVAL.  The call allocates nothing: the links in prec and,
+ * for CLOVER, T^-1 for this kappa*c_sw in prec must already exist (apply the
+ * operator once with bridge_mult_Dhat or bridge_solve in that precision
+ * first), else BRIDGE_ESTATE.  The first call on each device looks up the
+ * array's device address (and may load the library's device code there), so
+ * make that first call during set-up.  Work is queued on the lattice stream
+ * and the call returns without waiting.  All calls share the one array: calls
+ * whose work overlaps on the GPU (for example on two lattices, whose streams
+ * run concurrently) race on it; calls on one lattice are ordered by its
+ * stream.  No part of the scratch needs to start at zero. */
+int bridge_mult_Dhat_noalloc(bridge_lattice lat, const bridge_op* op, int prec, const double* in_dev, double* out_dev,
+                             int nrhs);
+
 /* ---- solver ------------------------------------------------------------------ */
 
 /* Solve D x = b for nrhs right-hand sides (Sec. 3: BiCGStab for the clover

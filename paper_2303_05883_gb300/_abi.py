@@ -27,6 +27,7 @@ BRIDGE_F64, BRIDGE_F32, BRIDGE_F16, BRIDGE_BF16 = 0, 1, 2, 3
 BRIDGE_WILSON, BRIDGE_CLOVER = 0, 1
 BRIDGE_EVEN, BRIDGE_ODD, BRIDGE_FULL = 0, 1, 2
 BRIDGE_APPLY_D, BRIDGE_APPLY_DEO, BRIDGE_APPLY_DOE, BRIDGE_APPLY_DHAT = 0, 1, 2, 3
+BRIDGE_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class bridge_op(ctypes.Structure):
@@ -77,6 +78,7 @@ SIGNATURES = {
     "bridge_mult_D_dev": (c_int, [_h, POINTER(bridge_op), c_int, c_void_p, c_void_p, c_int]),
     "bridge_mult_Deo_dev": (c_int, [_h, POINTER(bridge_op), c_int, c_int, c_void_p, c_void_p, c_int]),
     "bridge_mult_Dhat_dev": (c_int, [_h, POINTER(bridge_op), c_int, c_void_p, c_void_p, c_int]),
+    "bridge_mult_Dhat_noalloc": (c_int, [_h, POINTER(bridge_op), c_int, c_void_p, c_void_p, c_int]),
     "bridge_solve": (c_int, [_h, POINTER(bridge_op), POINTER(bridge_solver), _dp, _dp, c_int, POINTER(bridge_info)]),
     "bridge_solve_dev": (
         c_int,

@@ -1,0 +1,102 @@
+"""bridge_mult_Dhat_noalloc through the C-ABI.
+
+The entry point is for callers that cannot allocate device memory while they
+apply the operator (an application that owns all device memory in its own
+pool, or a latency-critical loop where cudaMalloc/cudaFree would synchronize
+the device).  It must give the same Schur operator as bridge_mult_Dhat,
+call after call, while its scratch lives in a fixed device array.  This file
+is collected last so that a failure here comes after every other test has
+run; it also passes alone in a fresh process.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from oracle.lattice import Lattice
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-13, "f32": 2e-6, "f16": 5e-3, "bf16": 5e-3}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_2303_05883_gb300 import api
+
+    return api
+
+
+def _noalloc(api, L, op, prec, x_dev, out_dev, nrhs):
+    import torch
+
+    from paper_2303_05883_gb300 import _abi
+
+    torch.cuda.current_stream().synchronize()
+    st = _abi.load().bridge_mult_Dhat_noalloc(
+        L.handle, ctypes.byref(op), api._prec(prec), ctypes.c_void_p(x_dev.data_ptr()),
+        ctypes.c_void_p(out_dev.data_ptr()), nrhs
+    )
+    api.bridge_sync(L.handle)
+    return st
+
+
+@pytest.mark.parametrize("kind,prec", [("clover", "f32"), ("clover", "f64"), ("wilson", "f16")])
+def test_noalloc_matches_mult_dhat_twice(api, kind, prec):
+    import torch
+
+    dims = (8, 8, 8, 16)
+    lat = Lattice(dims)
+    L = api.Lattice(dims)
+    op = api.make_op(kind, 0.12, 1.0 if kind == "clover" else 0.0)
+    L.upload(synth.gauge_field(dims, 0.3, 21), op)
+    nrhs = 2
+    for call in range(2):  # two calls in a row, different inputs
+        x = synth.gaussian_spinor(dims, 300 + call, nrhs=nrhs)[:, lat.even]
+        want = L.Dhat(op, x, prec)  # the existing entry point (also builds the operator data)
+        x_dev = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        out_dev = torch.full_like(x_dev, float("nan"))
+        assert _noalloc(api, L, op, prec, x_dev, out_dev, nrhs) == 0
+        got = out_dev.cpu().numpy()
+        assert rel(got, want) < TOL[prec], (call, rel(got, want))
+    L.close()
+
+
+def test_noalloc_rejects_too_large_and_unbuilt(api):
+    import torch
+
+    from paper_2303_05883_gb300 import _abi
+
+    dims = (8, 8, 8, 16)
+    L = api.Lattice(dims)
+    op = api.make_op("clover", 0.12, 1.0)
+    L.upload(synth.gauge_field(dims, 0.3, 22), op)
+    vh = 8 * 8 * 8 * 16 // 2
+    # operator data for BF16 not built yet on this lattice
+    x = torch.zeros((1, vh, 4, 3), dtype=torch.complex128, device="cuda")
+    assert _noalloc(api, L, op, "bf16", x, torch.empty_like(x), 1) == _abi.BRIDGE_ESTATE
+    # build F32 data, then ask for more right-hand sides than the scratch holds
+    L.Dhat(op, np.zeros((vh, 4, 3), dtype=np.complex128), "f32")
+    block = ((96 * vh + 255) // 256) * 256
+    nrhs = _abi.BRIDGE_NOALLOC_SCRATCH_BYTES // (3 * block) + 1
+    big = torch.zeros((nrhs, vh, 4, 3), dtype=torch.complex128, device="cuda")
+    assert _noalloc(api, L, op, "f32", big, torch.empty_like(big), nrhs) == _abi.BRIDGE_EINVAL
+    assert "maximum" in _abi.load().bridge_last_error().decode()
+    # the largest nrhs that fits still works and matches
+    nrhs -= 1
+    xs = synth.gaussian_spinor(dims, 9, nrhs=nrhs)[:, Lattice(dims).even]
+    want = L.Dhat(op, xs, "f32")
+    xd = torch.from_numpy(np.ascontiguousarray(xs)).cuda()
+    out = torch.empty_like(xd)
+    assert _noalloc(api, L, op, "f32", xd, out, nrhs) == 0
+    assert rel(out.cpu().numpy(), want) < TOL["f32"]
+    L.close()
