@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--workload", default="clover_32x32x32x64")
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg through host buffers")
     ap.add_argument("--oracle-sites", type=int, default=16384, help="sites per oracle sample")
     return ap.parse_args()
 
@@ -276,6 +277,46 @@ def aggregate_ranks(ms: float, nbytes: float, device="cpu"):
     return float(t.item()), float(b.item())
 
 
+def _parity_odd_index(dims):
+    """For each lexicographic pair (2k, 2k+1), which member is the odd site."""
+    Lx, Ly, Lz, Lt = dims
+    k = np.arange(int(np.prod(dims)) // 2)
+    rest = k // (Lx // 2)
+    y, z, t = rest % Ly, (rest // Ly) % Lz, rest // (Ly * Lz)
+    return ((1 + y + z + t) % 2).astype(np.int64)
+
+
+def run_e2e(args, h, op, solver, b_dev, b_host, nrhs, total_bytes, world):
+    """The same solve through bridge_solve with pinned host buffers."""
+    import ctypes
+
+    import torch
+
+    from paper_2303_05883_gb300 import _abi
+
+    if b_host is None:
+        b_host = b_dev.cpu().numpy()
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    x_pin = torch.zeros_like(b_pin).pin_memory()
+    bn, xn = b_pin.numpy(), x_pin.numpy()
+    lib = _abi.load()
+    info = (_abi.bridge_info * nrhs)()
+    dp = ctypes.POINTER(ctypes.c_double)
+    bp, xp = ctypes.cast(b_pin.data_ptr(), dp), ctypes.cast(x_pin.data_ptr(), dp)
+    e2e_t = []
+    for k in range(args.steps):
+        xn[...] = 0
+        t0 = time.perf_counter()
+        _abi.check(lib.bridge_solve(h, ctypes.byref(op), ctypes.byref(solver), bp, xp, nrhs, info), "bridge_solve")
+        e2e_t.append(time.perf_counter() - t0)
+    nbytes = b_host.nbytes
+    e2e = {"value": (total_bytes / args.steps) / statistics.median(e2e_t) / 1e9 if world == 1 else None,
+           "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes,
+           "ms_per_step": 1e3 * statistics.median(e2e_t)}
+
+    return e2e
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -344,31 +385,42 @@ def run_ours(args):
 
     w = synth.WORKLOADS[args.workload]
     U = w.gauge()
-    b_host = w.sources()[0]
+    nrhs = w.nrhs
+    inner = w.inner
+    if w.source == "point":
+        # the 12 spin-colour point sources at the origin, built on the device
+        b_dev = torch.zeros((nrhs, w.volume, 4, 3), dtype=torch.complex128, device=f"cuda:{local}")
+        for k in range(nrhs):
+            b_dev[k, 0, k // 3, k % 3] = 1.0
+        b_host = None
+    else:
+        b_host = w.sources()[0] if nrhs == 1 else w.sources()
+        b_dev = torch.from_numpy(b_host).to(f"cuda:{local}")
     kind = w.kind
     op = api.make_op(kind, w.kappa, w.csw, w.bc)
     L = api.Lattice(w.dims)
     L.upload(U, op)
     h = L.handle
-    solver = api.make_solver(tol=w.tol, inner_prec="f32", mixed=1)
+    solver = api.make_solver(tol=w.tol, inner_prec=inner, mixed=1)
     stream = L.stream
-    b_dev = torch.from_numpy(b_host).to(f"cuda:{local}")
     x_dev = torch.zeros_like(b_dev)
 
-    def solve_dev(prm):
+    def solve_dev(prm, n=None):
+        """One solve of the first n right-hand sides; returns the worst info record."""
+        n = nrhs if n is None else n
         x_dev.zero_()
         torch.cuda.current_stream().synchronize()
         from ctypes import byref, c_void_p
 
         from paper_2303_05883_gb300 import _abi
 
-        info = (_abi.bridge_info * 1)()
+        info = (_abi.bridge_info * n)()
         st = _abi.load().bridge_solve_dev(h, byref(op), byref(prm), c_void_p(b_dev.data_ptr()),
-                                          c_void_p(x_dev.data_ptr()), 1, info)
+                                          c_void_p(x_dev.data_ptr()), n, info)
         _abi.check(st, "bridge_solve_dev")
-        return info[0]
+        return max((info[k] for k in range(n)), key=lambda i: i.true_rel_residual)
 
-    api.bridge_tune(h, op, "f32", 1)
+    api.bridge_tune(h, op, inner, nrhs)
     if not args.no_fp64:
         api.bridge_tune(h, op, "f64", 1)
     for _ in range(args.warmup):
@@ -427,13 +479,13 @@ def run_ours(args):
     shares = {k: round(v["ms"] / step_ms_prof, 4) for k, v in pst.items() if v["ms"] > 0}
 
     # ---- the plain D_eo hop kernel alone on resident FP32 fields
-    lat_half = b_host.reshape(-1, 4, 3)
-    fo = api.bridge_field_create(h, "f32", 1, 1)
-    fe = api.bridge_field_create(h, "f32", 0, 1)
-    from oracle.lattice import Lattice as _OL  # index order only: odd sites of the lattice
-
-    odd = _OL(w.dims).odd
-    api.bridge_field_import(fo, np.ascontiguousarray(lat_half[odd]))
+    fo = api.bridge_field_create(h, inner, 1, nrhs)
+    fe = api.bridge_field_create(h, inner, 0, nrhs)
+    # any odd half-lattice vectors do: use the odd sites of the source(s)
+    half = b_dev.reshape(nrhs, w.volume // 2, 2, 4, 3)  # lexicographic pairs (2k, 2k+1)
+    par = torch.from_numpy(_parity_odd_index(w.dims)).to(b_dev.device)
+    src_odd = torch.gather(half, 2, par.view(1, -1, 1, 1, 1).expand(nrhs, -1, 1, 4, 3)).squeeze(2).contiguous()
+    api.bridge_field_import(fo, src_odd)
     api.bridge_sync(h)
     for _ in range(3):
         api.bridge_apply(h, op, 1, fe, fo)
@@ -447,60 +499,51 @@ def run_ours(args):
     torch.cuda.synchronize()
     deo_ms = a0.elapsed_time(a1) / reps
     deo_bytes = api.bridge_stats(h)["hop_deo"]["bytes"] / reps
-    deo = {"kernel": "hop_deo", "prec": "f32", "gbs": deo_bytes / (deo_ms * 1e-3) / 1e9, "us_per_launch": deo_ms * 1e3,
-           "bytes_per_launch": deo_bytes, "frac": deo_bytes / (deo_ms * 1e-3) / 1e9 / peak,
-           "gflops": w.volume / 2 * 1344 / (deo_ms * 1e-3) / 1e9}
+    deo = {"kernel": "hop_deo", "prec": inner, "nrhs": nrhs, "gbs": deo_bytes / (deo_ms * 1e-3) / 1e9,
+           "us_per_launch": deo_ms * 1e3, "bytes_per_launch": deo_bytes,
+           "frac": deo_bytes / (deo_ms * 1e-3) / 1e9 / peak,
+           "gflops": nrhs * w.volume / 2 * 1344 / (deo_ms * 1e-3) / 1e9}
     api.bridge_field_destroy(fo)
     api.bridge_field_destroy(fe)
 
     # ---- plain FP64 BiCGStab on the same system
-    solve = {"mixed_ms": ms / args.steps, "mixed_inner_iters": iters, "mixed_true_rel_residual": res}
+    solve = {"mixed_ms": ms / args.steps, "mixed_inner_iters": iters, "mixed_true_rel_residual": res,
+             "inner_prec": inner, "nrhs": nrhs}
     if not args.no_fp64:
+        # plain FP64 BiCGStab on the first right-hand side; with several
+        # right-hand sides the comparison is nrhs x that single solve
         s64 = api.make_solver(tol=w.tol, mixed=0)
         t0 = time.perf_counter()
-        i64 = solve_dev(s64)
+        i64 = solve_dev(s64, n=1)
         t64 = time.perf_counter() - t0
-        solve.update({"fp64_ms": t64 * 1e3, "fp64_inner_iters": i64.inner_iters,
-                      "fp64_true_rel_residual": i64.true_rel_residual, "speedup": t64 * 1e3 / (ms / args.steps)})
+        solve.update({"fp64_ms_one_rhs": t64 * 1e3, "fp64_ms": nrhs * t64 * 1e3, "fp64_inner_iters": i64.inner_iters,
+                      "fp64_true_rel_residual": i64.true_rel_residual,
+                      "speedup": nrhs * t64 * 1e3 / (ms / args.steps)})
 
     # ---- end to end through bridge_solve with pinned host buffers
-    b_pin = torch.from_numpy(b_host).pin_memory()
-    x_pin = torch.zeros_like(b_pin).pin_memory()
-    bn, xn = b_pin.numpy(), x_pin.numpy()
-    import ctypes
-
-    from paper_2303_05883_gb300 import _abi
-
-    lib = _abi.load()
-    info = (_abi.bridge_info * 1)()
-    dp = ctypes.POINTER(ctypes.c_double)
-    bp, xp = ctypes.cast(b_pin.data_ptr(), dp), ctypes.cast(x_pin.data_ptr(), dp)
-    e2e_t = []
-    for k in range(args.steps):
-        xn[...] = 0
-        t0 = time.perf_counter()
-        _abi.check(lib.bridge_solve(h, ctypes.byref(op), ctypes.byref(solver), bp, xp, 1, info), "bridge_solve")
-        e2e_t.append(time.perf_counter() - t0)
-    nbytes = b_host.nbytes
-    e2e = {"value": (total_bytes / args.steps) / statistics.median(e2e_t) / 1e9 if world == 1 else None,
-           "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes,
-           "ms_per_step": 1e3 * statistics.median(e2e_t)}
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, h, op, solver, b_dev, b_host, nrhs, total_bytes, world)
 
     # ---- serving sample
+    # ---- serving sample
     serving = None
-    if args.serving_requests > 0 and rank == 0:
+    if args.serving_requests > 0 and rank == 0 and nrhs == 1:
         serving = serving_sample(api, args.serving_requests, {"dims": w.dims, "L": L}, U)
 
     # ---- CPU oracle baseline (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1:
-        v, secs, cores = oracle_sample(w, U, b_host, 4 * args.oracle_sites, seed=0)
+        # the oracle's cost does not depend on the values: time it on a Gaussian spinor
+        b_cpu = synth.gaussian_spinor(w.dims, w.seed) if b_host is None else (b_host[0] if b_host.ndim == 4 else b_host)
+        v, secs, cores = oracle_sample(w, U, b_cpu, 4 * args.oracle_sites, seed=0)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"FP64 numpy oracle: clover D at {4 * args.oracle_sites} random sites of the "
                          f"{args.workload} lattice ({secs:.1f} s)"}
 
     if rank == 0:
-        working_set = (4 * w.volume * 48 + w.volume * 288 + 12 * w.volume / 2 * 96 + 3 * w.volume * 192) / 1e9
+        sb = {"f32": 96, "f16": 52, "bf16": 52, "f64": 192}[inner]
+        working_set = (4 * w.volume * sb / 2 + w.volume * sb * 1.5 + nrhs * (12 * w.volume / 2 * sb + 3 * w.volume * 192)) / 1e9
         line = {
             "metric": METRIC,
             "value": value,
@@ -512,15 +555,16 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32+f64",
+            "dtype": f"{'f32' if inner == 'f32' else inner + ' storage, f32 math'}+f64",
             "data": "synthetic",
             "config": {
                 "workload": args.workload,
                 "lattice": "x".join(map(str, w.dims)),
                 "operator": f"{kind}, kappa={w.kappa}, c_sw={w.csw}, bc={list(w.bc)}",
                 "links": f"exp({w.eps} i A), seed {w.seed}",
-                "source": "gaussian",
-                "solver": "even-odd BiCGStab, f32 inner, f64 defect correction",
+                "source": w.source if nrhs == 1 else f"{nrhs} {w.source} sources",
+                "nrhs": nrhs,
+                "solver": f"even-odd BiCGStab, {inner} inner, f64 defect correction",
                 "tol": w.tol,
                 "l2": f"inputs larger than L2 (solve working set ~{working_set:.1f} GB)",
                 "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",

@@ -253,6 +253,7 @@ static int gauge_upload(bridge_lattice L, const double* U, const bridge_op* op, 
     clover_ptr(L, P_F64, true, op_kcsw(*op));
   }
   BR_CUDA(cudaStreamSynchronize(L->stream));
+  if (host) L->stage_in.reset();  // the link staging buffer is as large as the FP64 links
   BR_API_END
 }
 

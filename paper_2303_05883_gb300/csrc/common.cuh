@@ -280,13 +280,23 @@ BR_D void load_clover_block(const char* base, long vh, uint32_t i, int b, typena
       a[4 * k + 3] = v.w;
     }
   } else {
-    const uint32_t* p = reinterpret_cast<const uint32_t*>(base);
+    // 72 halves in 9 planes of 8: block 0 = planes 0-3 and the first half of
+    // plane 4, block 1 = the second half of plane 4 and planes 5-8.
+    const uint4* p = reinterpret_cast<const uint4*>(base);
     H16<P> h;
-    // 18 words of 2 halves; word w of the 72-half row lives in plane w / 4, lane w % 4
+    uint32_t w[20];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const uint4 v = __ldg(p + (4 * b + q) * vh + i);
+      w[4 * q] = v.x;
+      w[4 * q + 1] = v.y;
+      w[4 * q + 2] = v.z;
+      w[4 * q + 3] = v.w;
+    }
+    const int off = 2 * b;  // block 1 starts at word 2 of plane 4
 #pragma unroll
     for (int k = 0; k < 18; ++k) {
-      const int w = 18 * b + k;
-      float2 t = h.to2(__ldg(p + ((w >> 2) * vh + i) * 4 + (w & 3)));
+      const float2 t = h.to2(w[off + k]);
       a[2 * k] = t.x;
       a[2 * k + 1] = t.y;
     }

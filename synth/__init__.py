@@ -208,6 +208,7 @@ class Workload:
     source: str  # "gaussian" or "point"
     tol: float
     bc: tuple = field(default=(1, 1, 1, -1))
+    inner: str = "f32"  # storage precision of the inner solver
 
     @property
     def volume(self) -> int:
@@ -232,6 +233,6 @@ WORKLOADS = {
     "clover_24x24x24x48": Workload("clover_24x24x24x48", (24, 24, 24, 48), "clover", 0.125, 1.0, 0.2, 4, 1, "gaussian", 1e-10),
     # Twelve point sources on 48^3x96 clover with half-precision storage.
     "clover_48x48x48x96_12rhs": Workload(
-        "clover_48x48x48x96_12rhs", (48, 48, 48, 96), "clover", 0.125, 1.0, 0.2, 3, 12, "point", 1e-10
+        "clover_48x48x48x96_12rhs", (48, 48, 48, 96), "clover", 0.125, 1.0, 0.2, 3, 12, "point", 1e-10, inner="f16"
     ),
 }

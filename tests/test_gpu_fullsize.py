@@ -1,0 +1,141 @@
+"""Parity at the full workload sizes, on sampled outputs.
+
+At 32^3 x 64 (the benchmarked workload) and 48^3 x 96 x 12 right-hand sides
+the oracle cannot process whole fields in seconds, so it computes the
+operator at sampled sites -- random sites plus the lattice corners, where
+every boundary wrap is exercised -- and the GPU results are compared there
+element by element.  Solves are checked by the GPU's FP64 true residual and
+by the oracle's own residual b - D x evaluated at sampled sites.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dirac
+from oracle.lattice import Lattice
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-13, "f32": 2e-6, "f16": 5e-3, "bf16": 5e-3}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def sample_sites(lat, n, seed, parity=None):
+    gen = np.random.default_rng(seed)
+    L = lat.dims
+    corners = [lat.index(np.array([[x], [y], [z], [t]]))[0]
+               for x in (0, L[0] - 1) for y in (0, L[1] - 1) for z in (0, L[2] - 1) for t in (0, L[3] - 1)]
+    pool = np.arange(lat.V) if parity is None else lat.sites_of(parity)
+    s = np.concatenate([gen.choice(pool, n, replace=False), np.array(corners)])
+    if parity is not None:
+        s = s[lat.parity[s] == parity]
+    return np.unique(s)
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_2303_05883_gb300 import api
+
+    return api
+
+
+@pytest.fixture(scope="module")
+def c2(api):
+    w = synth.WORKLOADS["clover_32x32x32x64"]
+    lat = Lattice(w.dims)
+    U = w.gauge()
+    b = w.sources()[0]
+    op = api.make_op("clover", w.kappa, w.csw)
+    L = api.Lattice(w.dims)
+    L.upload(U, op)
+    yield dict(w=w, lat=lat, U=U, b=b, op=op, L=L)
+    L.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_full_operator_sampled_32x32x32x64(c2, prec):
+    w, lat, U, b = c2["w"], c2["lat"], c2["U"], c2["b"]
+    got = c2["L"].D(c2["op"], b, prec)
+    s = sample_sites(lat, 1500, 1)
+    want = dirac.dirac(U, b, lat, w.kappa, w.csw, w.bc, sites=s)
+    assert rel(got[s], want) < TOL[prec]
+
+
+def test_deo_sampled_32x32x32x64(c2):
+    w, lat, U, b = c2["w"], c2["lat"], c2["U"], c2["b"]
+    got = c2["L"].Deo(c2["op"], np.ascontiguousarray(b[lat.odd]), 0, "f32")  # D_eo psi_o
+    s = sample_sites(lat, 1500, 2, parity=0)
+    full = lat.embed(b[lat.odd], 1)
+    want = -w.kappa * dirac.hop(U, full, lat, w.bc, sites=s)
+    assert rel(got[s // 2], want) < TOL["f32"]
+
+
+def test_schur_sampled_32x32x32x64(c2):
+    """D^(eo) x_e at sampled even sites, built by the oracle from its neighbour set."""
+    w, lat, U, b = c2["w"], c2["lat"], c2["U"], c2["b"]
+    xe = np.ascontiguousarray(b[lat.even])
+    got = c2["L"].Dhat(c2["op"], xe, "f32")
+    s = sample_sites(lat, 400, 3, parity=0)
+    ys = np.unique(np.concatenate([lat.neighbor(s, mu, st)[0] for mu in range(4) for st in (1, -1)]))
+    full_e = lat.embed(xe, 0)
+    Tinv_y = np.linalg.inv(dirac.clover_term(U, lat, w.kappa, w.csw, ys))
+    tmp = dirac.apply_site(Tinv_y, -w.kappa * dirac.hop(U, full_e, lat, w.bc, sites=ys))
+    tmp_full = np.zeros_like(full_e)
+    tmp_full[ys] = tmp
+    Tinv_s = np.linalg.inv(dirac.clover_term(U, lat, w.kappa, w.csw, s))
+    want = full_e[s] - dirac.apply_site(Tinv_s, -w.kappa * dirac.hop(U, tmp_full, lat, w.bc, sites=s))
+    assert rel(got[s // 2], want) < TOL["f32"]
+
+
+def test_mixed_solve_32x32x32x64(c2, api):
+    """The benchmarked solve: FP32 inner, FP64 outer, 1e-10 true residual."""
+    w, lat, U, b = c2["w"], c2["lat"], c2["U"], c2["b"]
+    x, info = c2["L"].solve(c2["op"], b, api.make_solver(tol=w.tol, inner_prec="f32"))
+    assert info[0]["status"] == 0 and info[0]["true_rel_residual"] <= w.tol
+    # the oracle's residual at sampled sites
+    s = sample_sites(lat, 3000, 4)
+    r = b[s] - dirac.dirac(U, x, lat, w.kappa, w.csw, w.bc, sites=s)
+    assert np.linalg.norm(r) / np.linalg.norm(b[s]) < 5 * w.tol
+    # and the GPU's FP64 operator on the solution agrees with the oracle there
+    Dx = c2["L"].D(c2["op"], x, "f64")
+    assert rel(Dx[s], b[s] - r) < 1e-13
+
+
+def test_twelve_rhs_f16_48x48x48x96(api):
+    """48^3 x 96, 12 point sources, FP16 storage inner solver, FP64 outer to 1e-10."""
+    import torch
+
+    w = synth.WORKLOADS["clover_48x48x48x96_12rhs"]
+    lat = Lattice(w.dims)
+    U = w.gauge()
+    op = api.make_op("clover", w.kappa, w.csw)
+    L = api.Lattice(w.dims)
+    L.upload(U, op)
+    B = torch.zeros((12, w.volume, 4, 3), dtype=torch.complex128, device="cuda")
+    for k in range(12):
+        B[k, 0, k // 3, k % 3] = 1.0
+    X, info = L.solve(op, B, api.make_solver(tol=w.tol, inner_prec="f16"))
+    assert len(info) == 12
+    for k in range(12):
+        assert info[k]["status"] == 0 and info[k]["true_rel_residual"] <= w.tol, (k, info[k])
+    # oracle residual at sampled sites (the origin's neighbourhood and random
+    # sites) for three of the twelve right-hand sides
+    s = np.unique(np.concatenate([sample_sites(lat, 2000, 5),
+                                  np.concatenate([lat.neighbor(np.array([0]), mu, st)[0] for mu in range(4) for st in (1, -1)]),
+                                  np.array([0])]))
+    del B
+    for k in (0, 5, 11):
+        x = X[k].cpu().numpy()
+        bk = np.zeros((len(s), 4, 3), dtype=np.complex128)
+        bk[s == 0, k // 3, k % 3] = 1.0
+        r = bk - dirac.dirac(U, x, lat, w.kappa, w.csw, w.bc, sites=s)
+        # |b| = 1 (one unit entry); the sampled residual is bounded by the global one
+        assert np.linalg.norm(r) <= 2 * w.tol, (k, np.linalg.norm(r))
+    L.close()
