@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg through host buffers")
+    ap.add_argument("--inner", default=None, help="override the workload's inner storage precision (f32, f16, bf16)")
     ap.add_argument("--oracle-sites", type=int, default=16384, help="sites per oracle sample")
     return ap.parse_args()
 
@@ -386,7 +387,7 @@ def run_ours(args):
     w = synth.WORKLOADS[args.workload]
     U = w.gauge()
     nrhs = w.nrhs
-    inner = w.inner
+    inner = args.inner or w.inner
     if w.source == "point":
         # the 12 spin-colour point sources at the origin, built on the device
         b_dev = torch.zeros((nrhs, w.volume, 4, 3), dtype=torch.complex128, device=f"cuda:{local}")

@@ -303,8 +303,8 @@ def bridge_tune_table(lat) -> dict:
     _abi.load().bridge_tune_table(lat, buf, len(buf))
     out = {}
     for line in buf.value.decode().splitlines():
-        k, b, n = line.split()
-        out[k] = (int(b), int(n))
+        k, b, n, v = line.split()
+        out[k] = (int(b), int(n), int(v))
     return out
 
 

@@ -174,6 +174,25 @@ BR_D void load_spinor(const char* base, long vh, uint32_t i, cx<typename Tr<P>::
   }
 }
 
+// 16-bit spinor without its per-site scale applied; returns the scale.
+template <int P>
+BR_D float load_spinor_unscaled(const char* base, long vh, uint32_t i, cx<float> s[12]) {
+  static_assert(Tr<P>::half, "16-bit storage only");
+  const uint4* p = reinterpret_cast<const uint4*>(base);
+  const float* sc = reinterpret_cast<const float*>(base + 48 * vh);
+  H16<P> h;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint4 v = __ldg(p + k * vh + i);
+    const float2 a = h.to2(v.x), b = h.to2(v.y), c = h.to2(v.z), d = h.to2(v.w);
+    s[4 * k + 0] = {a.x, a.y};
+    s[4 * k + 1] = {b.x, b.y};
+    s[4 * k + 2] = {c.x, c.y};
+    s[4 * k + 3] = {d.x, d.y};
+  }
+  return __ldg(sc + i);
+}
+
 template <int P>
 BR_D void store_spinor(char* base, long vh, uint32_t i, const cx<typename Tr<P>::R> s[12]) {
   if constexpr (P == P_F64) {

@@ -105,17 +105,29 @@ BR_D void hop_one(const char* in, const char* lb, long vh, uint32_t nb, uint32_t
                   cx<typename Tr<P>::R> acc[12]) {
   using R = typename Tr<P>::R;
   cx<R> h[2][3];
-  {
-    cx<R> psi[12];
-    load_spinor<P>(in, vh, nb, psi);
+  if constexpr (Tr<P>::half) {
+    // project the stored values, then apply the per-site scale and the
+    // boundary phase to the 12 projected components only
+    cx<float> psi[12];
+    const float sc = load_spinor_unscaled<P>(in, vh, nb, psi) * (wraps ? (float)bc : 1.0f);
     project<R, MU, FWD>(psi, h);
-  }
-  if (wraps) {
-    const R ph = (R)bc;
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) h[k][c] = ph * h[k][c];
+      for (int c = 0; c < 3; ++c) h[k][c] = sc * h[k][c];
+  } else {
+    {
+      cx<R> psi[12];
+      load_spinor<P>(in, vh, nb, psi);
+      project<R, MU, FWD>(psi, h);
+    }
+    if (wraps) {
+      const R ph = (R)bc;
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[k][c] = ph * h[k][c];
+    }
   }
   Link<R> U;
   load_link<P>(lb, vh, li, U);
@@ -143,8 +155,11 @@ BR_D void hop_dir(const HopArgs& a, const char* in, const char* g_out, const cha
   hop_one<P, MU, false>(in, g_in + MU * lbb, a.g.vh, b, b, wb, a.bc[MU], acc);
 }
 
-template <int P, int FL, int RED>
-__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
+// MINB: minimum resident 256-thread blocks per SM the compiler must allow
+// (1 = no register cap, 3 = <= 80 registers, 4 = <= 64 registers); the
+// autotuner picks the variant per kernel and lattice.
+template <int P, int FL, int RED, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
   using R = typename Tr<P>::R;
   const int nrhs = a.nrhs;
   const int rhs = blockIdx.x % nrhs;
@@ -238,15 +253,18 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
 // Launch with the given block size on a stream; returns false for a
 // (flags, reduction) pair that is not instantiated.  With occ != null,
 // nothing is launched: *occ receives the resident blocks per SM instead.
+// variant: register budget (0 = none, 1 = 80, 2 = 64 registers); only the
+// kernels of the Schur passes and D_eo have the capped variants.
 template <int P>
-bool launch_hop(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ = nullptr);
+bool launch_hop(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ = nullptr, int variant = 0);
 template <>
-bool launch_hop<P_F64>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ);
+bool launch_hop<P_F64>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ, int variant);
 template <>
-bool launch_hop<P_F32>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ);
+bool launch_hop<P_F32>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ, int variant);
 template <>
-bool launch_hop<P_F16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ);
+bool launch_hop<P_F16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ, int variant);
 template <>
-bool launch_hop<P_BF16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ);
+bool launch_hop<P_BF16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ, int variant);
+bool hop_has_variants(int flags, int red);
 
 }  // namespace bridge

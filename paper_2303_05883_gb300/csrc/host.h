@@ -87,7 +87,8 @@ Field make_field(int prec, int subset, int nrhs, long vh);
 // Launch shapes picked per (kernel class, precision, flags, lattice, nrhs).
 struct LaunchShape {
   int block = 256;
-  int nblk = 0;  // site blocks per rhs; 0 -> cover the lattice once
+  int nblk = 0;     // site blocks per rhs; 0 -> cover the lattice once
+  int variant = 0;  // register-budget variant of the kernel (see launch_hop)
 };
 
 struct Stats {

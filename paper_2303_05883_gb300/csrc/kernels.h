@@ -7,7 +7,8 @@
 namespace bridge {
 
 // ---------------------------------------------------------------- hop
-bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ = nullptr);
+bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ = nullptr,
+                    int variant = 0);
 
 // ----------------------------------------------------- BiCGStab vectors
 enum BlasOp { B_INIT = 0, B_S = 1, B_XR = 2, B_P = 3 };

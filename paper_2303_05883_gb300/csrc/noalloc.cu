@@ -159,7 +159,7 @@ extern "C" int bridge_mult_Dhat_noalloc(bridge_lattice L, const bridge_op* op, i
       return n;
     });
     a.nblk = s1.nblk;
-    BR_CHECK(launch_hop_any(prec, f1, R_NONE, a, s1.block, st), BRIDGE_EINVAL, "hop variant");
+    BR_CHECK(launch_hop_any(prec, f1, R_NONE, a, s1.block, st, nullptr, s1.variant), BRIDGE_EINVAL, "hop variant");
     // pass 2: out_e = in_e + kappa T_ee^-1 H_eo tmp_o
     const int f2 = F_SELF | (clov ? F_E_CLOV : 0);
     a.out_parity = 0;
@@ -176,7 +176,7 @@ extern "C" int bridge_mult_Dhat_noalloc(bridge_lattice L, const bridge_op* op, i
       return n;
     });
     a.nblk = s2.nblk;
-    BR_CHECK(launch_hop_any(prec, f2, R_NONE, a, s2.block, st), BRIDGE_EINVAL, "hop variant");
+    BR_CHECK(launch_hop_any(prec, f2, R_NONE, a, s2.block, st, nullptr, s2.variant), BRIDGE_EINVAL, "hop variant");
 
     ca.canon = nullptr;
     ca.dst = nullptr;

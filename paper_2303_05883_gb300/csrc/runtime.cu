@@ -247,7 +247,7 @@ void run_hop(bridge_lattice_s* L, HopCall c, cudaStream_t st) {
                           std::to_string(c.red) + "/" + dims_key(L) + "/" + std::to_string(c.nrhs);
   LaunchShape sh = shape_for(L, key, L->vh, c.nrhs, [&](int block) {
     int n = 0;
-    launch_hop_any(c.prec, c.flags, c.red, a, block, st, &n);
+    launch_hop_any(c.prec, c.flags, c.red, a, block, st, &n, 0);
     return n;
   });
   a.nblk = sh.nblk;
@@ -263,7 +263,8 @@ void run_hop(bridge_lattice_s* L, HopCall c, cudaStream_t st) {
   const double bytes = c.count_work ? (double)L->vh * (hc.rhs_bytes * c.nrhs + hc.shared_bytes) : 0.0;
   const double flops = c.count_work ? (double)L->vh * c.nrhs * hc.rhs_flops : 0.0;
   note_launch(L, c.cls, bytes, flops, st, true);
-  BR_CHECK(launch_hop_any(c.prec, c.flags, c.red, a, sh.block, st), BRIDGE_EINVAL, "hop variant not instantiated");
+  BR_CHECK(launch_hop_any(c.prec, c.flags, c.red, a, sh.block, st, nullptr, sh.variant), BRIDGE_EINVAL,
+           "hop variant not instantiated");
   note_launch(L, c.cls, bytes, flops, st, false);
   BR_CUDA(cudaGetLastError());
 }
@@ -446,12 +447,19 @@ void clover_site(bridge_lattice_s* L, int prec, bool inverse, double kcsw, int p
   BR_CUDA(cudaGetLastError());
 }
 
-bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ) {
+bool hop_has_variants(int flags, int red) {
+  return (flags == 0 && red == R_NONE) || (flags == F_E_CLOV && red == R_NONE) ||
+         ((flags == F_SELF || flags == (F_SELF | F_E_CLOV)) && (red == R_DOT_A || red == R_TS));
+}
+
+bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ,
+                    int variant) {
+  if (!hop_has_variants(flags, red)) variant = 0;
   switch (prec) {
-    case P_F64: return launch_hop<P_F64>(flags, red, a, block, st, occ);
-    case P_F32: return launch_hop<P_F32>(flags, red, a, block, st, occ);
-    case P_F16: return launch_hop<P_F16>(flags, red, a, block, st, occ);
-    case P_BF16: return launch_hop<P_BF16>(flags, red, a, block, st, occ);
+    case P_F64: return launch_hop<P_F64>(flags, red, a, block, st, occ, variant);
+    case P_F32: return launch_hop<P_F32>(flags, red, a, block, st, occ, variant);
+    case P_F16: return launch_hop<P_F16>(flags, red, a, block, st, occ, variant);
+    case P_BF16: return launch_hop<P_BF16>(flags, red, a, block, st, occ, variant);
   }
   return false;
 }

@@ -459,8 +459,11 @@ bool SolveState::advance() {
     switch (state_) {
       case ST_START: {
         canon_to_field(L_, b_dev_, b64_, st_);
+        canon_to_field(L_, x_dev_, x64_, st_);
         norm2_field(L_, b64_, 0, red(FIN_STORE, 0), st_);
         norm2_field(L_, b64_, 1, red(FIN_STORE, 1), st_);
+        norm2_field(L_, x64_, 0, red(FIN_STORE, 2), st_);
+        norm2_field(L_, x64_, 1, red(FIN_STORE, 3), st_);
         BR_CUDA(cudaMemcpyAsync(h_result_->ptr, result_->ptr, sizeof(double) * 4 * 4 * nrhs_, cudaMemcpyDeviceToHost, st_));
         BR_CUDA(cudaEventRecord(ev_misc_, st_));
         pending_ = ev_misc_;
@@ -468,15 +471,32 @@ bool SolveState::advance() {
         break;
       }
       case ST_BNORM: {
-        const double* hr = reinterpret_cast<const double*>(h_result_->ptr);
+        double* hr = reinterpret_cast<double*>(h_result_->ptr);
         int* hm = reinterpret_cast<int*>(h_mask_->ptr);
+        bool drop_guess = false, guess = false;
         for (int r = 0; r < nrhs_; ++r) {
           b2_[r] = hr[(0 * nrhs_ + r) * 4] + hr[(1 * nrhs_ + r) * 4];
+          const double x2 = hr[(2 * nrhs_ + r) * 4] + hr[(3 * nrhs_ + r) * 4];
           hm[r] = b2_[r] > 0.0;  // the solution of D x = 0 is x = 0: drop the guess
+          drop_guess = drop_guess || (b2_[r] == 0.0 && x2 != 0.0);
+          guess = guess || (b2_[r] > 0.0 && x2 != 0.0);
         }
-        BR_CUDA(cudaMemcpyAsync(mask_->ptr, hm, sizeof(int) * nrhs_, cudaMemcpyHostToDevice, st_));
-        canon_to_field(L_, x_dev_, x64_, st_, reinterpret_cast<const int*>(mask_->ptr));
-        enqueue_residual();
+        if (drop_guess) {
+          BR_CUDA(cudaMemcpyAsync(mask_->ptr, hm, sizeof(int) * nrhs_, cudaMemcpyHostToDevice, st_));
+          canon_to_field(L_, x_dev_, x64_, st_, reinterpret_cast<const int*>(mask_->ptr));
+        }
+        if (guess) {
+          enqueue_residual();
+        } else {
+          // x = 0 for every right-hand side: r = b exactly, no FP64 operator needed
+          convert_field(L_, b64_, r64_, 0, st_, nullptr);
+          convert_field(L_, b64_, r64_, 1, st_, nullptr);
+          for (int r = 0; r < nrhs_; ++r) {
+            hr[(2 * nrhs_ + r) * 4] = hr[(0 * nrhs_ + r) * 4];
+            hr[(3 * nrhs_ + r) * 4] = hr[(1 * nrhs_ + r) * 4];
+          }
+          pending_ = nullptr;
+        }
         state_ = ST_RESID;
         break;
       }

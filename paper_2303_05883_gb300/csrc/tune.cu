@@ -38,7 +38,7 @@ static std::string cache_path() {
   return p ? std::string(p) : std::string();
 }
 
-// Cache format: one line per entry, "device key block nblk".
+// Cache format: one line per entry, "device key block nblk variant".
 void tune_cache_load(bridge_lattice_s* L) {
   const std::string path = cache_path();
   if (path.empty()) return;
@@ -46,10 +46,10 @@ void tune_cache_load(bridge_lattice_s* L) {
   if (!f) return;
   const std::string tag = device_tag();
   std::string dev, key;
-  int block, nblk;
+  int block, nblk, variant;
   std::lock_guard<std::mutex> lk(L->tune_mu);
-  while (f >> dev >> key >> block >> nblk)
-    if (dev == tag) L->tuned[key] = LaunchShape{block, nblk};
+  while (f >> dev >> key >> block >> nblk >> variant)
+    if (dev == tag) L->tuned[key] = LaunchShape{block, nblk, variant};
 }
 
 static void tune_cache_save(bridge_lattice_s* L, const std::vector<std::string>& keys) {
@@ -60,7 +60,8 @@ static void tune_cache_save(bridge_lattice_s* L, const std::vector<std::string>&
   std::lock_guard<std::mutex> lk(L->tune_mu);
   for (const auto& k : keys) {
     auto it = L->tuned.find(k);
-    if (it != L->tuned.end()) f << tag << " " << k << " " << it->second.block << " " << it->second.nblk << "\n";
+    if (it != L->tuned.end())
+      f << tag << " " << k << " " << it->second.block << " " << it->second.nblk << " " << it->second.variant << "\n";
   }
 }
 
@@ -94,20 +95,23 @@ static float time_launches(Launch&& launch, cudaStream_t st, cudaEvent_t a, cuda
 }
 
 struct Candidate {
-  int block, nblk;
+  int block, nblk, variant;
 };
 
-static std::vector<Candidate> candidates(long vh, int nrhs, const std::function<int(int)>& occ) {
+// Block sizes x {persistent grid, 2x persistent, one site per thread} for
+// each register-budget variant; occ(block, variant) gives resident blocks/SM.
+static std::vector<Candidate> candidates(long vh, int nrhs, int nvariants, const std::function<int(int, int)>& occ) {
   std::vector<Candidate> out;
-  for (int block : {64, 128, 256}) {
-    const long cover = (vh + block - 1) / block;
-    const int per_sm = std::max(1, occ(block));
-    for (int m : {1, 2}) {
-      long n = std::max<long>(1, (long)sm_count() * per_sm * m / std::max(1, nrhs));
-      if (n < cover) out.push_back({block, (int)n});
+  for (int v = 0; v < nvariants; ++v)
+    for (int block : {64, 128, 256}) {
+      const long cover = (vh + block - 1) / block;
+      const int per_sm = std::max(1, occ(block, v));
+      for (int m : {1, 2}) {
+        long n = std::max<long>(1, (long)sm_count() * per_sm * m / std::max(1, nrhs));
+        if (n < cover) out.push_back({block, (int)n, v});
+      }
+      out.push_back({block, (int)cover, v});
     }
-    out.push_back({block, (int)cover});
-  }
   return out;
 }
 
@@ -181,16 +185,17 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
     a.red.fin = v.red == R_NONE ? FIN_NONE : FIN_STORE;
     const std::string key = "hop/" + std::to_string(prec) + "/" + std::to_string(v.flags) + "/" + std::to_string(v.red) +
                             "/" + dims + "/" + std::to_string(nrhs);
-    auto occ = [&](int block) {
+    auto occ = [&](int block, int variant) {
       int n = 0;
-      launch_hop_any(prec, v.flags, v.red, a, block, st, &n);
+      launch_hop_any(prec, v.flags, v.red, a, block, st, &n, variant);
       return n;
     };
     float best = 1e30f;
-    Candidate pick{128, 0};
-    for (const auto& c : candidates(vh, nrhs, occ)) {
+    Candidate pick{128, 0, 0};
+    for (const auto& c : candidates(vh, nrhs, hop_has_variants(v.flags, v.red) ? 3 : 1, occ)) {
       a.nblk = c.nblk;
-      const float ms = time_launches([&] { launch_hop_any(prec, v.flags, v.red, a, c.block, st); }, st, ea, eb, 5);
+      const float ms =
+          time_launches([&] { launch_hop_any(prec, v.flags, v.red, a, c.block, st, nullptr, c.variant); }, st, ea, eb, 5);
       if (ms < best) {
         best = ms;
         pick = c;
@@ -199,7 +204,7 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
     BR_CUDA(cudaGetLastError());
     {
       std::lock_guard<std::mutex> lk(L->tune_mu);
-      L->tuned[key] = LaunchShape{pick.block, pick.nblk};
+      L->tuned[key] = LaunchShape{pick.block, pick.nblk, pick.variant};
     }
     keys.push_back(key);
   }
@@ -229,14 +234,14 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
     a.red.fin = FIN_STORE;
     const std::string key = "blas/" + std::to_string(op_) + "/" + std::to_string(prec) + "/" + std::to_string(vh) + "/" +
                             std::to_string(nrhs);
-    auto occ = [&](int block) {
+    auto occ = [&](int block, int) {
       int n = 0;
       launch_blas(op_, prec, px, a, block, st, &n);
       return n;
     };
     float best = 1e30f;
-    Candidate pick{128, 0};
-    for (const auto& c : candidates(vh, nrhs, occ)) {
+    Candidate pick{128, 0, 0};
+    for (const auto& c : candidates(vh, nrhs, 1, occ)) {
       a.nblk = c.nblk;
       const float ms = time_launches([&] { launch_blas(op_, prec, px, a, c.block, st); }, st, ea, eb, 5);
       if (ms < best) {
@@ -277,7 +282,8 @@ extern "C" int bridge_tune_table(bridge_lattice L, char* out, int n) {
   std::ostringstream s;
   {
     std::lock_guard<std::mutex> lk(L->tune_mu);
-    for (const auto& kv : L->tuned) s << kv.first << " " << kv.second.block << " " << kv.second.nblk << "\n";
+    for (const auto& kv : L->tuned)
+      s << kv.first << " " << kv.second.block << " " << kv.second.nblk << " " << kv.second.variant << "\n";
   }
   const std::string t = s.str();
   std::strncpy(out, t.c_str(), (size_t)n - 1);

@@ -231,6 +231,10 @@ WORKLOADS = {
     "clover_32x32x32x64": Workload("clover_32x32x32x64", (32, 32, 32, 64), "clover", 0.125, 1.0, 0.2, 2, 1, "gaussian", 1e-10),
     # Mid-size clover case (working set above L2, a few GB) for profiler captures.
     "clover_24x24x24x48": Workload("clover_24x24x24x48", (24, 24, 24, 48), "clover", 0.125, 1.0, 0.2, 4, 1, "gaussian", 1e-10),
+    # The same with twelve point sources, for profiler captures of the multi-RHS kernels.
+    "clover_24x24x24x48_12rhs": Workload(
+        "clover_24x24x24x48_12rhs", (24, 24, 24, 48), "clover", 0.125, 1.0, 0.2, 4, 12, "point", 1e-10, inner="f16"
+    ),
     # Twelve point sources on 48^3x96 clover with half-precision storage.
     "clover_48x48x48x96_12rhs": Workload(
         "clover_48x48x48x96_12rhs", (48, 48, 48, 96), "clover", 0.125, 1.0, 0.2, 3, 12, "point", 1e-10, inner="f16"
