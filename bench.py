@@ -572,6 +572,8 @@ def run_ours(args):
             },
             "roofline": roofline,
             "kernel_shares": shares,
+            "launch_shapes": {k: {"block": v[0], "site_blocks": v[1], "variant": v[2]}
+                              for k, v in api.bridge_tune_table(h).items() if k.startswith("hop/")},
             "deo": deo,
             "solve": solve,
             "serving": serving,

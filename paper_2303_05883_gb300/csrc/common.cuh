@@ -138,33 +138,90 @@ struct H16<P_BF16> {
   }
 };
 
+// -------------------------------------------------- read-only loads
+// ST = true marks data read exactly once per kernel (links, clover blocks,
+// the self / aux / dot-product vectors): it bypasses L1 so that L1 keeps the
+// neighbour spinors, each of which is read by eight sites.
+template <bool ST>
+BR_D float4 ldg4(const float4* p) {
+  if constexpr (ST) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+  } else {
+    return __ldg(p);
+  }
+}
+template <bool ST>
+BR_D double2 ldg4(const double2* p) {
+  if constexpr (ST) {
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+  } else {
+    return __ldg(p);
+  }
+}
+template <bool ST>
+BR_D uint4 ldg4(const uint4* p) {
+  if constexpr (ST) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+  } else {
+    return __ldg(p);
+  }
+}
+template <bool ST>
+BR_D uint2 ldg4(const uint2* p) {
+  if constexpr (ST) {
+    uint2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+  } else {
+    return __ldg(p);
+  }
+}
+template <bool ST>
+BR_D float ldg4(const float* p) {
+  if constexpr (ST) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+  } else {
+    return __ldg(p);
+  }
+}
+
 // ------------------------------------------------------- spinor access
 // s[k] with k = spin * 3 + colour.
-template <int P, bool NC = true>
+template <int P, bool NC = true, bool ST = false>
 BR_D void load_spinor(const char* base, long vh, uint32_t i, cx<typename Tr<P>::R> s[12]) {
   if constexpr (P == P_F64) {
     const double2* p = reinterpret_cast<const double2*>(base);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      double2 v = NC ? __ldg(p + k * vh + i) : p[k * vh + i];
+      double2 v = NC ? ldg4<ST>(p + k * vh + i) : p[k * vh + i];
       s[k] = {v.x, v.y};
     }
   } else if constexpr (P == P_F32) {
     const float4* p = reinterpret_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      float4 v = NC ? __ldg(p + k * vh + i) : p[k * vh + i];
+      float4 v = NC ? ldg4<ST>(p + k * vh + i) : p[k * vh + i];
       s[2 * k] = {v.x, v.y};
       s[2 * k + 1] = {v.z, v.w};
     }
   } else {
     const uint4* p = reinterpret_cast<const uint4*>(base);
     const float* sc = reinterpret_cast<const float*>(base + 48 * vh);
-    float scale = NC ? __ldg(sc + i) : sc[i];
+    float scale = NC ? ldg4<ST>(sc + i) : sc[i];
     H16<P> h;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      uint4 v = NC ? __ldg(p + k * vh + i) : p[k * vh + i];
+      uint4 v = NC ? ldg4<ST>(p + k * vh + i) : p[k * vh + i];
       float2 a = h.to2(v.x), b = h.to2(v.y), c = h.to2(v.z), d = h.to2(v.w);
       s[4 * k + 0] = {a.x * scale, a.y * scale};
       s[4 * k + 1] = {b.x * scale, b.y * scale};
@@ -239,18 +296,18 @@ BR_D void recon_row2(Link<R>& u) {
 }
 
 // base points at the block of one (parity, direction).
-template <int P>
+template <int P, bool ST = false>
 BR_D void load_link(const char* base, long vh, uint32_t i, Link<typename Tr<P>::R>& u) {
   if constexpr (P == P_F64) {
     const double2* p = reinterpret_cast<const double2*>(base);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      double2 v = __ldg(p + k * vh + i);
+      double2 v = ldg4<ST>(p + k * vh + i);
       u.m[k / 3][k % 3] = {v.x, v.y};
     }
   } else if constexpr (P == P_F32) {
     const float4* p = reinterpret_cast<const float4*>(base);
-    float4 a = __ldg(p + i), b = __ldg(p + vh + i), c = __ldg(p + 2 * vh + i);
+    float4 a = ldg4<ST>(p + i), b = ldg4<ST>(p + vh + i), c = ldg4<ST>(p + 2 * vh + i);
     u.m[0][0] = {a.x, a.y};
     u.m[0][1] = {a.z, a.w};
     u.m[0][2] = {b.x, b.y};
@@ -260,7 +317,7 @@ BR_D void load_link(const char* base, long vh, uint32_t i, Link<typename Tr<P>::
     recon_row2(u);
   } else {
     const uint2* p = reinterpret_cast<const uint2*>(base);
-    uint2 a = __ldg(p + i), b = __ldg(p + vh + i), c = __ldg(p + 2 * vh + i);
+    uint2 a = ldg4<ST>(p + i), b = ldg4<ST>(p + vh + i), c = ldg4<ST>(p + 2 * vh + i);
     H16<P> h;
     float2 t;
     t = h.to2(a.x); u.m[0][0] = {t.x, t.y};
@@ -278,13 +335,13 @@ BR_D void load_link(const char* base, long vh, uint32_t i, Link<typename Tr<P>::
 // [36 b + 0 .. 36 b + 5] diagonal, then 15 complex (row, col) pairs with
 // row > col in row-major order.  F16/BF16 store the 72 reals as 9 planes of
 // 8 halves (block 0 = halves 0..35, block 1 = halves 36..71).
-template <int P>
+template <int P, bool ST = false>
 BR_D void load_clover_block(const char* base, long vh, uint32_t i, int b, typename Tr<P>::R a[36]) {
   if constexpr (P == P_F64) {
     const double2* p = reinterpret_cast<const double2*>(base) + 18 * b * vh;
 #pragma unroll
     for (int k = 0; k < 18; ++k) {
-      double2 v = __ldg(p + k * vh + i);
+      double2 v = ldg4<ST>(p + k * vh + i);
       a[2 * k] = v.x;
       a[2 * k + 1] = v.y;
     }
@@ -292,7 +349,7 @@ BR_D void load_clover_block(const char* base, long vh, uint32_t i, int b, typena
     const float4* p = reinterpret_cast<const float4*>(base) + 9 * b * vh;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      float4 v = __ldg(p + k * vh + i);
+      float4 v = ldg4<ST>(p + k * vh + i);
       a[4 * k] = v.x;
       a[4 * k + 1] = v.y;
       a[4 * k + 2] = v.z;
@@ -306,7 +363,7 @@ BR_D void load_clover_block(const char* base, long vh, uint32_t i, int b, typena
     uint32_t w[20];
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      const uint4 v = __ldg(p + (4 * b + q) * vh + i);
+      const uint4 v = ldg4<ST>(p + (4 * b + q) * vh + i);
       w[4 * q] = v.x;
       w[4 * q + 1] = v.y;
       w[4 * q + 2] = v.z;
@@ -341,14 +398,14 @@ BR_D void hermitian6_apply(const R a[36], const cx<R> x[6], cx<R> y[6]) {
 }
 
 // y = A x with A the packed site term at site i (x and y must not alias).
-template <int P>
+template <int P, bool ST = false>
 BR_D void clover_apply(const char* base, long vh, uint32_t i, const cx<typename Tr<P>::R> x[12],
                        cx<typename Tr<P>::R> y[12]) {
   using R = typename Tr<P>::R;
 #pragma unroll
   for (int b = 0; b < 2; ++b) {
     R a[36];
-    load_clover_block<P>(base, vh, i, b, a);
+    load_clover_block<P, ST>(base, vh, i, b, a);
     hermitian6_apply<R>(a, x + 6 * b, y + 6 * b);
   }
 }
@@ -446,6 +503,28 @@ BR_HD uint32_t neighbour_rt(const Geom& g, uint32_t ih, const int c[4], uint32_t
   }
   return step > 0 ? f : b;
 }
+
+// Per-thread partial sums.  Kernels computing in FP32 accumulate their
+// per-site contributions with compensated (Kahan) FP32 additions and widen to
+// FP64 once per thread: the FP64 pipe of the GPU runs at a small fraction of
+// the FP32 rate, so no FP64 instruction is left in the site loop.
+template <class R>
+struct PartialSum {
+  R s = 0, c = 0;
+  BR_D void add(R x) {
+    const R y = x - c;
+    const R t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  BR_D double value() const { return (double)s - (double)c; }
+};
+template <>
+struct PartialSum<double> {
+  double s = 0;
+  BR_D void add(double x) { s += x; }
+  BR_D double value() const { return s; }
+};
 
 // ------------------------------------------------------ solver scalars
 // Complex BiCGStab scalars of one right-hand side, kept on the device so

@@ -37,6 +37,7 @@ struct HopArgs {
   int nblk;  // site blocks per right-hand side (grid = nblk * nrhs)
   double beta, s1, caux;
   double bc[4];
+  float betaf, s1f, cauxf, bcf[4];  // the same in FP32 for the FP32-math kernels
   // Field pointers address the block of the right parity for rhs 0; *_rs is
   // the byte stride between right-hand sides.
   char* out;
@@ -100,16 +101,16 @@ BR_D void reconstruct(const cx<R> u[2][3], cx<R> acc[12]) {
 }
 
 // One hop: psi at half-lattice site nb of the input, link block lb at index li.
-template <int P, int MU, bool FWD>
-BR_D void hop_one(const char* in, const char* lb, long vh, uint32_t nb, uint32_t li, bool wraps, double bc,
-                  cx<typename Tr<P>::R> acc[12]) {
+template <int P, int MU, bool FWD, bool ST>
+BR_D void hop_one(const char* in, const char* lb, long vh, uint32_t nb, uint32_t li, bool wraps,
+                  typename Tr<P>::R bc, cx<typename Tr<P>::R> acc[12]) {
   using R = typename Tr<P>::R;
   cx<R> h[2][3];
   if constexpr (Tr<P>::half) {
     // project the stored values, then apply the per-site scale and the
     // boundary phase to the 12 projected components only
     cx<float> psi[12];
-    const float sc = load_spinor_unscaled<P>(in, vh, nb, psi) * (wraps ? (float)bc : 1.0f);
+    const float sc = load_spinor_unscaled<P>(in, vh, nb, psi) * (wraps ? bc : 1.0f);
     project<R, MU, FWD>(psi, h);
 #pragma unroll
     for (int k = 0; k < 2; ++k)
@@ -122,15 +123,14 @@ BR_D void hop_one(const char* in, const char* lb, long vh, uint32_t nb, uint32_t
       project<R, MU, FWD>(psi, h);
     }
     if (wraps) {
-      const R ph = (R)bc;
 #pragma unroll
       for (int k = 0; k < 2; ++k)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) h[k][c] = ph * h[k][c];
+        for (int c = 0; c < 3; ++c) h[k][c] = bc * h[k][c];
     }
   }
   Link<R> U;
-  load_link<P>(lb, vh, li, U);
+  load_link<P, ST>(lb, vh, li, U);
   cx<R> u[2][3];
 #pragma unroll
   for (int k = 0; k < 2; ++k)
@@ -144,21 +144,33 @@ BR_D void hop_one(const char* in, const char* lb, long vh, uint32_t nb, uint32_t
   reconstruct<R, MU, FWD>(u, acc);
 }
 
-template <int P, int MU>
+template <class R>
+BR_HD R pick(double d, float f) {
+  if constexpr (sizeof(R) == sizeof(double)) {
+    return d;
+  } else {
+    return f;
+  }
+}
+
+template <int P, int MU, bool ST>
 BR_D void hop_dir(const HopArgs& a, const char* in, const char* g_out, const char* g_in, long lbb, uint32_t ih,
                   const int c[4], uint32_t xh, cx<typename Tr<P>::R> acc[12]) {
+  using R = typename Tr<P>::R;
   uint32_t f, b;
   bool wf, wb;
   neighbours<MU>(a.g, ih, c, xh, f, b, wf, wb);
+  const R bc = pick<R>(a.bc[MU], a.bcf[MU]);
   // forward: link U_mu(x) lives at x (output parity); backward: U_mu(x - mu) at x - mu.
-  hop_one<P, MU, true>(in, g_out + MU * lbb, a.g.vh, f, ih, wf, a.bc[MU], acc);
-  hop_one<P, MU, false>(in, g_in + MU * lbb, a.g.vh, b, b, wb, a.bc[MU], acc);
+  hop_one<P, MU, true, ST>(in, g_out + MU * lbb, a.g.vh, f, ih, wf, bc, acc);
+  hop_one<P, MU, false, ST>(in, g_in + MU * lbb, a.g.vh, b, b, wb, bc, acc);
 }
 
 // MINB: minimum resident 256-thread blocks per SM the compiler must allow
-// (1 = no register cap, 3 = <= 80 registers, 4 = <= 64 registers); the
-// autotuner picks the variant per kernel and lattice.
-template <int P, int FL, int RED, int MINB = 1>
+// (1 = no register cap, 3 = <= 80 registers, 4 = <= 64 registers); ST:
+// load the read-once operands around L1 (see ldg4).  The autotuner picks
+// the variant per kernel and lattice.
+template <int P, int FL, int RED, int MINB = 1, bool ST = false>
 __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
   using R = typename Tr<P>::R;
   const int nrhs = a.nrhs;
@@ -166,9 +178,8 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
   const int sb = blockIdx.x / nrhs;
   const long vh = a.g.vh;
   constexpr int NV = RED == R_NORM ? 1 : RED == R_DOT_A ? 2 : 3;
-  double rv[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) rv[k] = 0.0;
+  PartialSum<R> ps[NV];
+  const R beta = pick<R>(a.beta, a.betaf), s1 = pick<R>(a.s1, a.s1f), ca = pick<R>(a.caux, a.cauxf);
   const bool skip = a.red.check_done && a.red.sc != nullptr && a.red.sc[rhs].done != RUNNING;
   if (!skip) {
     const int p = a.out_parity;
@@ -184,34 +195,31 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
       cx<R> acc[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = czero<R>();
-      hop_dir<P, 0>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
-      hop_dir<P, 1>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
-      hop_dir<P, 2>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
-      hop_dir<P, 3>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
-      const R beta = (R)a.beta;
+      hop_dir<P, 0, ST>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+      hop_dir<P, 1, ST>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+      hop_dir<P, 2, ST>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+      hop_dir<P, 3, ST>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = beta * acc[k];
       if (FL & F_AUX) {
         cx<R> x[12];
-        load_spinor<P>(a.aux + rhs * a.aux_rs, vh, ih, x);
-        const R ca = (R)a.caux;
+        load_spinor<P, true, ST>(a.aux + rhs * a.aux_rs, vh, ih, x);
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = acc[k] + ca * x[k];
       }
       cx<R> v[12];
       if (FL & F_E_CLOV) {
-        clover_apply<P>(a.clovE + p * cbb, vh, ih, acc, v);
+        clover_apply<P, ST>(a.clovE + p * cbb, vh, ih, acc, v);
       } else {
 #pragma unroll
         for (int k = 0; k < 12; ++k) v[k] = acc[k];
       }
       cx<R> s[12];
       if (FL & F_SELF) {
-        load_spinor<P>(a.self + rhs * a.self_rs, vh, ih, s);
-        const R s1 = (R)a.s1;
+        load_spinor<P, true, ST>(a.self + rhs * a.self_rs, vh, ih, s);
         if (FL & F_SELF_CLOV) {
           cx<R> ms[12];
-          clover_apply<P>(a.clovM + p * cbb, vh, ih, s, ms);
+          clover_apply<P, ST>(a.clovM + p * cbb, vh, ih, s, ms);
 #pragma unroll
           for (int k = 0; k < 12; ++k) v[k] = v[k] + s1 * ms[k];
         } else {
@@ -224,15 +232,15 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
         R n = 0;
 #pragma unroll
         for (int k = 0; k < 12; ++k) n += v[k].r * v[k].r + v[k].i * v[k].i;
-        rv[0] += (double)n;
+        ps[0].add(n);
       } else if (RED == R_DOT_A) {
         cx<R> w[12];
-        load_spinor<P>(a.avec + rhs * a.avec_rs, vh, ih, w);
+        load_spinor<P, true, ST>(a.avec + rhs * a.avec_rs, vh, ih, w);
         cx<R> d = czero<R>();
 #pragma unroll
         for (int k = 0; k < 12; ++k) d = d + cmul_conj(w[k], v[k]);
-        rv[0] += (double)d.r;
-        rv[1] += (double)d.i;
+        ps[0].add(d.r);
+        ps[1].add(d.i);
       } else if (RED == R_TS) {
         cx<R> d = czero<R>();
         R n = 0;
@@ -241,20 +249,26 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
           d = d + cmul_conj(v[k], s[k]);
           n += v[k].r * v[k].r + v[k].i * v[k].i;
         }
-        rv[0] += (double)d.r;
-        rv[1] += (double)d.i;
-        rv[2] += (double)n;
+        ps[0].add(d.r);
+        ps[1].add(d.i);
+        ps[2].add(n);
       }
     }
   }
-  if (RED != R_NONE) reduce_finalize<NV>(a.red, rhs, sb, a.nblk, nrhs, rv);
+  if (RED != R_NONE) {
+    double rv[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) rv[k] = ps[k].value();
+    reduce_finalize<NV>(a.red, rhs, sb, a.nblk, nrhs, rv);
+  }
 }
 
 // Launch with the given block size on a stream; returns false for a
 // (flags, reduction) pair that is not instantiated.  With occ != null,
 // nothing is launched: *occ receives the resident blocks per SM instead.
-// variant: register budget (0 = none, 1 = 80, 2 = 64 registers); only the
-// kernels of the Schur passes and D_eo have the capped variants.
+// variant v in [0, 6): register budget {none, 80, 64}[v % 3] and, for v >= 3,
+// read-once operands loaded around L1; only the kernels of the Schur passes,
+// D_eo and the FP64 residual have variants other than 0.
 template <int P>
 bool launch_hop(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ = nullptr, int variant = 0);
 template <>

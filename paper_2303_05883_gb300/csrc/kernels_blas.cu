@@ -10,9 +10,8 @@ namespace bridge {
   for (uint32_t ih = (uint32_t)(blockIdx.x / a.nrhs) * blockDim.x + threadIdx.x; ih < (vh_); ih += (uint32_t)(nblk_) * blockDim.x)
 
 template <class R>
-BR_D cx<R> scal(double re, double im, cx<R> v) {  // (re + i im) * v in precision R
-  const R a = (R)re, b = (R)im;
-  return {a * v.r - b * v.i, a * v.i + b * v.r};
+BR_D cx<R> scal(cx<R> z, cx<R> v) {  // z * v
+  return {z.r * v.r - z.i * v.i, z.r * v.i + z.i * v.r};
 }
 
 // ------------------------------------------------------------- BiCGStab
@@ -20,7 +19,7 @@ template <int P, int PX>
 __global__ void __launch_bounds__(256) k_blas_init(const BlasArgs a) {
   using R = typename Tr<P>::R;
   const int rhs = blockIdx.x % a.nrhs, sb = blockIdx.x / a.nrhs;
-  double rv[1] = {0.0};
+  PartialSum<R> ps;
   BR_SITE_LOOP(a.vh, a.nblk) {
     cx<R> b[12], z[12];
     load_spinor<P>(a.b + rhs * a.b_rs, a.vh, ih, b);
@@ -34,8 +33,9 @@ __global__ void __launch_bounds__(256) k_blas_init(const BlasArgs a) {
     store_spinor<P>(a.rhat + rhs * a.rhat_rs, a.vh, ih, b);
     store_spinor<P>(a.p + rhs * a.p_rs, a.vh, ih, b);
     store_spinor<PX>(a.x + rhs * a.x_rs, a.vh, ih, z);
-    rv[0] += (double)n;
+    ps.add(n);
   }
+  double rv[1] = {ps.value()};
   reduce_finalize<1>(a.red, rhs, sb, a.nblk, a.nrhs, rv);
 }
 
@@ -45,13 +45,13 @@ __global__ void __launch_bounds__(256) k_blas_s(const BlasArgs a) {
   const int rhs = blockIdx.x % a.nrhs;
   const BiCGScalars* q = a.red.sc + rhs;
   if (q->done != RUNNING) return;
-  const double ar = q->alpha_r, ai = q->alpha_i;
+  const cx<R> al = {(R)q->alpha_r, (R)q->alpha_i};
   BR_SITE_LOOP(a.vh, a.nblk) {
     cx<R> r[12], v[12];
     load_spinor<P, false>(a.r + rhs * a.r_rs, a.vh, ih, r);
     load_spinor<P, false>(a.v + rhs * a.v_rs, a.vh, ih, v);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) r[k] = r[k] - scal<R>(ar, ai, v[k]);
+    for (int k = 0; k < 12; ++k) r[k] = r[k] - scal<R>(al, v[k]);
     store_spinor<P>(a.s + rhs * a.s_rs, a.vh, ih, r);
   }
 }
@@ -61,20 +61,20 @@ __global__ void __launch_bounds__(256) k_blas_xr(const BlasArgs a) {
   using R = typename Tr<P>::R;
   const int rhs = blockIdx.x % a.nrhs, sb = blockIdx.x / a.nrhs;
   const BiCGScalars* q = a.red.sc + rhs;
-  double rv[3] = {0.0, 0.0, 0.0};
+  PartialSum<R> ps[3];
   if (q->done == RUNNING) {
-    const double ar = q->alpha_r, ai = q->alpha_i, wr = q->omega_r, wi = q->omega_i;
+    const cx<R> al = {(R)q->alpha_r, (R)q->alpha_i}, om = {(R)q->omega_r, (R)q->omega_i};
     BR_SITE_LOOP(a.vh, a.nblk) {
       cx<R> x[12], p[12], s[12], t[12];
       load_spinor<PX, false>(a.x + rhs * a.x_rs, a.vh, ih, x);
       load_spinor<P, false>(a.p + rhs * a.p_rs, a.vh, ih, p);
       load_spinor<P, false>(a.s + rhs * a.s_rs, a.vh, ih, s);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) x[k] = x[k] + scal<R>(ar, ai, p[k]) + scal<R>(wr, wi, s[k]);
+      for (int k = 0; k < 12; ++k) x[k] = x[k] + scal<R>(al, p[k]) + scal<R>(om, s[k]);
       store_spinor<PX>(a.x + rhs * a.x_rs, a.vh, ih, x);
       load_spinor<P, false>(a.t + rhs * a.t_rs, a.vh, ih, t);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) s[k] = s[k] - scal<R>(wr, wi, t[k]);  // new r
+      for (int k = 0; k < 12; ++k) s[k] = s[k] - scal<R>(om, t[k]);  // new r
       store_spinor<P>(a.r + rhs * a.r_rs, a.vh, ih, s);
       load_spinor<P, false>(a.rhat + rhs * a.rhat_rs, a.vh, ih, p);
       cx<R> d = czero<R>();
@@ -84,11 +84,12 @@ __global__ void __launch_bounds__(256) k_blas_xr(const BlasArgs a) {
         d = d + cmul_conj(p[k], s[k]);
         n += s[k].r * s[k].r + s[k].i * s[k].i;
       }
-      rv[0] += (double)d.r;
-      rv[1] += (double)d.i;
-      rv[2] += (double)n;
+      ps[0].add(d.r);
+      ps[1].add(d.i);
+      ps[2].add(n);
     }
   }
+  double rv[3] = {ps[0].value(), ps[1].value(), ps[2].value()};
   reduce_finalize<3>(a.red, rhs, sb, a.nblk, a.nrhs, rv);
 }
 
@@ -98,14 +99,14 @@ __global__ void __launch_bounds__(256) k_blas_p(const BlasArgs a) {
   const int rhs = blockIdx.x % a.nrhs;
   const BiCGScalars* q = a.red.sc + rhs;
   if (q->done != RUNNING) return;
-  const double br = q->beta_r, bi = q->beta_i, wr = q->omega_r, wi = q->omega_i;
+  const cx<R> be = {(R)q->beta_r, (R)q->beta_i}, om = {(R)q->omega_r, (R)q->omega_i};
   BR_SITE_LOOP(a.vh, a.nblk) {
     cx<R> r[12], p[12], v[12];
     load_spinor<P, false>(a.r + rhs * a.r_rs, a.vh, ih, r);
     load_spinor<P, false>(a.p + rhs * a.p_rs, a.vh, ih, p);
     load_spinor<P, false>(a.v + rhs * a.v_rs, a.vh, ih, v);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) p[k] = r[k] + scal<R>(br, bi, p[k] - scal<R>(wr, wi, v[k]));
+    for (int k = 0; k < 12; ++k) p[k] = r[k] + scal<R>(be, p[k] - scal<R>(om, v[k]));
     store_spinor<P>(a.p + rhs * a.p_rs, a.vh, ih, p);
   }
 }
@@ -217,15 +218,16 @@ template <int P>
 __global__ void __launch_bounds__(256) k_norm2(const CopyArgs a) {
   using R = typename Tr<P>::R;
   const int rhs = blockIdx.x % a.nrhs, sb = blockIdx.x / a.nrhs;
-  double rv[1] = {0.0};
+  PartialSum<R> ps;
   BR_SITE_LOOP(a.vh, a.nblk) {
     cx<R> s[12];
     load_spinor<P>(a.src + rhs * a.src_rs, a.vh, ih, s);
     R n = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) n += s[k].r * s[k].r + s[k].i * s[k].i;
-    rv[0] += (double)n;
+    ps.add(n);
   }
+  double rv[1] = {ps.value()};
   reduce_finalize<1>(a.red, rhs, sb, a.nblk, a.nrhs, rv);
 }
 

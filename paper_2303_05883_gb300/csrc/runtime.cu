@@ -449,7 +449,8 @@ void clover_site(bridge_lattice_s* L, int prec, bool inverse, double kcsw, int p
 
 bool hop_has_variants(int flags, int red) {
   return (flags == 0 && red == R_NONE) || (flags == F_E_CLOV && red == R_NONE) ||
-         ((flags == F_SELF || flags == (F_SELF | F_E_CLOV)) && (red == R_DOT_A || red == R_TS));
+         ((flags == F_SELF || flags == (F_SELF | F_E_CLOV)) && (red == R_DOT_A || red == R_TS)) ||
+         (flags == (F_AUX | F_SELF | F_SELF_CLOV) && red == R_NORM);
 }
 
 bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ,

@@ -158,7 +158,9 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
     int flags, red;
   };
   const int fE = clov ? F_E_CLOV : 0;
-  const HopVariant hv[] = {{0, R_NONE}, {fE, R_NONE}, {F_SELF | fE, R_DOT_A}, {F_SELF | fE, R_TS}, {F_AUX | fE, R_NONE}};
+  std::vector<HopVariant> hv = {{0, R_NONE}, {fE, R_NONE}, {F_SELF | fE, R_DOT_A}, {F_SELF | fE, R_TS}, {F_AUX | fE, R_NONE}};
+  if (prec == P_F64 && clov) hv.push_back({F_AUX | F_SELF | F_SELF_CLOV, R_NORM});
+  std::shared_ptr<CloverSet> keep_cs = cs;
   for (const auto& v : hv) {
     HopArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -181,6 +183,8 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
     a.avec_rs = f2.rs;
     a.gauge = gauge_ptr(L, prec);
     if (v.flags & F_E_CLOV) a.clovE = clover_ptr(L, *cs, prec, true);
+    if (v.flags & F_SELF_CLOV) a.clovM = clover_ptr(L, *cs, prec, false);
+    if (v.flags & F_SELF_CLOV) a.s1 = -1.0;
     a.red = red;
     a.red.fin = v.red == R_NONE ? FIN_NONE : FIN_STORE;
     const std::string key = "hop/" + std::to_string(prec) + "/" + std::to_string(v.flags) + "/" + std::to_string(v.red) +
@@ -192,7 +196,7 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
     };
     float best = 1e30f;
     Candidate pick{128, 0, 0};
-    for (const auto& c : candidates(vh, nrhs, hop_has_variants(v.flags, v.red) ? 3 : 1, occ)) {
+    for (const auto& c : candidates(vh, nrhs, hop_has_variants(v.flags, v.red) ? 6 : 1, occ)) {
       a.nblk = c.nblk;
       const float ms =
           time_launches([&] { launch_hop_any(prec, v.flags, v.red, a, c.block, st, nullptr, c.variant); }, st, ea, eb, 5);
