@@ -218,9 +218,16 @@ void bridge_solver_defaults(bridge_solver* s);
  * naming a file, results are appended there and loaded by later
  * bridge_lattice_create calls on the same device model.  Synchronous. */
 int bridge_tune(bridge_lattice lat, const bridge_op* op, int prec, int nrhs);
-/* The current shape table as text ("key block nblk" per line) in out[n];
- * returns the full length. */
+/* The current shape table as text ("key block nblk variant" per line) in
+ * out[n]; returns the full length. */
 int bridge_tune_table(bridge_lattice lat, char* out, int n);
+/* Set one entry of the shape table (key as printed by bridge_tune_table):
+ * block in [64, 256] (multiple of 32), nblk >= 1 site blocks per
+ * right-hand-side group, variant in [0, 8] (register budget / read-once
+ * loads for 0-5, 2-4 right-hand sides per thread for 6-8; a variant a
+ * kernel does not have falls back to 0).  Lets tests and users pin a launch
+ * shape; EINVAL for values out of range. */
+int bridge_tune_set(bridge_lattice lat, const char* key, int block, int nblk, int variant);
 
 /* ---- fields in the GPU layout (resident data) ------------------------------- */
 

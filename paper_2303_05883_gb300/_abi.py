@@ -104,6 +104,7 @@ SIGNATURES = {
     "bridge_launch_count": (c_long, []),
     "bridge_tune": (c_int, [_h, POINTER(bridge_op), c_int, c_int]),
     "bridge_tune_table": (c_int, [_h, c_char_p, c_int]),
+    "bridge_tune_set": (c_int, [_h, c_char_p, c_int, c_int, c_int]),
     "bridge_debug_neighbours": (c_int, [POINTER(c_int), c_int, c_long, POINTER(c_long), POINTER(c_int)]),
 }
 

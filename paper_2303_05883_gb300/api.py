@@ -308,6 +308,10 @@ def bridge_tune_table(lat) -> dict:
     return out
 
 
+def bridge_tune_set(lat, key: str, block: int, nblk: int, variant: int) -> None:
+    check(_abi.load().bridge_tune_set(lat, key.encode(), int(block), int(nblk), int(variant)), "bridge_tune_set")
+
+
 def bridge_strerror(status: int) -> str:
     return _abi.load().bridge_strerror(int(status)).decode()
 

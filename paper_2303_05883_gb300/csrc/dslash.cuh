@@ -263,12 +263,195 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// NR right-hand sides per thread.  With several right-hand sides the stencil
+// is limited by instruction issue rather than by memory, so one thread
+// computes one site for NR consecutive right-hand sides and shares among
+// them the neighbour indices, the link loads with row-3 reconstruction and
+// the clover blocks.  Right-hand sides [r0, r0 + nr) of group g; a
+// right-hand side whose solve has finished is skipped (uniform per block).
+template <int P, int MU, bool FWD, int NR>
+BR_D void hop_one_mr(const char* in, long in_rs, const bool live[NR], const char* lb, long vh, uint32_t nb,
+                     uint32_t li, bool wraps, typename Tr<P>::R bc, cx<typename Tr<P>::R> acc[NR][12]) {
+  using T = typename Tr<P>::R;
+  Link<T> U;
+  load_link<P, true>(lb, vh, li, U);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (!live[r]) continue;
+    cx<T> h[2][3];
+    const char* src = in + r * in_rs;
+    if constexpr (Tr<P>::half) {
+      cx<float> psi[12];
+      const float sc = load_spinor_unscaled<P>(src, vh, nb, psi) * (wraps ? bc : 1.0f);
+      project<T, MU, FWD>(psi, h);
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[k][c] = sc * h[k][c];
+    } else {
+      {
+        cx<T> psi[12];
+        load_spinor<P>(src, vh, nb, psi);
+        project<T, MU, FWD>(psi, h);
+      }
+      if (wraps) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) h[k][c] = bc * h[k][c];
+      }
+    }
+    cx<T> u[2][3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (FWD)
+          u[k][q] = U.m[q][0] * h[k][0] + U.m[q][1] * h[k][1] + U.m[q][2] * h[k][2];
+        else
+          u[k][q] = cmul_conj(U.m[0][q], h[k][0]) + cmul_conj(U.m[1][q], h[k][1]) + cmul_conj(U.m[2][q], h[k][2]);
+      }
+    reconstruct<T, MU, FWD>(u, acc[r]);
+  }
+}
+
+template <int P, int MU, int NR>
+BR_D void hop_dir_mr(const HopArgs& a, const char* in, const bool live[NR], const char* g_out, const char* g_in,
+                     long lbb, uint32_t ih, const int c[4], uint32_t xh, cx<typename Tr<P>::R> acc[NR][12]) {
+  using T = typename Tr<P>::R;
+  uint32_t f, b;
+  bool wf, wb;
+  neighbours<MU>(a.g, ih, c, xh, f, b, wf, wb);
+  const T bc = pick<T>(a.bc[MU], a.bcf[MU]);
+  hop_one_mr<P, MU, true, NR>(in, a.in_rs, live, g_out + MU * lbb, a.g.vh, f, ih, wf, bc, acc);
+  hop_one_mr<P, MU, false, NR>(in, a.in_rs, live, g_in + MU * lbb, a.g.vh, b, b, wb, bc, acc);
+}
+
+template <int P, int FL, int RED, int NR>
+__global__ void __launch_bounds__(256) hop_kernel_mr(const HopArgs a) {
+  using T = typename Tr<P>::R;
+  const int ng = (a.nrhs + NR - 1) / NR;
+  const int g = blockIdx.x % ng;
+  const int sb = blockIdx.x / ng;
+  const int r0 = g * NR;
+  const long vh = a.g.vh;
+  constexpr int NV = RED == R_NORM ? 1 : RED == R_DOT_A ? 2 : 3;
+  bool live[NR];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    live[r] = (r0 + r < a.nrhs) &&
+              !(a.red.check_done && a.red.sc != nullptr && a.red.sc[r0 + r].done != RUNNING);
+    any = any || live[r];
+  }
+  PartialSum<T> ps[NR][NV];
+  const T beta = pick<T>(a.beta, a.betaf), s1 = pick<T>(a.s1, a.s1f), ca = pick<T>(a.caux, a.cauxf);
+  if (any) {
+    const int p = a.out_parity;
+    const long lbb = link_block_bytes(P, vh), cbb = clover_block_bytes(P, vh);
+    const char* g_out = a.gauge + (long)p * 4 * lbb;
+    const char* g_in = a.gauge + (long)(1 - p) * 4 * lbb;
+    const char* in = a.in + r0 * a.in_rs;
+    const uint32_t stride = (uint32_t)a.nblk * blockDim.x;
+    for (uint32_t ih = sb * blockDim.x + threadIdx.x; ih < (uint32_t)vh; ih += stride) {
+      int c[4];
+      uint32_t xh;
+      site_coords(a.g, ih, p, c, xh);
+      cx<T> acc[NR][12];
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[r][k] = czero<T>();
+      hop_dir_mr<P, 0, NR>(a, in, live, g_out, g_in, lbb, ih, c, xh, acc);
+      hop_dir_mr<P, 1, NR>(a, in, live, g_out, g_in, lbb, ih, c, xh, acc);
+      hop_dir_mr<P, 2, NR>(a, in, live, g_out, g_in, lbb, ih, c, xh, acc);
+      hop_dir_mr<P, 3, NR>(a, in, live, g_out, g_in, lbb, ih, c, xh, acc);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[r][k] = beta * acc[r][k];
+        if ((FL & F_AUX) && live[r]) {
+          cx<T> x[12];
+          load_spinor<P, true, true>(a.aux + (r0 + r) * a.aux_rs, vh, ih, x);
+#pragma unroll
+          for (int k = 0; k < 12; ++k) acc[r][k] = acc[r][k] + ca * x[k];
+        }
+      }
+      if (FL & F_E_CLOV) {
+        // one load of each 6x6 block, applied to every right-hand side
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          T m[36];
+          load_clover_block<P, true>(a.clovE + p * cbb, vh, ih, b, m);
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            cx<T> y[6];
+            hermitian6_apply<T>(m, acc[r] + 6 * b, y);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[r][6 * b + k] = y[k];
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (!live[r]) continue;
+        cx<T> s[12];
+        if (FL & F_SELF) {
+          load_spinor<P, true, true>(a.self + (r0 + r) * a.self_rs, vh, ih, s);
+#pragma unroll
+          for (int k = 0; k < 12; ++k) acc[r][k] = acc[r][k] + s1 * s[k];
+        }
+        store_spinor<P>(a.out + (r0 + r) * a.out_rs, vh, ih, acc[r]);
+        if (RED == R_NORM) {
+          T n = 0;
+#pragma unroll
+          for (int k = 0; k < 12; ++k) n += acc[r][k].r * acc[r][k].r + acc[r][k].i * acc[r][k].i;
+          ps[r][0].add(n);
+        } else if (RED == R_DOT_A) {
+          cx<T> w[12];
+          load_spinor<P, true, true>(a.avec + (r0 + r) * a.avec_rs, vh, ih, w);
+          cx<T> d = czero<T>();
+#pragma unroll
+          for (int k = 0; k < 12; ++k) d = d + cmul_conj(w[k], acc[r][k]);
+          ps[r][0].add(d.r);
+          ps[r][1].add(d.i);
+        } else if (RED == R_TS) {
+          cx<T> d = czero<T>();
+          T n = 0;
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            d = d + cmul_conj(acc[r][k], s[k]);
+            n += acc[r][k].r * acc[r][k].r + acc[r][k].i * acc[r][k].i;
+          }
+          ps[r][0].add(d.r);
+          ps[r][1].add(d.i);
+          ps[r][2].add(n);
+        }
+      }
+    }
+  }
+  if (RED != R_NONE) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r0 + r >= a.nrhs) break;  // uniform per block
+      double rv[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) rv[k] = ps[r][k].value();
+      block_partial<NV>(a.red, r0 + r, sb, a.nblk, rv);
+    }
+    grid_finish<NV>(a.red, a.nblk, a.nrhs);
+  }
+}
+
 // Launch with the given block size on a stream; returns false for a
 // (flags, reduction) pair that is not instantiated.  With occ != null,
 // nothing is launched: *occ receives the resident blocks per SM instead.
 // variant v in [0, 6): register budget {none, 80, 64}[v % 3] and, for v >= 3,
-// read-once operands loaded around L1; only the kernels of the Schur passes,
-// D_eo and the FP64 residual have variants other than 0.
+// read-once operands loaded around L1; v in {6, 7, 8}: 2, 3 or 4 right-hand
+// sides per thread (hop_kernel_mr; grid = nblk x ceil(nrhs / NR)).  Only the
+// kernels of the Schur passes, D_eo and the FP64 residual have variants
+// other than 0, and only FP32/FP16/BF16 have the multi-RHS ones.
 template <int P>
 bool launch_hop(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ = nullptr, int variant = 0);
 template <>
@@ -280,5 +463,7 @@ bool launch_hop<P_F16>(int flags, int red, const HopArgs& a, int block, cudaStre
 template <>
 bool launch_hop<P_BF16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ, int variant);
 bool hop_has_variants(int flags, int red);
+// right-hand sides per thread of a variant (1 for v < 6)
+inline int hop_variant_rpt(int variant) { return variant >= 6 ? variant - 4 : 1; }
 
 }  // namespace bridge

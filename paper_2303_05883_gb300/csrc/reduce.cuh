@@ -129,16 +129,25 @@ __device__ __forceinline__ void block_sum(double v[NV], double (*sh)[4]) {
   }
 }
 
-// Block partial -> global partial; the last block reduces and finalizes.
-// Must be reached by every thread of every block.
+// Block partial of one right-hand side -> its slot in ra.partials.
+// Must be reached by every thread of the block.
 template <int NV>
-__device__ void reduce_finalize(const RedArgs& ra, int rhs, int sb, int nblk, int nrhs, double v[NV]) {
+__device__ __forceinline__ void block_partial(const RedArgs& ra, int rhs, int sb, int nblk, double v[NV]) {
   __shared__ double sh[32][4];
-  __shared__ int is_last;
   block_sum<NV>(v, sh);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0)
 #pragma unroll
     for (int k = 0; k < NV; ++k) ra.partials[((long)rhs * nblk + sb) * 4 + k] = v[k];
+}
+
+// After this block's partials are written: take a ticket; the last block of
+// the grid sums every right-hand side's partials in a fixed order and runs
+// the finalizer.  Must be reached by every thread of every block.
+template <int NV>
+__device__ void grid_finish(const RedArgs& ra, int nblk, int nrhs) {
+  __shared__ double sh[32][4];
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
     __threadfence();
     unsigned t = atomicAdd(ra.counter, 1u);
     is_last = (t == gridDim.x - 1);
@@ -163,6 +172,14 @@ __device__ void reduce_finalize(const RedArgs& ra, int rhs, int sb, int nblk, in
     __syncthreads();
   }
   if (threadIdx.x == 0) *ra.counter = 0u;
+}
+
+// Block partial -> global partial; the last block reduces and finalizes.
+// Must be reached by every thread of every block.
+template <int NV>
+__device__ void reduce_finalize(const RedArgs& ra, int rhs, int sb, int nblk, int nrhs, double v[NV]) {
+  block_partial<NV>(ra, rhs, sb, nblk, v);
+  grid_finish<NV>(ra, nblk, nrhs);
 }
 
 }  // namespace bridge

@@ -456,13 +456,17 @@ bool hop_has_variants(int flags, int red) {
 bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ,
                     int variant) {
   if (!hop_has_variants(flags, red)) variant = 0;
-  switch (prec) {
-    case P_F64: return launch_hop<P_F64>(flags, red, a, block, st, occ, variant);
-    case P_F32: return launch_hop<P_F32>(flags, red, a, block, st, occ, variant);
-    case P_F16: return launch_hop<P_F16>(flags, red, a, block, st, occ, variant);
-    case P_BF16: return launch_hop<P_BF16>(flags, red, a, block, st, occ, variant);
+  for (;;) {
+    bool ok = false;
+    switch (prec) {
+      case P_F64: ok = launch_hop<P_F64>(flags, red, a, block, st, occ, variant); break;
+      case P_F32: ok = launch_hop<P_F32>(flags, red, a, block, st, occ, variant); break;
+      case P_F16: ok = launch_hop<P_F16>(flags, red, a, block, st, occ, variant); break;
+      case P_BF16: ok = launch_hop<P_BF16>(flags, red, a, block, st, occ, variant); break;
+    }
+    if (ok || variant == 0) return ok;
+    variant = 0;  // this kernel has no such variant (e.g. several RHS per thread in FP64)
   }
-  return false;
 }
 
 }  // namespace bridge

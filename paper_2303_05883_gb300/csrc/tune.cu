@@ -99,20 +99,36 @@ struct Candidate {
 };
 
 // Block sizes x {persistent grid, 2x persistent, one site per thread} for
-// each register-budget variant; occ(block, variant) gives resident blocks/SM.
-static std::vector<Candidate> candidates(long vh, int nrhs, int nvariants, const std::function<int(int, int)>& occ) {
+// each kernel variant; occ(block, variant) gives resident blocks/SM.  A
+// variant with NR right-hand sides per thread launches ceil(nrhs / NR)
+// groups of site blocks.
+static std::vector<Candidate> candidates(long vh, int nrhs, const std::vector<int>& variants,
+                                         const std::function<int(int, int)>& occ) {
   std::vector<Candidate> out;
-  for (int v = 0; v < nvariants; ++v)
+  for (int v : variants) {
+    const int groups = (nrhs + hop_variant_rpt(v) - 1) / hop_variant_rpt(v);
     for (int block : {64, 128, 256}) {
       const long cover = (vh + block - 1) / block;
       const int per_sm = std::max(1, occ(block, v));
       for (int m : {1, 2}) {
-        long n = std::max<long>(1, (long)sm_count() * per_sm * m / std::max(1, nrhs));
+        long n = std::max<long>(1, (long)sm_count() * per_sm * m / std::max(1, groups));
         if (n < cover) out.push_back({block, (int)n, v});
       }
       out.push_back({block, (int)cover, v});
     }
+  }
   return out;
+}
+
+static std::vector<int> hop_variants(int prec, int flags, int red, int nrhs) {
+  std::vector<int> v = {0};
+  if (!hop_has_variants(flags, red)) return v;
+  for (int k = 1; k < 6; ++k) v.push_back(k);
+  const bool residual = (flags & F_SELF_CLOV) != 0;
+  if (prec != P_F64 && !residual)
+    for (int k = 6; k < 9; ++k)
+      if (hop_variant_rpt(k) <= nrhs) v.push_back(k);
+  return v;
 }
 
 // Tune the hop variants and vector kernels that a solve with this operator,
@@ -146,6 +162,7 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
   red.sc = reinterpret_cast<BiCGScalars*>(scal.ptr);
   red.result = reinterpret_cast<double*>(result.ptr);
   red.check_done = 0;  // store-only finalizers below: scratch scalars never change
+  const bool verbose = std::getenv("BRIDGE_TUNE_VERBOSE") != nullptr;
   cudaEvent_t ea, eb;
   BR_CUDA(cudaEventCreate(&ea));
   BR_CUDA(cudaEventCreate(&eb));
@@ -196,10 +213,13 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
     };
     float best = 1e30f;
     Candidate pick{128, 0, 0};
-    for (const auto& c : candidates(vh, nrhs, hop_has_variants(v.flags, v.red) ? 6 : 1, occ)) {
+    for (const auto& c : candidates(vh, nrhs, hop_variants(prec, v.flags, v.red, nrhs), occ)) {
       a.nblk = c.nblk;
       const float ms =
           time_launches([&] { launch_hop_any(prec, v.flags, v.red, a, c.block, st, nullptr, c.variant); }, st, ea, eb, 5);
+      if (verbose)
+        std::fprintf(stderr, "tune %s block %d nblk %d variant %d: %.1f us\n", key.c_str(), c.block, c.nblk, c.variant,
+                     1e3f * ms);
       if (ms < best) {
         best = ms;
         pick = c;
@@ -245,7 +265,7 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
     };
     float best = 1e30f;
     Candidate pick{128, 0, 0};
-    for (const auto& c : candidates(vh, nrhs, 1, occ)) {
+    for (const auto& c : candidates(vh, nrhs, {0}, occ)) {
       a.nblk = c.nblk;
       const float ms = time_launches([&] { launch_blas(op_, prec, px, a, c.block, st); }, st, ea, eb, 5);
       if (ms < best) {
@@ -278,6 +298,15 @@ extern "C" int bridge_tune(bridge_lattice L, const bridge_op* op, int prec, int 
     set_error(e.code, e.msg);
     return e.code;
   }
+  return BRIDGE_OK;
+}
+
+extern "C" int bridge_tune_set(bridge_lattice L, const char* key, int block, int nblk, int variant) {
+  // block >= 64: the solver sizes its reduction partials for at most vh / 64 site blocks
+  if (!L || !key || block < 64 || block > 256 || block % 32 || nblk < 1 || variant < 0 || variant > 8)
+    return BRIDGE_EINVAL;
+  std::lock_guard<std::mutex> lk(L->tune_mu);
+  L->tuned[key] = LaunchShape{block, nblk, variant};
   return BRIDGE_OK;
 }
 

@@ -216,3 +216,32 @@ def test_autotuned_shapes_keep_parity(clover_odd, api):
         assert block in (64, 128, 256) and nblk >= 1 and 0 <= variant < 6
     x, info = clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], api.make_solver(tol=1e-12))
     assert info[0]["true_rel_residual"] <= 1e-12 and rel(x, clover_odd["x"]) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("variant", [3, 5, 6, 7, 8])
+def test_forced_kernel_variants_keep_parity(api, prec, variant):
+    """Every stencil variant (read-once loads, 2/3/4 right-hand sides per
+    thread) inside a 5-RHS solve -- ragged right-hand-side groups -- against
+    the oracle, with the launch shape pinned by bridge_tune_set."""
+    dims, kappa, csw, nrhs = (4, 6, 8, 10), 0.125, 1.0, 5
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, 0.2, 17)
+    B = synth.gaussian_spinor(dims, 17, nrhs=nrhs)
+    L = api.Lattice(dims)
+    op = api.make_op("clover", kappa, csw)
+    L.upload(U, op)
+    p = {"f32": 1, "f16": 2}[prec]
+    key = "x".join(map(str, dims))
+    for flags, red in [(4, 0), (5, 2), (5, 3), (0, 0)]:
+        api.bridge_tune_set(L.handle, f"hop/{p}/{flags}/{red}/{key}/{nrhs}", 64, 3, variant)
+    X, info = L.solve(op, B, api.make_solver(tol=1e-12, inner_prec=prec))
+    eo = evenodd.EvenOdd(U, lat, kappa, csw)
+    for k in range(nrhs):
+        xe, _ = solvers.bicgstab(eo.schur, eo.prepare(B[k]), tol=1e-14)
+        assert info[k]["status"] == 0 and rel(X[k], eo.reconstruct(xe, B[k])) < 1e-10, (k, info[k])
+    # D_eo with the same pinned variant, against the oracle block
+    got = L.Deo(op, np.ascontiguousarray(B[:, lat.odd]), 0, prec)
+    want = np.stack([eo.D_hop(0, B[k][lat.odd]) for k in range(nrhs)])
+    assert rel(got, want) < {"f32": 2e-6, "f16": 5e-3}[prec]
+    L.close()
