@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg through host buffers")
     ap.add_argument("--inner", default=None, help="override the workload's inner storage precision (f32, f16, bf16)")
+    ap.add_argument("--rate-factors", type=float, nargs="+", default=[0.5, 0.9],
+                    help="serving workload: arrival rates as fractions of the saturated rate")
     ap.add_argument("--oracle-sites", type=int, default=16384, help="sites per oracle sample")
     return ap.parse_args()
 
@@ -179,7 +181,7 @@ def oracle_sample(w, U, b, nsites, seed):
 # ------------------------------------------------------------------- serving
 
 
-def serving_sample(api, n_requests, main_lattice, main_U, seed=5):
+def serving_sample(api, n_requests, main_lattice, main_U, seed=5, rate_factor=0.9):
     """Poisson stream through the request engine; returns latency stats."""
     import synth
 
@@ -217,8 +219,8 @@ def serving_sample(api, n_requests, main_lattice, main_U, seed=5):
         api.bridge_wait(h)
         api.bridge_request_release(h)
     sat = len(burst) / (time.perf_counter() - t0)
-    # Poisson arrivals at 0.9x the saturated rate
-    lam = 0.9 * sat
+    # Poisson arrivals at rate_factor x the saturated rate
+    lam = rate_factor * sat
     arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_requests))
     handles = []
     start = time.perf_counter()
@@ -226,12 +228,16 @@ def serving_sample(api, n_requests, main_lattice, main_U, seed=5):
         delay = start + ta - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        handles.append((api.bridge_submit(L.handle, op, solver, b), b.shape[0]))
-    lat_ms, lat_ok, ok, nrhs_total, statuses = [], [], 0, 0, {}
-    for h, nr in handles:
+        handles.append((api.bridge_submit(L.handle, op, solver, b), b.shape[0], "x".join(map(str, L.dims))))
+    lat_ms, lat_ok, ok, nrhs_total, statuses, by_size = [], [], 0, 0, {}, {}
+    waits, runs = [], []
+    for h, nr, size in handles:
         st, _, info = api.bridge_wait(h)
-        ts, _, td = api.bridge_request_times(h)
+        ts, ta, td = api.bridge_request_times(h)
         lat_ms.append((td - ts) * 1e3)
+        waits.append((ta - ts) * 1e3)
+        runs.append((td - ta) * 1e3)
+        by_size.setdefault(size, []).append((td - ts) * 1e3)
         if st == 0:
             lat_ok.append((td - ts) * 1e3)
         ok += st == 0
@@ -255,6 +261,10 @@ def serving_sample(api, n_requests, main_lattice, main_U, seed=5):
         "p50_ms_converged": float(np.percentile(lat_ok, 50)) if lat_ok else None,
         "p99_ms_converged": float(np.percentile(lat_ok, 99)) if lat_ok else None,
         "rhs_solved": nrhs_total,
+        "p50_ms_by_lattice": {k: float(np.percentile(v, 50)) for k, v in sorted(by_size.items())},
+        "queue_wait_ms_p50_p99": [float(np.percentile(waits, 50)), float(np.percentile(waits, 99))],
+        "run_ms_p50_p99": [float(np.percentile(runs, 50)), float(np.percentile(runs, 99))],
+        "rate_factor": rate_factor,
         "lattices": ["x".join(map(str, d)) for d in sizes],
         "kappa": [0.11, 0.13],
         "nrhs": [1, 12],
@@ -590,10 +600,51 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serving(args):
+    """The request stream alone: lattices {8^4, 16^4, 24^3x48, 32^3x64},
+    kappa in [0.11, 0.13], 1-12 right-hand sides, Wilson or clover."""
+    import torch
+
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+
+    g.build()
+    import synth
+    from paper_2303_05883_gb300 import api
+
+    w = synth.WORKLOADS["clover_32x32x32x64"]
+    L = api.Lattice(w.dims)
+    U = w.gauge()
+    L.upload(U)
+    out = {}
+    for f in args.rate_factors:
+        out[str(f)] = serving_sample(api, args.serving_requests, {"dims": w.dims, "L": L}, U, rate_factor=f)
+    L.close()
+    first = out[str(args.rate_factors[0])]
+    line = {
+        "metric": METRIC,
+        "value": first["p99_ms"],
+        "unit": "ms (p99 latency)",
+        "n_gpus": 1,
+        "steps": args.serving_requests,
+        "warmup": 0,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "serving", "requests": args.serving_requests, "rate_factors": args.rate_factors},
+        "serving": out,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -248,11 +248,13 @@ int bridge_apply(bridge_lattice lat, const bridge_op* op, int which, bridge_fiel
 
 /* Limits of the request engine: total device bytes that admitted requests
  * may hold (0 = 80% of free memory at first use) and the maximum number of
- * requests on the GPU at once (<= 0: 16).  Call before the first submit. */
+ * requests on the GPU at once (<= 0: 64).  Call before the first submit. */
 int bridge_engine_config(size_t memory_budget_bytes, int max_active);
 /* Queue a solve of D x = b (as bridge_solve, x0 = 0).  b is copied; the
- * request is admitted when memory and a slot are free and then advances
- * concurrently with the other admitted requests, each on its own stream.
+ * request is admitted when memory and a slot are free (requests that fit may
+ * pass older ones that do not, until the oldest has waited 2 s) and then
+ * advances concurrently with the other admitted requests, each on its own
+ * stream; smaller requests get higher stream priority.
  * The lattice must outlive the request.  Errors: EINVAL, ENOMEM (request
  * larger than the whole budget). */
 int bridge_submit(bridge_lattice lat, const bridge_op* op, const bridge_solver* s, const double* b, int nrhs,

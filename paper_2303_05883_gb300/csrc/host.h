@@ -58,11 +58,17 @@ struct KStat {
 };
 
 // --------------------------------------------------------- device memory
+// Device buffer.  With a stream, memory comes from the device's
+// stream-ordered pool (cudaMallocAsync / cudaFreeAsync on that stream): no
+// device-wide synchronization on release, which matters when many solves
+// start and finish while others run.  Without one, plain cudaMalloc.
 struct DevBuf {
   char* ptr = nullptr;
   size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  bool async = false;
   DevBuf() = default;
-  explicit DevBuf(size_t n);
+  explicit DevBuf(size_t n, cudaStream_t stream = nullptr, bool stream_ordered = false);
   ~DevBuf();
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
@@ -81,7 +87,7 @@ struct Field {
     return buf->ptr + ((subset == BRIDGE_FULL && parity == 1) ? block : 0);
   }
 };
-Field make_field(int prec, int subset, int nrhs, long vh);
+Field make_field(int prec, int subset, int nrhs, long vh, cudaStream_t st = nullptr, bool stream_ordered = false);
 
 // ----------------------------------------------------------- tuning
 // Launch shapes picked per (kernel class, precision, flags, lattice, nrhs).

@@ -24,21 +24,49 @@ const char* kclass_name(int k) {
   return (k >= 0 && k < K_NCLASS) ? names[k] : "?";
 }
 
-DevBuf::DevBuf(size_t n) {
+// Keep freed stream-ordered memory in the pool (no release back to the
+// driver between solves), once per device.
+static void retain_pool_memory() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done[dev] = true;
+}
+
+DevBuf::DevBuf(size_t n, cudaStream_t stream, bool stream_ordered) : st(stream), async(stream_ordered) {
   if (n == 0) return;
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ptr), n);
+  cudaError_t e;
+  if (async) {
+    retain_pool_memory();
+    e = cudaMallocAsync(reinterpret_cast<void**>(&ptr), n, st);
+  } else {
+    e = cudaMalloc(reinterpret_cast<void**>(&ptr), n);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     ptr = nullptr;
-    throw Error{BRIDGE_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e)};
+    throw Error{BRIDGE_ENOMEM, "device allocation of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e)};
   }
   bytes = n;
 }
 DevBuf::~DevBuf() {
-  if (ptr) cudaFree(ptr);
+  if (!ptr) return;
+  if (async)
+    cudaFreeAsync(ptr, st);
+  else
+    cudaFree(ptr);
 }
 
-Field make_field(int prec, int subset, int nrhs, long vh) {
+Field make_field(int prec, int subset, int nrhs, long vh, cudaStream_t st, bool stream_ordered) {
   Field f;
   f.prec = prec;
   f.subset = subset;
@@ -46,7 +74,7 @@ Field make_field(int prec, int subset, int nrhs, long vh) {
   f.vh = vh;
   f.block = spinor_block_bytes(prec, vh);
   f.rs = (subset == BRIDGE_FULL ? 2 : 1) * f.block;
-  f.buf = std::make_shared<DevBuf>((size_t)(f.rs * (nrhs > 0 ? nrhs : 1)));
+  f.buf = std::make_shared<DevBuf>((size_t)(f.rs * (nrhs > 0 ? nrhs : 1)), st, stream_ordered);
   return f;
 }
 

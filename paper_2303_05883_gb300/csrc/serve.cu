@@ -1,13 +1,23 @@
 // Request engine: continuous batching of solve requests on one GPU.
 //
-// Requests queue in FIFO order and are admitted when a slot is free and the
-// device memory they need (solve_footprint) fits in the budget.  Every
+// Requests queue in arrival order and are admitted when a slot is free and
+// the device memory they need (solve_footprint) fits in the budget.  A
+// request that fits may be admitted ahead of older ones that do not
+// (backfilling), unless the oldest waiting request has waited longer than
+// kMaxBypassSeconds, after which admission is strictly in order until it
+// is admitted -- so a large request is never starved by a stream of small
+// ones.  Every
 // admitted request gets its own stream and device state and advances by the
 // same resumable solver as bridge_solve, so the kernels of different
 // requests overlap on the GPU and a result is bit-identical alone or in a
 // mix (deterministic reductions, fixed launch shapes).  One host thread
 // drives all admitted requests; it only ever polls events, never blocks on
-// one request while others could progress.
+// one request while others could progress.  Copies between the caller's
+// (pageable) host buffers and the device run on a separate I/O thread, and
+// request buffers come from the stream-ordered pool, so neither a large copy
+// nor a release stalls the other requests.  Smaller requests get
+// higher-priority streams, so a quick solve is not queued behind the kernels
+// of a large one.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -26,6 +36,9 @@ double now_seconds() {
 }  // namespace bridge
 
 enum ReqState { RQ_QUEUED = 0, RQ_ACTIVE = 1, RQ_DONE = 2 };
+// Phase of an active request: its upload is pending on the I/O thread, it is
+// solving (engine thread), or its result download is pending.
+enum ReqPhase { PH_UPLOAD = 0, PH_SOLVE = 1, PH_DOWNLOAD = 2 };
 
 struct bridge_request_s {
   bridge_lattice_s* L = nullptr;
@@ -37,15 +50,16 @@ struct bridge_request_s {
   std::vector<double> b_host;
   // set by the engine thread
   int state = RQ_QUEUED;
+  std::atomic<int> phase{PH_UPLOAD};
   int status = BRIDGE_PENDING;
-  bool cancel = false;
-  bool released = false;
+  std::vector<double> x_host;
+  std::atomic<bool> cancel{false};
+  std::atomic<bool> released{false};
   std::string error;
   std::vector<bridge_info> info;
   double t_submit = 0, t_admit = 0, t_done = 0;
   cudaStream_t st = nullptr;
   std::unique_ptr<DevBuf> b_dev, x_dev;
-  std::unique_ptr<PinnedBuf> x_pinned;
   std::unique_ptr<SolveState> solve;
 };
 
@@ -57,9 +71,13 @@ struct Engine {
   std::deque<bridge_request_s*> queue;
   std::vector<bridge_request_s*> active;
   size_t budget = 0, used = 0;
-  int max_active = 16;
+  int max_active = 64;
+  static constexpr double kMaxBypassSeconds = 2.0;
   bool started = false;
-  std::thread th;
+  std::thread th, io;
+  std::mutex io_mu;
+  std::condition_variable io_cv;
+  std::deque<bridge_request_s*> io_queue;  // requests whose upload or download is pending
 
   void start(int device) {
     if (started) return;
@@ -72,12 +90,60 @@ struct Engine {
     }
     th = std::thread([this, device] { run(device); });
     th.detach();
+    io = std::thread([this, device] { io_loop(device); });
+    io.detach();
+  }
+
+  // I/O thread: host <-> device copies of pageable buffers (synchronous for
+  // the calling thread, so they must not run on the engine thread).
+  void io_loop(int device) {
+    cudaSetDevice(device);
+    for (;;) {
+      bridge_request_s* r;
+      {
+        std::unique_lock<std::mutex> lk(io_mu);
+        io_cv.wait(lk, [this] { return !io_queue.empty(); });
+        r = io_queue.front();
+        io_queue.pop_front();
+      }
+      const size_t n = r->nvals * sizeof(double);
+      if (r->phase.load() == PH_UPLOAD) {
+        cudaError_t e = cudaMemcpyAsync(r->b_dev->ptr, r->b_host.data(), n, cudaMemcpyHostToDevice, r->st);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          r->error = std::string("upload: ") + cudaGetErrorString(e);
+          r->cancel = true;
+        }
+        r->phase.store(PH_SOLVE);  // queued ahead of every kernel of the solve
+      } else {
+        r->x_host.resize(r->nvals);
+        cudaError_t e = cudaMemcpyAsync(r->x_host.data(), r->x_dev->ptr, n, cudaMemcpyDeviceToHost, r->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(r->st);
+        std::lock_guard<std::mutex> lk(mu);
+        int status = r->status;
+        std::string err = r->error;
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          status = BRIDGE_ECUDA;
+          err = std::string("download: ") + cudaGetErrorString(e);
+        }
+        finish(r, status, err);
+        if (r->released) delete r;
+        cv_done.notify_all();
+      }
+    }
+  }
+
+  void to_io(bridge_request_s* r) {
+    std::lock_guard<std::mutex> lk(io_mu);
+    io_queue.push_back(r);
+    io_cv.notify_one();
   }
 
   void finish(bridge_request_s* r, int status, const std::string& err) {
-    // engine mutex held by caller
+    // engine mutex held by caller; the request's stream has no work a caller
+    // waits for any more: its buffers return to the pool in stream order
     if (r->st) {
-      cudaStreamSynchronize(r->st);
       r->solve.reset();
       r->b_dev.reset();
       r->x_dev.reset();
@@ -92,15 +158,24 @@ struct Engine {
     r->t_done = now_seconds();
   }
 
+  // Stream priority from the work of the request (sites x right-hand sides):
+  // small solves overtake the kernels of large ones on the GPU.
+  static int priority_for(const bridge_request_s* r) {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    const double work = (double)r->L->V * r->nrhs;
+    if (work <= (double)(1 << 21)) return greatest;
+    if (work <= (double)(1 << 24)) return (least + greatest) / 2;
+    return least;
+  }
+
   void admit(bridge_request_s* r) {
     // called without the engine mutex; only the engine thread touches r's GPU state
     try {
-      BR_CUDA(cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking));
+      BR_CUDA(cudaStreamCreateWithPriority(&r->st, cudaStreamNonBlocking, priority_for(r)));
       const size_t n = r->nvals * sizeof(double);
-      r->b_dev.reset(new DevBuf(n));
-      r->x_dev.reset(new DevBuf(n));
-      r->x_pinned.reset(new PinnedBuf(n));
-      BR_CUDA(cudaMemcpyAsync(r->b_dev->ptr, r->b_host.data(), n, cudaMemcpyHostToDevice, r->st));
+      r->b_dev.reset(new DevBuf(n, r->st, true));
+      r->x_dev.reset(new DevBuf(n, r->st, true));
       BR_CUDA(cudaMemsetAsync(r->x_dev->ptr, 0, n, r->st));
       {
         std::lock_guard<std::mutex> lk(r->L->api_mu);
@@ -108,6 +183,8 @@ struct Engine {
                                       reinterpret_cast<double*>(r->x_dev->ptr)));
       }
       r->t_admit = now_seconds();
+      r->phase.store(PH_UPLOAD);
+      to_io(r);
     } catch (const Error& e) {
       std::lock_guard<std::mutex> lk(mu);
       finish(r, e.code, e.msg);
@@ -124,14 +201,21 @@ struct Engine {
       {
         std::unique_lock<std::mutex> lk(mu);
         if (active.empty() && queue.empty()) cv_work.wait(lk, [this] { return !queue.empty(); });
-        while (!queue.empty() && (int)active.size() < max_active && used + queue.front()->bytes <= budget) {
-          bridge_request_s* r = queue.front();
-          queue.pop_front();
+        const bool strict = !queue.empty() && now_seconds() - queue.front()->t_submit > kMaxBypassSeconds;
+        for (auto it = queue.begin(); it != queue.end() && (int)active.size() < max_active;) {
+          bridge_request_s* r = *it;
+          if (used + r->bytes > budget) {
+            if (strict) break;  // the oldest request goes first
+            ++it;
+            continue;
+          }
+          it = queue.erase(it);
           r->state = RQ_ACTIVE;
           r->L->in_flight.fetch_add(1);
           used += r->bytes;
           active.push_back(r);
           starting.push_back(r);
+          if (strict) break;
         }
       }
       for (auto* r : starting) admit(r);
@@ -142,23 +226,20 @@ struct Engine {
         snapshot = active;
       }
       for (auto* r : snapshot) {
-        if (r->state != RQ_ACTIVE || !r->solve) continue;
-        bool done = false;
+        if (r->state != RQ_ACTIVE || !r->solve || r->phase.load() != PH_SOLVE) continue;
+        bool done = false, ok = false;
         int status = BRIDGE_OK;
         std::string err;
         if (r->cancel) {
           done = true;
           status = BRIDGE_EINVAL;
-          err = "cancelled";
+          err = r->error.empty() ? "cancelled" : r->error;
         } else {
           try {
             if (r->solve->advance()) {
-              done = true;
+              done = ok = true;
               status = r->solve->status();
               r->info = r->solve->info();
-              const size_t n = r->nvals * sizeof(double);
-              BR_CUDA(cudaMemcpyAsync(r->x_pinned->ptr, r->x_dev->ptr, n, cudaMemcpyDeviceToHost, r->st));
-              BR_CUDA(cudaStreamSynchronize(r->st));
             }
           } catch (const Error& e) {
             done = true;
@@ -166,12 +247,18 @@ struct Engine {
             err = e.msg;
           }
         }
-        if (done) {
-          std::lock_guard<std::mutex> lk(mu);
+        if (!done) continue;
+        progressed = true;
+        std::lock_guard<std::mutex> lk(mu);
+        active.erase(std::find(active.begin(), active.end(), r));
+        if (ok) {
+          // the solution goes back on the I/O thread, which then finishes the request
+          r->status = status;
+          r->phase.store(PH_DOWNLOAD);
+          to_io(r);
+        } else {
           finish(r, status, err);
-          active.erase(std::find(active.begin(), active.end(), r));
           if (r->released) delete r;
-          progressed = true;
           cv_done.notify_all();
         }
       }
@@ -215,7 +302,7 @@ int engine_submit(bridge_lattice_s* L, const bridge_op& op, const bridge_solver&
 }  // namespace bridge
 
 static int collect(bridge_request_s* r, double* x_out, bridge_info* info) {
-  if (x_out && r->x_pinned) std::memcpy(x_out, r->x_pinned->ptr, r->nvals * sizeof(double));
+  if (x_out && r->x_host.size() == r->nvals) std::memcpy(x_out, r->x_host.data(), r->nvals * sizeof(double));
   if (info)
     for (int k = 0; k < r->nrhs; ++k) info[k] = k < (int)r->info.size() ? r->info[k] : bridge_info{r->status, 0, 0, 0, 0, 0};
   if (r->status < 0 && !r->error.empty()) set_error(r->status, r->error);

@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "solver.h"
 
@@ -26,16 +28,40 @@ namespace bridge {
 
 extern std::atomic<long> g_launches;
 
+// Small pinned host buffers are recycled through a process-wide free list:
+// cudaFreeHost, like cudaFree, may synchronize the device, which would stall
+// every concurrently running solve whenever one finishes.
+namespace {
+std::mutex g_pinned_mu;
+std::multimap<size_t, void*> g_pinned_free;
+size_t pinned_class(size_t n) {
+  size_t c = 256;
+  while (c < n) c <<= 1;
+  return c;
+}
+}  // namespace
+
 PinnedBuf::PinnedBuf(size_t n) {
-  if (cudaMallocHost(&ptr, n) != cudaSuccess) {
+  bytes = pinned_class(n);
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    auto it = g_pinned_free.find(bytes);
+    if (it != g_pinned_free.end()) {
+      ptr = it->second;
+      g_pinned_free.erase(it);
+    }
+  }
+  if (!ptr && cudaMallocHost(&ptr, bytes) != cudaSuccess) {
     cudaGetLastError();
     ptr = nullptr;
     throw Error{BRIDGE_ENOMEM, "cudaMallocHost failed"};
   }
-  std::memset(ptr, 0, n);
+  std::memset(ptr, 0, bytes);
 }
 PinnedBuf::~PinnedBuf() {
-  if (ptr) cudaFreeHost(ptr);
+  if (!ptr) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free.emplace(bytes, ptr);
 }
 
 static int inner_prec(const bridge_solver& prm) { return prm.mixed ? prm.inner_prec : P_F64; }
@@ -75,26 +101,26 @@ SolveState::SolveState(bridge_lattice_s* L, const bridge_op& op, const bridge_so
     inflight_ = 1;
   }
   const long vh = L_->vh;
-  b64_ = make_field(P_F64, BRIDGE_FULL, nrhs, vh);
-  x64_ = make_field(P_F64, BRIDGE_FULL, nrhs, vh);
-  r64_ = make_field(P_F64, BRIDGE_FULL, nrhs, vh);
-  rin_ = make_field(P_, BRIDGE_FULL, nrhs, vh);
-  bh_ = make_field(P_, BRIDGE_EVEN, nrhs, vh);
-  r_ = make_field(P_, BRIDGE_EVEN, nrhs, vh);
-  rhat_ = make_field(P_, BRIDGE_EVEN, nrhs, vh);
-  p_ = make_field(P_, BRIDGE_EVEN, nrhs, vh);
-  v_ = make_field(P_, BRIDGE_EVEN, nrhs, vh);
-  s_ = make_field(P_, BRIDGE_EVEN, nrhs, vh);
-  t_ = make_field(P_, BRIDGE_EVEN, nrhs, vh);
-  xin_ = make_field(PX_, BRIDGE_EVEN, nrhs, vh);
-  if (PX_ != P_) xinp_ = make_field(P_, BRIDGE_EVEN, nrhs, vh);
-  tmp_ = make_field(P_, BRIDGE_ODD, nrhs, vh);
-  eo_ = make_field(P_, BRIDGE_ODD, nrhs, vh);
-  scal_.reset(new DevBuf(sizeof(BiCGScalars) * nrhs));
-  partials_.reset(new DevBuf((size_t)nrhs * ((vh + 63) / 64) * 4 * sizeof(double)));
-  counter_.reset(new DevBuf(256));
-  result_.reset(new DevBuf(sizeof(double) * 4 * 4 * nrhs));
-  mask_.reset(new DevBuf(sizeof(int) * nrhs));
+  b64_ = make_field(P_F64, BRIDGE_FULL, nrhs, vh, st_, true);
+  x64_ = make_field(P_F64, BRIDGE_FULL, nrhs, vh, st_, true);
+  r64_ = make_field(P_F64, BRIDGE_FULL, nrhs, vh, st_, true);
+  rin_ = make_field(P_, BRIDGE_FULL, nrhs, vh, st_, true);
+  bh_ = make_field(P_, BRIDGE_EVEN, nrhs, vh, st_, true);
+  r_ = make_field(P_, BRIDGE_EVEN, nrhs, vh, st_, true);
+  rhat_ = make_field(P_, BRIDGE_EVEN, nrhs, vh, st_, true);
+  p_ = make_field(P_, BRIDGE_EVEN, nrhs, vh, st_, true);
+  v_ = make_field(P_, BRIDGE_EVEN, nrhs, vh, st_, true);
+  s_ = make_field(P_, BRIDGE_EVEN, nrhs, vh, st_, true);
+  t_ = make_field(P_, BRIDGE_EVEN, nrhs, vh, st_, true);
+  xin_ = make_field(PX_, BRIDGE_EVEN, nrhs, vh, st_, true);
+  if (PX_ != P_) xinp_ = make_field(P_, BRIDGE_EVEN, nrhs, vh, st_, true);
+  tmp_ = make_field(P_, BRIDGE_ODD, nrhs, vh, st_, true);
+  eo_ = make_field(P_, BRIDGE_ODD, nrhs, vh, st_, true);
+  scal_.reset(new DevBuf(sizeof(BiCGScalars) * nrhs, st_, true));
+  partials_.reset(new DevBuf((size_t)nrhs * ((vh + 63) / 64) * 4 * sizeof(double), st_, true));
+  counter_.reset(new DevBuf(256, st_, true));
+  result_.reset(new DevBuf(sizeof(double) * 4 * 4 * nrhs, st_, true));
+  mask_.reset(new DevBuf(sizeof(int) * nrhs, st_, true));
   for (int i = 0; i < 2; ++i) h_sc_[i].reset(new PinnedBuf(sizeof(BiCGScalars) * nrhs));
   h_result_.reset(new PinnedBuf(sizeof(double) * 4 * 4 * nrhs));
   h_mask_.reset(new PinnedBuf(sizeof(int) * nrhs));

@@ -13,6 +13,7 @@ namespace bridge {
 
 struct PinnedBuf {
   void* ptr = nullptr;
+  size_t bytes = 0;
   explicit PinnedBuf(size_t n);
   ~PinnedBuf();
   PinnedBuf(const PinnedBuf&) = delete;
