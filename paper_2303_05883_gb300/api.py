@@ -227,7 +227,7 @@ def bridge_submit(lat, op, solver, b) -> Request:
     nrhs = 1 if bb.ndim == 3 else bb.shape[0]
     h = c_void_p()
     check(_abi.load().bridge_submit(lat, byref(op), byref(solver), _dptr(bb), nrhs, byref(h)), "bridge_submit")
-    return Request(h.value, bb.shape, nrhs, bb)
+    return Request(h.value, bb.shape, nrhs)  # the library keeps its own copy of b
 
 
 def bridge_poll(req: Request):
@@ -240,10 +240,11 @@ def bridge_poll(req: Request):
     return st, x, _infos(info, req.nrhs)
 
 
-def bridge_wait(req: Request, timeout_ms=-1):
-    x = np.empty(req.shape, dtype=np.complex128)
+def bridge_wait(req: Request, timeout_ms=-1, want_x=True):
+    """None on timeout, else (status, x or None, infos)."""
+    x = np.empty(req.shape, dtype=np.complex128) if want_x else None
     info = (bridge_info * req.nrhs)()
-    st = _abi.load().bridge_wait(req.handle, int(timeout_ms), _dptr(x), info)
+    st = _abi.load().bridge_wait(req.handle, int(timeout_ms), _dptr(x) if want_x else None, info)
     if st == _abi.BRIDGE_ETIMEDOUT:
         return None
     return st, x, _infos(info, req.nrhs)

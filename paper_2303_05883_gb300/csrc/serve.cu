@@ -114,7 +114,8 @@ struct Engine {
           r->error = std::string("upload: ") + cudaGetErrorString(e);
           r->cancel = true;
         }
-        r->phase.store(PH_SOLVE);  // queued ahead of every kernel of the solve
+        std::vector<double>().swap(r->b_host);  // staged by the copy above: the host copy is no longer needed
+        r->phase.store(PH_SOLVE);             // queued ahead of every kernel of the solve
       } else {
         r->x_host.resize(r->nvals);
         cudaError_t e = cudaMemcpyAsync(r->x_host.data(), r->x_dev->ptr, n, cudaMemcpyDeviceToHost, r->st);
