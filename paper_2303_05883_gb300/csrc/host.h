@@ -37,7 +37,9 @@ enum KClass {
   K_HOP = 0,     // D_eo / D_oe
   K_FULLD,       // full operator, one parity
   K_DHAT1,       // Schur pass 1: T^-1 D_oe
-  K_DHAT2,       // Schur pass 2 (+ fused dot products)
+  K_DHAT2,       // Schur pass 2 (operator application)
+  K_DHAT2A,      // Schur pass 2 with <rhat, v> -> alpha (solver)
+  K_DHAT2W,      // Schur pass 2 with <t, s>, |t|^2 -> omega (solver)
   K_PREP,        // even-odd prepare / reconstruct
   K_RESID,       // FP64 residual b - D x with |r|^2
   K_BLAS_INIT,

@@ -18,9 +18,10 @@ const char* last_error_text() { return tl_last_error.c_str(); }
 std::atomic<long> g_launches{0};
 
 const char* kclass_name(int k) {
-  static const char* names[K_NCLASS] = {"hop_deo",   "dirac_full", "schur_pass1", "schur_pass2", "evenodd_prep",
-                                        "residual64", "blas_init",  "blas_s",      "blas_xr",     "blas_p",
-                                        "convert",   "norm",       "clover_site", "setup"};
+  static const char* names[K_NCLASS] = {"hop_deo",      "dirac_full",    "schur_pass1", "schur_pass2",
+                                        "schur_pass2_alpha", "schur_pass2_omega", "evenodd_prep", "residual64",
+                                        "blas_init",    "blas_s",        "blas_xr",     "blas_p",
+                                        "convert",      "norm",          "clover_site", "setup"};
   return (k >= 0 && k < K_NCLASS) ? names[k] : "?";
 }
 

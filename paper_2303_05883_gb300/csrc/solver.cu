@@ -324,6 +324,7 @@ void SolveState::enqueue_iteration() {
   p1.in_rs = p_.rs;
   run_hop(L_, p1, st_);
   p2.red = R_DOT_A;
+  p2.cls = K_DHAT2A;
   p2.self = p_.ptr(0);
   p2.self_rs = p_.rs;
   p2.avec = rhat_.ptr(0);
@@ -339,6 +340,7 @@ void SolveState::enqueue_iteration() {
   p1.in_rs = s_.rs;
   run_hop(L_, p1, st_);
   p2.red = R_TS;
+  p2.cls = K_DHAT2W;
   p2.self = s_.ptr(0);
   p2.self_rs = s_.rs;
   p2.avec = nullptr;
@@ -426,7 +428,8 @@ void SolveState::credit_iterations(const std::vector<long>& iters) {
     L_->stats.k[cls].flops += vh * rhs_flops * sum;
   };
   add(K_DHAT1, 2 * h1.rhs_bytes, 2 * h1.shared_bytes, 2 * h1.rhs_flops);
-  add(K_DHAT2, ha.rhs_bytes + ht.rhs_bytes, ha.shared_bytes + ht.shared_bytes, ha.rhs_flops + ht.rhs_flops);
+  add(K_DHAT2A, ha.rhs_bytes, ha.shared_bytes, ha.rhs_flops);
+  add(K_DHAT2W, ht.rhs_bytes, ht.shared_bytes, ht.rhs_flops);
   add(K_BLAS_S, 3 * S, 0, 48);
   add(K_BLAS_XR, 5 * S + 2 * SX, 0, 192);
   add(K_BLAS_P, 4 * S, 0, 96);

@@ -202,7 +202,8 @@ def test_profile_stats_report_event_times(clover_odd, api):
     clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], api.make_solver(tol=1e-10))
     api.bridge_profile(h, False)
     st = api.bridge_stats(h)
-    assert st["schur_pass2"]["launches"] > 0 and st["schur_pass2"]["ms"] > 0
+    assert st["schur_pass2_alpha"]["launches"] > 0 and st["schur_pass2_alpha"]["ms"] > 0
+    assert st["schur_pass2_omega"]["launches"] == st["schur_pass2_alpha"]["launches"]
     assert st["residual64"]["launches"] >= 4
 
 
