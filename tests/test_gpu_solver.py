@@ -246,3 +246,32 @@ def test_forced_kernel_variants_keep_parity(api, prec, variant):
     want = np.stack([eo.D_hop(0, B[k][lat.odd]) for k in range(nrhs)])
     assert rel(got, want) < {"f32": 2e-6, "f16": 5e-3}[prec]
     L.close()
+
+
+def test_nonfinite_source_reports_breakdown(clover_odd, api):
+    """A NaN in b propagates to the FP64 residual; the solve stops with EBREAKDOWN."""
+    from paper_2303_05883_gb300 import _abi
+
+    b = clover_odd["b"].copy()
+    b[7, 1, 2] = np.nan
+    x, info = clover_odd["L"].solve(clover_odd["op"], b, api.make_solver(tol=1e-10), raise_on_fail=False)
+    assert info[0]["status"] == _abi.BRIDGE_EBREAKDOWN
+    # the lattice stays usable
+    x, info = clover_odd["L"].solve(clover_odd["op"], clover_odd["b"], api.make_solver(tol=1e-12))
+    assert info[0]["status"] == 0 and rel(x, clover_odd["x"]) < 1e-10
+
+
+def test_null_pointers_are_einval(clover_odd, api):
+    import ctypes
+
+    from paper_2303_05883_gb300 import _abi
+
+    lib = _abi.load()
+    op = clover_odd["op"]
+    h = clover_odd["L"].handle
+    assert lib.bridge_mult_D(h, ctypes.byref(op), 1, None, None, 1) == _abi.BRIDGE_EINVAL
+    assert lib.bridge_mult_D(h, None, 1, None, None, 1) == _abi.BRIDGE_EINVAL
+    s = api.make_solver()
+    assert lib.bridge_solve(h, ctypes.byref(op), ctypes.byref(s), None, None, 1, None) == _abi.BRIDGE_EINVAL
+    assert lib.bridge_gauge_upload(h, None, None) == _abi.BRIDGE_EINVAL
+    assert lib.bridge_apply(h, ctypes.byref(op), 9, None, None) == _abi.BRIDGE_EINVAL
