@@ -126,6 +126,8 @@ typedef struct {
  * >= 2 with V/2 < 2^31.  Allocates the handle and a CUDA stream; no field
  * memory yet.  Errors: EINVAL (dims), ECUDA (no sm_103 device). */
 int bridge_lattice_create(const int dims[4], bridge_lattice* out);
+/* Free the handle and everything it owns; ESTATE while engine requests on
+ * it are still running. */
 int bridge_lattice_destroy(bridge_lattice lat);
 /* The cudaStream_t (as void*) on which all work of this lattice is ordered. */
 void* bridge_lattice_stream(bridge_lattice lat);

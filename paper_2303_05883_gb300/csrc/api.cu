@@ -199,6 +199,7 @@ int bridge_lattice_create(const int dims[4], bridge_lattice* out) {
 int bridge_lattice_destroy(bridge_lattice L) {
   BR_API_BEGIN
   if (!L) return BRIDGE_OK;
+  BR_CHECK(L->in_flight.load() == 0, BRIDGE_ESTATE, "requests on this lattice are still running");
   cudaStreamSynchronize(L->stream);
   {
     std::lock_guard<std::mutex> lk(L->stats.mu);

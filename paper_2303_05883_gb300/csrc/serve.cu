@@ -212,7 +212,6 @@ struct Engine {
           }
           it = queue.erase(it);
           r->state = RQ_ACTIVE;
-          r->L->in_flight.fetch_add(1);
           used += r->bytes;
           active.push_back(r);
           starting.push_back(r);
@@ -296,6 +295,7 @@ int engine_submit(bridge_lattice_s* L, const bridge_op& op, const bridge_solver&
     throw Error{BRIDGE_ENOMEM, "request needs " + std::to_string(need) + " bytes, more than the whole budget"};
   }
   E.queue.push_back(r);
+  L->in_flight.fetch_add(1);  // held from submission until the request is done or withdrawn
   *out = r;
   E.cv_work.notify_all();
   return BRIDGE_OK;
@@ -345,6 +345,7 @@ int bridge_request_release(bridge_request_h h) {
   if (h->state == RQ_QUEUED) {
     auto it = std::find(E.queue.begin(), E.queue.end(), h);
     if (it != E.queue.end()) E.queue.erase(it);
+    h->L->in_flight.fetch_sub(1);
     delete h;
   } else if (h->state == RQ_ACTIVE) {
     h->cancel = true;  // the engine thread frees it once it stops

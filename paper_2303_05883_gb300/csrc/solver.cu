@@ -22,6 +22,8 @@
 #include <map>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "solver.h"
 
 namespace bridge {
@@ -173,6 +175,7 @@ int SolveState::status() const {
 }
 
 void SolveState::enqueue_residual() {
+  nvtxRangePushA("bridge: FP64 residual");
   // r = b - T x + kappa H x (one launch per output parity), |r|^2 per parity
   for (int q = 0; q < 2; ++q) {
     HopCall c;
@@ -202,6 +205,7 @@ void SolveState::enqueue_residual() {
   BR_CUDA(cudaMemcpyAsync(h_result_->ptr, result_->ptr, sizeof(double) * 4 * 4 * nrhs_, cudaMemcpyDeviceToHost, st_));
   BR_CUDA(cudaEventRecord(ev_misc_, st_));
   pending_ = ev_misc_;
+  nvtxRangePop();
 }
 
 void SolveState::launch_blas(int op, int cls, double bytes_per_site, double flops_per_site, int fin, bool count_work) {
@@ -242,6 +246,7 @@ void SolveState::launch_blas(int op, int cls, double bytes_per_site, double flop
 }
 
 void SolveState::begin_inner() {
+  nvtxRangePushA("bridge: even-odd prepare + inner start");
   // mask: right-hand sides still above tolerance
   int* hm = reinterpret_cast<int*>(h_mask_->ptr);
   for (int r = 0; r < nrhs_; ++r) hm[r] = active_[r];
@@ -288,6 +293,7 @@ void SolveState::begin_inner() {
   launch_blas(B_INIT, K_BLAS_INIT, 4 * S + SX, 24, FIN_INIT);
   batches_launched_ = batches_checked_ = 0;
   for (int k = 0; k < inflight_; ++k) enqueue_batch();
+  nvtxRangePop();
 }
 
 void SolveState::enqueue_iteration() {
@@ -387,6 +393,7 @@ void SolveState::capture_batch() {
 }
 
 void SolveState::enqueue_batch() {
+  nvtxRangePushA("bridge: BiCGStab batch");
   const bool use_graph = prm_.use_graph && !L_->stats.profiling;
   if (use_graph) {
     if (!graph_) capture_batch();
@@ -407,6 +414,7 @@ void SolveState::enqueue_batch() {
   BR_CUDA(cudaMemcpyAsync(h_sc_[slot]->ptr, scal_->ptr, sizeof(BiCGScalars) * nrhs_, cudaMemcpyDeviceToHost, st_));
   BR_CUDA(cudaEventRecord(ev_[slot], st_));
   ++batches_launched_;
+  nvtxRangePop();
 }
 
 // Algorithmic work of the iterations that ran (launched iterations past
@@ -436,6 +444,10 @@ void SolveState::credit_iterations(const std::vector<long>& iters) {
 }
 
 void SolveState::finish_inner() {
+  nvtxRangePushA("bridge: reconstruct + accumulate");
+  struct Pop {
+    ~Pop() { nvtxRangePop(); }
+  } pop;
   const BiCGScalars* sc = reinterpret_cast<const BiCGScalars*>(h_sc_[(batches_checked_ - 1) & 1]->ptr);
   long most = 0;
   std::vector<long> iters(nrhs_, 0);

@@ -170,13 +170,36 @@ def test_gauge_reupload_refused_while_requests_run(api):
     L.upload(U)
     b = synth.gaussian_spinor(dims, 5, nrhs=12)
     h = api.bridge_submit(L.handle, api.make_op("wilson", 0.124), api.make_solver(tol=1e-13, inner_prec="f16"), b)
-    try:
+    # a submitted request holds the lattice from submission on, queued or running
+    with pytest.raises(_abi.BridgeError) as e:
         L.upload(U)
-        refused = False
-    except _abi.BridgeError as e:
-        refused = e.status == _abi.BRIDGE_ESTATE
+    assert e.value.status == _abi.BRIDGE_ESTATE
+    with pytest.raises(_abi.BridgeError) as e:
+        api.bridge_lattice_destroy(L.handle)
+    assert e.value.status == _abi.BRIDGE_ESTATE
     st, x, info = api.bridge_wait(h)
+    assert st == 0
+    L.upload(U)  # done requests no longer hold it
     api.bridge_request_release(h)
-    # either the upload raced ahead of admission (allowed) or it was refused while running
-    assert st == 0 or refused
     L.close()
+
+
+def test_release_of_queued_request_frees_the_lattice(api):
+    dims = (8, 8, 8, 8)
+    api.bridge_engine_config(max_active=1)
+    try:
+        L = api.Lattice(dims)
+        U = synth.gauge_field(dims, 0.2, 6)
+        L.upload(U)
+        op = api.make_op("wilson", 0.1249)
+        slv = api.make_solver(tol=1e-12, inner_prec="f32")
+        b = synth.gaussian_spinor(dims, 7, nrhs=12)
+        h1 = api.bridge_submit(L.handle, op, slv, b)
+        h2 = api.bridge_submit(L.handle, op, slv, b)  # queued behind the long-running h1
+        api.bridge_request_release(h2)
+        api.bridge_wait(h1)
+        api.bridge_request_release(h1)
+        L.upload(U)  # nothing holds the lattice now
+        L.close()
+    finally:
+        api.bridge_engine_config(max_active=64)
