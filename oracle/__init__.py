@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for the even-odd Wilson/clover solver path.
+"""FP64 CPU oracle for the even-odd Wilson/clover and Moebius domain-wall solver paths.
 
 TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously correct
 definition that the CUDA library is checked against.  Only the test suite,
@@ -16,8 +16,13 @@ paper is silent, the docstring states the reading taken):
 * ``evenodd``  -- the blocks D_ee, D_oo, D_eo, D_oe and the Schur operator
                   D^(eo) = 1 - D_ee^-1 D_eo D_oo^-1 D_oe (Eq. 1), source
                   preparation and odd-site reconstruction;
-* ``solvers``  -- BiCGStab (van der Vorst) as named in Sec. 3, dense matrices
-                  by their matrix elements and dense LU solves.
+* ``domainwall`` -- the Moebius domain-wall operator (Sec. 2), its even-odd
+                  blocks over four-dimensional parity with the fifth
+                  coordinate as an inner index, the Schur operator and its
+                  adjoint;
+* ``solvers``  -- BiCGStab (van der Vorst) as named in Sec. 3, CG and CG on
+                  the normal equations (the domain-wall solver of Fig. 7),
+                  dense matrices by their matrix elements and dense LU solves.
 
 Arrays are complex128 in the canonical layouts of ``synth``: spinors
 ``(V, 4, 3)``, links ``(4, V, 3, 3)``, half-lattice vectors ``(V/2, 4, 3)``
@@ -27,7 +32,10 @@ Parity status: every function here is pinned by a CPU test against a closed
 form, an invariant or a library routine (see tests/test_oracle_pins.py);
 none is marked "parity unpinned" except the overall sign/normalisation of the
 clover term, which is a convention the paper does not state (the abelian-flux
-closed form pins the reading taken, not the paper).
+closed form pins the reading taken, not the paper).  The domain-wall operator
+is pinned by the overlap relation (its boundary-field operator equals the
+polar approximation of the sign function of the Moebius kernel), in the free
+field against the Fourier symbol and on random gauge fields.
 """
 
-from . import lattice, gamma, dirac, evenodd, solvers  # noqa: F401
+from . import lattice, gamma, dirac, evenodd, domainwall, solvers  # noqa: F401

@@ -10,7 +10,7 @@ from __future__ import annotations
 import numpy as np
 
 import synth
-from oracle import dirac, evenodd, gamma, solvers
+from oracle import dirac, domainwall, evenodd, gamma, solvers
 from oracle.lattice import Lattice
 
 
@@ -248,3 +248,152 @@ def gamma_algebra_error():
     for mu in range(4):
         err = max(err, np.abs(G[mu] - PINNED_GAMMA[mu]).max())
     return float(err)
+
+
+# --- Moebius domain wall -------------------------------------------------------------
+#
+# Closed form used below (the overlap relation of domain-wall fermions): with
+# K = (b + c) W (2 + (b - c) W)^-1 and the polar approximation
+#     eps_Ls(h) = ((1 + h)^Ls - (1 - h)^Ls) / ((1 + h)^Ls + (1 - h)^Ls)
+# of the sign function applied to the Hermitian gamma_5 K, the four-dimensional
+# operator seen by the boundary fields q = P_- psi_0 + P_+ psi_{Ls-1} is
+#     D_eff(m_f) = (1 + m_f)/2 + (1 - m_f)/2 gamma_5 eps_Ls(gamma_5 K),
+# and it is reached from the five-dimensional operator as
+#     D_eff(m_f) chi = q( D(1)^-1 D(m_f) psi_chi ),  psi_chi = P_- chi at s = 0, P_+ chi at s = Ls-1.
+
+
+def _eps_polar(Hm, Ls):
+    lam, Q = np.linalg.eigh(Hm)
+    e = ((1 + lam) ** Ls - (1 - lam) ** Ls) / ((1 + lam) ** Ls + (1 - lam) ** Ls)
+    return (Q * e) @ Q.conj().T
+
+
+def _deff_closed_form(W, b, c, mf, Ls, g5):
+    n = W.shape[0]
+    K = np.linalg.solve(2 * np.eye(n) + (b - c) * W, (b + c) * W)
+    return (1 + mf) / 2 * np.eye(n) + (1 - mf) / 2 * g5 @ _eps_polar(g5 @ K, Ls)
+
+
+def _deff_from_5d(op1, opm, chis):
+    """D_eff chi for each chi in chis via the five-dimensional operators (dense LU for D(1))."""
+    Ls, V = op1.Ls, op1.lat.V
+    n5 = Ls * V * 12
+    D1 = solvers.dense_matrix(lambda v: op1.full(v.reshape(Ls, V, 4, 3)).reshape(-1), n5)
+    out = []
+    for chi in chis:
+        psi = np.zeros((Ls, V, 4, 3), dtype=np.complex128)
+        psi[0][:, 2:] = chi[:, 2:]
+        psi[Ls - 1][:, :2] = chi[:, :2]
+        z = np.linalg.solve(D1, opm.full(psi).reshape(-1)).reshape(Ls, V, 4, 3)
+        q = np.zeros_like(chi)
+        q[:, 2:] = z[0][:, 2:]
+        q[:, :2] = z[Ls - 1][:, :2]
+        out.append(q)
+    return out
+
+
+def mobius_overlap_error(dims=(2, 2, 2, 2), Ls=4, M5=1.8, b=1.5, c=0.5, mf=0.07, eps=0.5, seed=81):
+    """The oracle's 5-d Moebius operator reproduces the overlap closed form on a random gauge field.
+
+    W = D_W(-M5) comes from the dense Wilson matrix filled from its matrix
+    elements (solvers.dense_dirac, pinned on its own): with kappa = 1 that
+    matrix is 1 - H.
+    """
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    n4 = 12 * lat.V
+    H = np.eye(n4) - solvers.dense_dirac(U, lat, 1.0, 0.0)
+    W = (4.0 - M5) * np.eye(n4) - 0.5 * H
+    g5 = np.kron(np.eye(lat.V), np.kron(np.diag([1.0, 1.0, -1.0, -1.0]), np.eye(3)))
+    want = _deff_closed_form(W, b, c, mf, Ls, g5)
+    gen = np.random.default_rng(seed)
+    chis = [gen.standard_normal((lat.V, 4, 3)) + 1j * gen.standard_normal((lat.V, 4, 3)) for _ in range(3)]
+    got = _deff_from_5d(domainwall.Mobius(U, lat, Ls, M5, b, c, 1.0), domainwall.Mobius(U, lat, Ls, M5, b, c, mf), chis)
+    return max(rel(g.reshape(-1), want @ chi.reshape(-1)) for g, chi in zip(got, chis))
+
+
+def mobius_free_field_error(dims=(4, 2, 2, 2), Ls=4, M5=1.8, b=1.5, c=0.5, mf=0.05,
+                            modes=((0, 0, 0, 0), (1, 0, 1, 0), (3, 1, 0, 1)), seed=83):
+    """Free field: plane waves give the overlap closed form with the Fourier symbol
+    W(p) = (4 - M5) - sum cos p_mu + i sum gamma_mu sin p_mu (a 4x4 spin matrix)."""
+    lat = Lattice(dims)
+    U = synth.unit_gauge(dims)
+    gen = np.random.default_rng(seed)
+    g5 = np.diag([1.0, 1.0, -1.0, -1.0]).astype(np.complex128)
+    chis, wants = [], []
+    for n in modes:
+        u = gen.standard_normal((4, 3)) + 1j * gen.standard_normal((4, 3))
+        chi, p = plane_wave(lat, n, u)
+        Wp = (4.0 - M5 - sum(np.cos(q) for q in p)) * np.eye(4, dtype=np.complex128)
+        for mu in range(4):
+            Wp = Wp + 1j * np.sin(p[mu]) * PINNED_GAMMA[mu]
+        Dp = _deff_closed_form(Wp, b, c, mf, Ls, g5)
+        chis.append(chi)
+        wants.append(np.einsum("st,ntc->nsc", Dp, chi))
+    got = _deff_from_5d(domainwall.Mobius(U, lat, Ls, M5, b, c, 1.0), domainwall.Mobius(U, lat, Ls, M5, b, c, mf), chis)
+    return max(rel(g, w) for g, w in zip(got, wants))
+
+
+def _mobius(dims, Ls, eps, seed, M5=1.8, b=1.5, c=0.5, mf=0.1):
+    lat = Lattice(dims)
+    return domainwall.Mobius(synth.gauge_field(dims, eps, seed), lat, Ls, M5, b, c, mf)
+
+
+def mobius_schur_dense_error(dims=(2, 2, 2, 2), Ls=3, eps=0.5, seed=85):
+    """D^(eo) and the even-odd solve against the dense 5-d matrix: the Schur
+    complement A_ee^-1 (A_ee - D_eo A_oo^-1 D_oe) of its parity blocks, and LU."""
+    op = _mobius(dims, Ls, eps, seed)
+    lat, V = op.lat, op.lat.V
+    M = solvers.dense_matrix(lambda v: op.full(v.reshape(Ls, V, 4, 3)).reshape(-1), Ls * V * 12)
+    idx = np.arange(Ls * V * 12).reshape(Ls, V, 12)
+    e, o = idx[:, lat.even].reshape(-1), idx[:, lat.odd].reshape(-1)
+    Mee, Meo, Moe, Moo = M[np.ix_(e, e)], M[np.ix_(e, o)], M[np.ix_(o, e)], M[np.ix_(o, o)]
+    S = np.linalg.solve(Mee, Mee - Meo @ np.linalg.solve(Moo, Moe))
+    ne = len(e)
+    Sb = solvers.dense_matrix(lambda v: op.schur(v.reshape(Ls, -1, 4, 3)).reshape(-1), ne)
+    err = rel(Sb, S)
+    rhs = synth.gaussian_spinor(dims, seed, nrhs=Ls)
+    x_lu = np.linalg.solve(M, rhs.reshape(-1)).reshape(rhs.shape)
+    xe = np.linalg.solve(Sb, op.prepare(rhs).reshape(-1)).reshape(Ls, -1, 4, 3)
+    return max(err, rel(op.reconstruct(xe, rhs), x_lu))
+
+
+def mobius_adjoint_error(dims=(4, 2, 2, 4), Ls=5, eps=0.5, seed=87):
+    """<u, D^(eo) v> = <D^(eo)^dagger u, v> for random u, v."""
+    op = _mobius(dims, Ls, eps, seed)
+    vh = op.lat.V // 2
+    gen = np.random.default_rng(seed)
+    u = gen.standard_normal((Ls, vh, 4, 3)) + 1j * gen.standard_normal((Ls, vh, 4, 3))
+    v = gen.standard_normal((Ls, vh, 4, 3)) + 1j * gen.standard_normal((Ls, vh, 4, 3))
+    lhs, rhs = np.vdot(u, op.schur(v)), np.vdot(op.schur_dag(u), v)
+    return abs(lhs - rhs) / (np.linalg.norm(u) * np.linalg.norm(op.schur(v)))
+
+
+def shamir_reflection_error(dims=(2, 2, 4, 2), Ls=4, eps=0.5, seed=89):
+    """Shamir (b = 1, c = 0): gamma_5 R_5 D gamma_5 R_5 = D^dagger, R_5: s -> Ls-1-s."""
+    op = _mobius(dims, Ls, eps, seed, b=1.0, c=0.0)
+    gen = np.random.default_rng(seed)
+    sh = (Ls, op.lat.V, 4, 3)
+    u = gen.standard_normal(sh) + 1j * gen.standard_normal(sh)
+    v = gen.standard_normal(sh) + 1j * gen.standard_normal(sh)
+    g5r5 = lambda w: (w[::-1] * np.array([1, 1, -1, -1])[None, None, :, None])  # noqa: E731
+    lhs = np.vdot(u, g5r5(op.full(g5r5(v))))
+    rhs = np.vdot(op.full(u), v)
+    return abs(lhs - rhs) / (np.linalg.norm(u) * np.linalg.norm(v))
+
+
+def cg_error(n=48, seed=91, maxiter=400):
+    """CG on a random Hermitian positive definite matrix against LAPACK, and
+    CG on the normal equations of the even-odd Moebius system against LU."""
+    gen = np.random.default_rng(seed)
+    Z = gen.standard_normal((n, n)) + 1j * gen.standard_normal((n, n))
+    A = Z @ Z.conj().T + 0.5 * np.eye(n)
+    b = gen.standard_normal(n) + 1j * gen.standard_normal(n)
+    x, _ = solvers.cg(lambda v: A @ v, b, tol=1e-13, maxiter=maxiter)
+    err = rel(x, np.linalg.solve(A, b))
+    op = _mobius((2, 2, 2, 2), 3, 0.5, seed)
+    ne = 3 * op.lat.V // 2 * 12
+    S = solvers.dense_matrix(lambda v: op.schur(v.reshape(3, -1, 4, 3)).reshape(-1), ne)
+    bh = gen.standard_normal((3, op.lat.V // 2, 4, 3)) + 1j * gen.standard_normal((3, op.lat.V // 2, 4, 3))
+    xe, _ = solvers.cgnr(op.schur, op.schur_dag, bh, tol=1e-13, maxiter=maxiter)
+    return max(err, rel(xe.reshape(-1), np.linalg.solve(S, bh.reshape(-1))))

@@ -42,6 +42,27 @@ MUTANTS = [
     ("solvers", "x = x + alpha * p + omega * s", "x = x + alpha * p", lambda: pins.lu_vs_bicgstab_error(maxiter=400), 1e-10),
     ("solvers", "r = s - omega * t", "r = s + omega * t", lambda: pins.lu_vs_bicgstab_error(maxiter=400), 1e-10),
     ("solvers", "np.kron(_g.I4 + g, U[mu][y].conj().T)", "np.kron(_g.I4 + g, U[mu][y].conj())", pins.dense_vs_stencil_error, 1e-10),
+    # Moebius domain wall
+    ("domainwall", "out[s][:, LOWER] = up[:, LOWER]\n            out[s][:, UPPER] = dn[:, UPPER]",
+     "out[s][:, UPPER] = up[:, UPPER]\n            out[s][:, LOWER] = dn[:, LOWER]", pins.mobius_overlap_error, 1e-10),
+    ("domainwall", "up = psi[s + 1] if s + 1 < Ls else -mf * psi[0]", "up = psi[s + 1] if s + 1 < Ls else mf * psi[0]",
+     pins.mobius_overlap_error, 1e-10),
+    ("domainwall", "+ self.c * self.W(Ppsi[s], sites) - Ppsi[s][sites]", "- Ppsi[s][sites]",
+     pins.mobius_overlap_error, 1e-10),
+    ("domainwall", "return (4.0 - self.M5) * psi4[sites]", "return (4.0 + self.M5) * psi4[sites]",
+     pins.mobius_free_field_error, 1e-10),
+    ("domainwall", "- 0.5 * dirac.hop(self.U, psi4, lat, self.bc, sites)", "- dirac.hop(self.U, psi4, lat, self.bc, sites)",
+     pins.mobius_free_field_error, 1e-10),
+    ("domainwall", "Bv = _mix(self.B[0], self.B[1], v)", "Bv = v", pins.mobius_schur_dense_error, 1e-10),
+    ("domainwall", "return x_e - self.D_pp_inv(self.D_hop(0, t))", "return x_e - self.D_pp(self.D_hop(0, t))",
+     pins.mobius_schur_dense_error, 1e-10),
+    ("domainwall", "S[s, Ls - 1] = -mf", "S[s, Ls - 1] = mf", pins.mobius_schur_dense_error, 1e-10),
+    ("domainwall", "return _mix(self.Ainv[0].T, self.Ainv[1].T, v)", "return _mix(self.Ainv[0], self.Ainv[1], v)",
+     pins.mobius_adjoint_error, 1e-10),
+    ("domainwall", "return _mix(self.B[0].T, self.B[1].T, _g5(h))", "return _mix(self.B[0].T, self.B[1].T, h)",
+     pins.mobius_adjoint_error, 1e-10),
+    ("solvers", "p = r + (rr_new / rr) * p", "p = r", pins.cg_error, 1e-10),
+    ("solvers", "alpha = rr / dot(p, Ap).real", "alpha = rr / dot(Ap, Ap).real", pins.cg_error, 1e-10),
 ]
 
 

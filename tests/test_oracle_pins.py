@@ -143,3 +143,44 @@ def test_half_lattice_order_matches_lexicographic():
         assert np.all(np.diff(s) > 0) and len(s) == lat.V // 2
         # the k-th site of one parity is lexicographic index 2k or 2k+1
         assert np.all(s // 2 == np.arange(lat.V // 2))
+
+
+# --- Moebius domain wall and CG (Sec. 2 operators, Sec. 3 / Fig. 7 solver) -----------
+
+
+def test_mobius_overlap_relation_random_gauge():
+    assert pins.mobius_overlap_error() < 1e-12
+
+
+def test_mobius_free_field_overlap_closed_form():
+    assert pins.mobius_free_field_error() < 1e-12
+
+
+def test_mobius_schur_and_evenodd_solve_vs_dense():
+    assert pins.mobius_schur_dense_error() < 1e-12
+
+
+def test_mobius_schur_adjoint():
+    assert pins.mobius_adjoint_error() < 1e-14
+
+
+def test_shamir_gamma5_reflection_hermiticity():
+    assert pins.shamir_reflection_error() < 1e-14
+
+
+def test_cg_and_cgnr_vs_lapack():
+    assert pins.cg_error() < 1e-11
+
+
+def test_mobius_blocks_reassemble_full_operator():
+    from oracle import domainwall
+
+    dims, Ls = (4, 2, 2, 4), 5
+    lat = Lattice(dims)
+    op = domainwall.Mobius(synth.gauge_field(dims, 0.4, 93), lat, Ls, 1.8, 1.5, 0.5, 0.01)
+    psi = synth.gaussian_spinor(dims, 93, nrhs=Ls)
+    full = np.zeros_like(psi)
+    for p in (0, 1):
+        s = lat.sites_of(p)
+        full[:, s] = op.D_pp(psi[:, s]) + op.D_hop(p, psi[:, lat.sites_of(1 - p)])
+    assert pins.rel(full, op.full(psi)) < 1e-14
