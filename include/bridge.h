@@ -72,7 +72,7 @@ enum bridge_status {
  * blocks as plain 16-bit values, and compute in FP32. */
 enum bridge_prec { BRIDGE_F64 = 0, BRIDGE_F32 = 1, BRIDGE_F16 = 2, BRIDGE_BF16 = 3 };
 
-enum bridge_kind { BRIDGE_WILSON = 0, BRIDGE_CLOVER = 1 };
+enum bridge_kind { BRIDGE_WILSON = 0, BRIDGE_CLOVER = 1, BRIDGE_MOBIUS = 2 };
 
 /* Site subset of a field: one parity (half lattice) or the full lattice. */
 enum bridge_subset { BRIDGE_EVEN = 0, BRIDGE_ODD = 1, BRIDGE_FULL = 2 };
@@ -87,9 +87,30 @@ enum bridge_apply_op {
 
 typedef struct {
   int kind;     /* bridge_kind */
-  double kappa; /* hopping parameter */
-  double csw;   /* clover coefficient (ignored for WILSON) */
+  double kappa; /* hopping parameter (WILSON, CLOVER) */
+  double csw;   /* clover coefficient (CLOVER only) */
   int bc[4];    /* boundary phase per direction, +1 or -1; {1,1,1,-1} usual */
+  /* MOBIUS only (Sec. 2: Moebius domain-wall fermions, the fifth coordinate
+   * an inner index of each site).  With W = D_W(-M5) = (4 - M5) - H/2 and
+   * (P psi)_s = P_- psi_{s+1} + P_+ psi_{s-1} (P_+- = (1 +- gamma_5)/2,
+   * psi_{Ls} -> -mf psi_0, psi_{-1} -> -mf psi_{Ls-1}):
+   *   D psi = (b5 W + 1) psi + (c5 W - 1) P psi;
+   * b5 = 1, c5 = 0 is the Shamir operator.  Even-odd blocks (Eq. 1) by the
+   * parity of the four-dimensional site: D_ee = D_oo = A = (b5 (4-M5) + 1)
+   * + (c5 (4-M5) - 1) P, D_eo = -(1/2) H_eo B, D_oe = -(1/2) H_oe B with
+   * B = b5 + c5 P.  Every spinor argument then holds Ls slices per
+   * right-hand side, canonical layout [rhs][s][t][z][y][x][spin][colour][re,im]
+   * (half-lattice vectors [rhs][s][sites of one parity][spin][colour][re,im]):
+   * nrhs counts five-dimensional fields, and every buffer size stated below
+   * for an operator or solve call is multiplied by Ls.  Computed in FP64 or
+   * FP32 (prec / inner_prec F16 and BF16 return EINVAL); the solver is CG on
+   * the normal equations of D^(eo) (Sec. 3 / Fig. 7 of the paper use CG for
+   * this operator) inside the same FP64 defect correction.  Not accepted by
+   * bridge_apply, bridge_mult_Dhat_noalloc, bridge_tune or bridge_submit. */
+  int Ls;       /* fifth extent, 1 .. 32 */
+  double M5;    /* domain-wall height */
+  double b5, c5; /* Moebius coefficients */
+  double mf;    /* quark mass */
 } bridge_op;
 
 typedef struct {
@@ -156,13 +177,20 @@ int bridge_mult_Deo(bridge_lattice lat, const bridge_op* op, int prec, int out_p
 /* Schur operator D^(eo) = 1 - D_ee^-1 D_eo D_oo^-1 D_oe of Eq. 1 on even
  * half-lattice vectors.  Synchronous. */
 int bridge_mult_Dhat(bridge_lattice lat, const bridge_op* op, int prec, const double* in, double* out, int nrhs);
-/* Same three, with device buffers; work is queued on the lattice stream and
+/* Adjoint of the Schur operator, (D^(eo))^dagger = 1 - D_oe^dag D_oo^-dag
+ * D_eo^dag D_ee^-dag, on even half-lattice vectors (the normal-equation
+ * operator of the CG solve is D^(eo)^dagger D^(eo)).  MOBIUS only; EINVAL for
+ * WILSON and CLOVER.  Synchronous. */
+int bridge_mult_Dhat_dag(bridge_lattice lat, const bridge_op* op, int prec, const double* in, double* out, int nrhs);
+/* Same four, with device buffers; work is queued on the lattice stream and
  * the call returns without waiting (use bridge_sync or the stream). */
 int bridge_mult_D_dev(bridge_lattice lat, const bridge_op* op, int prec, const double* in_dev, double* out_dev, int nrhs);
 int bridge_mult_Deo_dev(bridge_lattice lat, const bridge_op* op, int prec, int out_parity, const double* in_dev,
                         double* out_dev, int nrhs);
 int bridge_mult_Dhat_dev(bridge_lattice lat, const bridge_op* op, int prec, const double* in_dev, double* out_dev,
                          int nrhs);
+int bridge_mult_Dhat_dag_dev(bridge_lattice lat, const bridge_op* op, int prec, const double* in_dev,
+                             double* out_dev, int nrhs);
 
 /* ---- operator without device allocation ------------------------------------- */
 

@@ -24,14 +24,24 @@ BRIDGE_ECUDA = -6
 BRIDGE_ESTATE = -7
 
 BRIDGE_F64, BRIDGE_F32, BRIDGE_F16, BRIDGE_BF16 = 0, 1, 2, 3
-BRIDGE_WILSON, BRIDGE_CLOVER = 0, 1
+BRIDGE_WILSON, BRIDGE_CLOVER, BRIDGE_MOBIUS = 0, 1, 2
 BRIDGE_EVEN, BRIDGE_ODD, BRIDGE_FULL = 0, 1, 2
 BRIDGE_APPLY_D, BRIDGE_APPLY_DEO, BRIDGE_APPLY_DOE, BRIDGE_APPLY_DHAT = 0, 1, 2, 3
 BRIDGE_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class bridge_op(ctypes.Structure):
-    _fields_ = [("kind", c_int), ("kappa", c_double), ("csw", c_double), ("bc", c_int * 4)]
+    _fields_ = [
+        ("kind", c_int),
+        ("kappa", c_double),
+        ("csw", c_double),
+        ("bc", c_int * 4),
+        ("Ls", c_int),
+        ("M5", c_double),
+        ("b5", c_double),
+        ("c5", c_double),
+        ("mf", c_double),
+    ]
 
 
 class bridge_solver(ctypes.Structure):
@@ -75,9 +85,11 @@ SIGNATURES = {
     "bridge_mult_D": (c_int, [_h, POINTER(bridge_op), c_int, _dp, _dp, c_int]),
     "bridge_mult_Deo": (c_int, [_h, POINTER(bridge_op), c_int, c_int, _dp, _dp, c_int]),
     "bridge_mult_Dhat": (c_int, [_h, POINTER(bridge_op), c_int, _dp, _dp, c_int]),
+    "bridge_mult_Dhat_dag": (c_int, [_h, POINTER(bridge_op), c_int, _dp, _dp, c_int]),
     "bridge_mult_D_dev": (c_int, [_h, POINTER(bridge_op), c_int, c_void_p, c_void_p, c_int]),
     "bridge_mult_Deo_dev": (c_int, [_h, POINTER(bridge_op), c_int, c_int, c_void_p, c_void_p, c_int]),
     "bridge_mult_Dhat_dev": (c_int, [_h, POINTER(bridge_op), c_int, c_void_p, c_void_p, c_int]),
+    "bridge_mult_Dhat_dag_dev": (c_int, [_h, POINTER(bridge_op), c_int, c_void_p, c_void_p, c_int]),
     "bridge_mult_Dhat_noalloc": (c_int, [_h, POINTER(bridge_op), c_int, c_void_p, c_void_p, c_int]),
     "bridge_solve": (c_int, [_h, POINTER(bridge_op), POINTER(bridge_solver), _dp, _dp, c_int, POINTER(bridge_info)]),
     "bridge_solve_dev": (

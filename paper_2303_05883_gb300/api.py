@@ -17,7 +17,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import _abi
-from ._abi import BRIDGE_CLOVER, BRIDGE_WILSON, bridge_info, bridge_kstat, bridge_op, bridge_solver, check
+from ._abi import BRIDGE_CLOVER, BRIDGE_MOBIUS, BRIDGE_WILSON, bridge_info, bridge_kstat, bridge_op, bridge_solver, check
 
 PRECISIONS = {"f64": _abi.BRIDGE_F64, "f32": _abi.BRIDGE_F32, "f16": _abi.BRIDGE_F16, "bf16": _abi.BRIDGE_BF16}
 
@@ -26,9 +26,26 @@ def _prec(p) -> int:
     return PRECISIONS[p] if isinstance(p, str) else int(p)
 
 
-def make_op(kind="wilson", kappa=0.12, csw=0.0, bc=(1, 1, 1, -1)) -> bridge_op:
-    k = {"wilson": BRIDGE_WILSON, "clover": BRIDGE_CLOVER}.get(kind, kind)
-    return bridge_op(int(k), float(kappa), float(csw), (c_int * 4)(*[int(b) for b in bc]))
+def make_op(kind="wilson", kappa=0.12, csw=0.0, bc=(1, 1, 1, -1), Ls=0, M5=0.0, b5=0.0, c5=0.0, mf=0.0) -> bridge_op:
+    k = {"wilson": BRIDGE_WILSON, "clover": BRIDGE_CLOVER, "mobius": BRIDGE_MOBIUS}.get(kind, kind)
+    return bridge_op(int(k), float(kappa), float(csw), (c_int * 4)(*[int(b) for b in bc]), int(Ls), float(M5),
+                     float(b5), float(c5), float(mf))
+
+
+def make_mobius(Ls, M5, b5, c5, mf, bc=(1, 1, 1, -1)) -> bridge_op:
+    """Moebius domain-wall operator; b5 = 1, c5 = 0 gives the Shamir operator."""
+    return make_op("mobius", 0.0, 0.0, bc, Ls, M5, b5, c5, mf)
+
+
+def _nrhs(op, a) -> int:
+    """Right-hand sides in a canonical array: its leading dimensions count
+    four-dimensional fields, Ls of them per right-hand side for MOBIUS."""
+    n4 = int(np.prod(a.shape[:-3])) if a.ndim > 3 else 1
+    if op.kind == BRIDGE_MOBIUS and op.Ls >= 1:  # (Ls < 1 is left to the library to refuse)
+        if n4 % op.Ls:
+            raise ValueError(f"a MOBIUS field holds a multiple of Ls = {op.Ls} slices, got {n4}")
+        return n4 // op.Ls
+    return n4
 
 
 def make_solver(**kw) -> bridge_solver:
@@ -102,7 +119,7 @@ def bridge_gauge_upload(lat, U, op: bridge_op | None = None) -> None:
 
 def _mult(name, lat, op, prec, psi, *extra):
     lib = _abi.load()
-    nrhs = 1 if psi.ndim == 3 else psi.shape[0]
+    nrhs = _nrhs(op, psi)
     if _is_torch_cuda(psi):
         import torch
 
@@ -135,6 +152,11 @@ def bridge_mult_Dhat(lat, op, prec, psi_even):
     return _mult("bridge_mult_Dhat", lat, op, prec, psi_even)
 
 
+def bridge_mult_Dhat_dag(lat, op, prec, psi_even):
+    """The adjoint of the Schur operator (MOBIUS operators)."""
+    return _mult("bridge_mult_Dhat_dag", lat, op, prec, psi_even)
+
+
 # --- solver -----------------------------------------------------------------------
 
 
@@ -155,7 +177,7 @@ def _infos(arr, n):
 def bridge_solve(lat, op, solver, b, x0=None, raise_on_fail=True):
     """Solve D x = b; returns (x, per-rhs info dicts)."""
     lib = _abi.load()
-    nrhs = 1 if b.ndim == 3 else b.shape[0]
+    nrhs = _nrhs(op, b)
     info = (bridge_info * nrhs)()
     if _is_torch_cuda(b):
         import torch
@@ -350,6 +372,9 @@ class Lattice:
 
     def Dhat(self, op, psi, prec="f64"):
         return bridge_mult_Dhat(self.handle, op, prec, psi)
+
+    def Dhat_dag(self, op, psi, prec="f64"):
+        return bridge_mult_Dhat_dag(self.handle, op, prec, psi)
 
     def solve(self, op, b, solver=None, x0=None, raise_on_fail=True):
         return bridge_solve(self.handle, op, solver or make_solver(), b, x0, raise_on_fail)

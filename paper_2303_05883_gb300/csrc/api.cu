@@ -4,9 +4,13 @@
 #include <cstring>
 #include <string>
 
+#include "dwf.h"
 #include "solver.h"
 
 using namespace bridge;
+
+// bridge_mult_Dhat_dag: internal selector next to bridge_apply_op
+static constexpr int APPLY_DHAT_DAG = 100;
 
 namespace bridge {
 const char* last_error_text();
@@ -43,10 +47,20 @@ struct bridge_field_s {
 
 static void check_op(const bridge_op* op) {
   BR_CHECK(op != nullptr, BRIDGE_EINVAL, "op is NULL");
-  BR_CHECK(op->kind == BRIDGE_WILSON || op->kind == BRIDGE_CLOVER, BRIDGE_EINVAL, "op.kind");
-  BR_CHECK(std::isfinite(op->kappa) && std::isfinite(op->csw), BRIDGE_EINVAL, "op.kappa / op.csw not finite");
+  BR_CHECK(op->kind == BRIDGE_WILSON || op->kind == BRIDGE_CLOVER || op->kind == BRIDGE_MOBIUS, BRIDGE_EINVAL,
+           "op.kind");
   for (int k = 0; k < 4; ++k) BR_CHECK(op->bc[k] == 1 || op->bc[k] == -1, BRIDGE_EINVAL, "op.bc must be +1 or -1");
+  if (op->kind == BRIDGE_MOBIUS)
+    check_mobius(*op);
+  else
+    BR_CHECK(std::isfinite(op->kappa) && std::isfinite(op->csw), BRIDGE_EINVAL, "op.kappa / op.csw not finite");
 }
+// Entry points that serve Wilson and clover only.
+static void check_not_mobius(const bridge_op* op, const char* what) {
+  BR_CHECK(op->kind != BRIDGE_MOBIUS, BRIDGE_EINVAL, std::string(what) + " does not take MOBIUS operators");
+}
+// Four-dimensional slices per right-hand side.
+static int slices(const bridge_op& op) { return op.kind == BRIDGE_MOBIUS ? op.Ls : 1; }
 static void check_prec(int prec) {
   BR_CHECK(prec >= BRIDGE_F64 && prec <= BRIDGE_BF16, BRIDGE_EINVAL, "precision");
 }
@@ -67,6 +81,32 @@ static char* stage(std::unique_ptr<DevBuf>& b, size_t n) {
 static void mult_dev(bridge_lattice_s* L, const bridge_op& op, int prec, int which, int out_parity, const double* in,
                      double* out, int nrhs) {
   cudaStream_t st = L->stream;
+  if (op_is_mobius(op)) {
+    BR_CHECK(prec == BRIDGE_F64 || prec == BRIDGE_F32, BRIDGE_EINVAL, "MOBIUS operators run in F64 or F32");
+    const int nq = nrhs * op.Ls;
+    if (which == BRIDGE_APPLY_D) {
+      Field& fi = workspace(L, "mult_in", prec, BRIDGE_FULL, nq);
+      Field& fo = workspace(L, "mult_out", prec, BRIDGE_FULL, nq);
+      canon_to_field(L, in, fi, st);
+      dwf_apply_d(L, op, fo, fi, st);
+      field_to_canon(L, fo, out, st);
+    } else if (which == BRIDGE_APPLY_DEO) {
+      const int q = out_parity;
+      Field& fi = workspace(L, "mult_in", prec, 1 - q, nq);
+      Field& fo = workspace(L, "mult_out", prec, q, nq);
+      canon_to_field(L, in, fi, st);
+      dwf_apply_deo(L, op, q, fo, fi, st);
+      field_to_canon(L, fo, out, st);
+    } else {
+      Field& fi = workspace(L, "mult_in", prec, BRIDGE_EVEN, nq);
+      Field& fo = workspace(L, "mult_out", prec, BRIDGE_EVEN, nq);
+      canon_to_field(L, in, fi, st);
+      dwf_apply_dhat(L, op, fo, fi, which == APPLY_DHAT_DAG, st);
+      field_to_canon(L, fo, out, st);
+    }
+    return;
+  }
+  BR_CHECK(which != APPLY_DHAT_DAG, BRIDGE_EINVAL, "bridge_mult_Dhat_dag is provided for MOBIUS operators only");
   if (which == BRIDGE_APPLY_D) {
     Field& fi = workspace(L, "mult_in", prec, BRIDGE_FULL, nrhs);
     Field& fo = workspace(L, "mult_out", prec, BRIDGE_FULL, nrhs);
@@ -102,7 +142,7 @@ static int mult_common(bridge_lattice L, const bridge_op* op, int prec, int whic
   BR_CHECK(in != nullptr && out != nullptr, BRIDGE_EINVAL, "in/out is NULL");
   std::lock_guard<std::mutex> lk(L->api_mu);
   const long sites = which == BRIDGE_APPLY_D ? L->V : L->vh;
-  const size_t n = (size_t)nrhs * sites * 24 * sizeof(double);
+  const size_t n = (size_t)nrhs * slices(*op) * sites * 24 * sizeof(double);
   if (host) {
     double* din = reinterpret_cast<double*>(stage(L->stage_in, n));
     double* dout = reinterpret_cast<double*>(stage(L->stage_out, n));
@@ -129,7 +169,7 @@ static int solve_common(bridge_lattice L, const bridge_op* op, const bridge_solv
   if (nrhs == 0) return BRIDGE_OK;
   BR_CHECK(b != nullptr && x != nullptr, BRIDGE_EINVAL, "b/x is NULL");
   std::lock_guard<std::mutex> lk(L->api_mu);
-  const size_t n = (size_t)nrhs * L->V * 24 * sizeof(double);
+  const size_t n = (size_t)nrhs * slices(*op) * L->V * 24 * sizeof(double);
   const double* db = b;
   double* dx = x;
   if (host) {
@@ -139,7 +179,9 @@ static int solve_common(bridge_lattice L, const bridge_op* op, const bridge_solv
     BR_CUDA(cudaMemcpyAsync(dx, x, n, cudaMemcpyHostToDevice, L->stream));
   }
   int status;
-  {
+  if (op_is_mobius(*op)) {
+    status = dwf_solve(L, *op, *s, db, dx, nrhs, info);
+  } else {
     SolveState S(L, *op, *s, nrhs, L->stream, db, dx);
     while (!S.advance()) BR_CUDA(cudaEventSynchronize(S.wait_event()));
     if (info)
@@ -273,6 +315,13 @@ int bridge_mult_Deo(bridge_lattice L, const bridge_op* op, int prec, int out_par
 int bridge_mult_Dhat(bridge_lattice L, const bridge_op* op, int prec, const double* in, double* out, int nrhs) {
   return mult_common(L, op, prec, BRIDGE_APPLY_DHAT, 0, in, out, nrhs, true);
 }
+int bridge_mult_Dhat_dag(bridge_lattice L, const bridge_op* op, int prec, const double* in, double* out, int nrhs) {
+  return mult_common(L, op, prec, APPLY_DHAT_DAG, 0, in, out, nrhs, true);
+}
+int bridge_mult_Dhat_dag_dev(bridge_lattice L, const bridge_op* op, int prec, const double* in, double* out,
+                             int nrhs) {
+  return mult_common(L, op, prec, APPLY_DHAT_DAG, 0, in, out, nrhs, false);
+}
 int bridge_mult_D_dev(bridge_lattice L, const bridge_op* op, int prec, const double* in, double* out, int nrhs) {
   return mult_common(L, op, prec, BRIDGE_APPLY_D, 0, in, out, nrhs, false);
 }
@@ -377,6 +426,7 @@ int bridge_apply(bridge_lattice L, const bridge_op* op, int which, bridge_field 
   BR_API_BEGIN
   check_lat(L, true);
   check_op(op);
+  check_not_mobius(op, "bridge_apply");
   BR_CHECK(out != nullptr && in != nullptr, BRIDGE_EINVAL, "NULL field");
   BR_CHECK(out->L == L && in->L == L, BRIDGE_EINVAL, "field belongs to another lattice");
   BR_CHECK(out->f.prec == in->f.prec, BRIDGE_EINVAL, "fields differ in precision");
@@ -496,6 +546,7 @@ int bridge_submit(bridge_lattice L, const bridge_op* op, const bridge_solver* s,
   BR_API_BEGIN
   check_lat(L, true);
   check_op(op);
+  check_not_mobius(op, "bridge_submit");
   BR_CHECK(s != nullptr && b != nullptr && out != nullptr, BRIDGE_EINVAL, "NULL argument");
   BR_CHECK(s->tol > 0, BRIDGE_EINVAL, "tol must be > 0");
   if (s->mixed) check_prec(s->inner_prec);

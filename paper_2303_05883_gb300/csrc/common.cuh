@@ -536,4 +536,14 @@ struct BiCGScalars {
 };
 enum Done { RUNNING = 0, CONVERGED = 1, BREAKDOWN = 2, MAXITER = 3 };
 
+// Conjugate-gradient scalars of one right-hand side, kept on the device.
+struct CGScalars {
+  double rr;     // |r|^2 of the current residual
+  double b2;     // |b|^2 of the system solved (sets the stopping threshold)
+  double pq;     // <p, A p> = |D p|^2 for A = D^dagger D
+  double alpha, beta;
+  double tol2;   // host stages tol^2; FIN_CG_INIT turns it into tol^2 |b|^2
+  int iter, done, max_iter, pad;
+};
+
 }  // namespace bridge

@@ -1,0 +1,782 @@
+// Moebius domain-wall operator and solver (host side).
+//
+// Operator and even-odd blocks as in dwf.cuh.  The Schur operator of Eq. 1
+// and its adjoint are applied in three launches each:
+//   D^ x    = x - A^-1 (-H_eo/2) (B A^-1) (-H_oe/2) (B x)
+//           : mix B;        hop_oe, epilogue B A^-1;     hop_eo, epilogue A^-1, + x
+//   D^dag y = y - B^T g5 (-H_eo/2) (A^-T B^T) (-H_oe/2) (g5 A^-T y)
+//           : mix g5 A^-T;  hop_oe, epilogue A^-T B^T;   hop_eo, epilogue B^T g5, + y
+// (using (H_eo)^dagger = g5 H_oe g5 and that g5 commutes with every s-matrix).
+//
+// Solver: CG (Hestenes-Stiefel) on the normal equations D^dag D^ x_e = D^dag b^_e
+// of the even-odd system -- the paper's solver for this operator is CG
+// (Sec. 3, Fig. 7) -- in FP32 (or FP64) inside the FP64 defect correction
+// r = b - D x, x += e of the Wilson/clover solver.  Per CG iteration:
+//   1 mix   p = r + beta p, xt = B p
+//   2 hop   t = B A^-1 (-H_oe/2) xt
+//   3 hop   q = p + A^-1 (H_eo/2) t,           |q|^2 -> alpha = |r|^2 / |q|^2
+//   4 mix   xt = g5 A^-T q
+//   5 hop   t = A^-T B^T (-H_oe/2) xt
+//   6 hop   v = q + B^T g5 (H_eo/2) t; x += alpha p; r -= alpha v; |r|^2 -> beta
+// with the scalars on the device and a host poll every check_every iterations.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "dwf.h"
+#include "solver.h"
+
+namespace bridge {
+
+bool op_is_mobius(const bridge_op& op) { return op.kind == BRIDGE_MOBIUS; }
+
+void check_mobius(const bridge_op& op) {
+  BR_CHECK(op.Ls >= 1 && op.Ls <= 32, BRIDGE_EINVAL, "op.Ls must be in 1..32");
+  BR_CHECK(std::isfinite(op.M5) && std::isfinite(op.b5) && std::isfinite(op.c5) && std::isfinite(op.mf),
+           BRIDGE_EINVAL, "op.M5 / b5 / c5 / mf not finite");
+}
+
+// ------------------------------------------------------------ s-matrices
+namespace {
+
+using Mat = std::vector<double>;  // Ls x Ls, row major
+
+Mat eye(int n) {
+  Mat m(n * n, 0.0);
+  for (int i = 0; i < n; ++i) m[i * n + i] = 1.0;
+  return m;
+}
+// The s-part of P on one chirality: (S v)_s = v_{s-1} for chirality +,
+// v_{s+1} for chirality -, with -mf on the wrap.
+Mat shift(int n, int chi, double mf) {
+  Mat m(n * n, 0.0);
+  for (int s = 0; s < n; ++s) {
+    if (chi == 0) {
+      if (s >= 1) m[s * n + s - 1] = 1.0;
+      else m[s * n + n - 1] = -mf;
+    } else {
+      if (s + 1 < n) m[s * n + s + 1] = 1.0;
+      else m[s * n + 0] = -mf;
+    }
+  }
+  return m;
+}
+Mat axpy(double a, const Mat& x, double b, const Mat& y) {
+  Mat m(x.size());
+  for (size_t i = 0; i < x.size(); ++i) m[i] = a * x[i] + b * y[i];
+  return m;
+}
+Mat matmul(const Mat& x, const Mat& y, int n) {
+  Mat m(n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j) m[i * n + j] += x[i * n + k] * y[k * n + j];
+  return m;
+}
+Mat transpose(const Mat& x, int n) {
+  Mat m(n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) m[j * n + i] = x[i * n + j];
+  return m;
+}
+// Gauss-Jordan elimination with partial pivoting.
+Mat inverse(const Mat& x, int n) {
+  Mat a = x, inv = eye(n);
+  double scale = 0.0;
+  for (double v : x) scale = std::max(scale, std::fabs(v));
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[r * n + c]) > std::fabs(a[piv * n + c])) piv = r;
+    BR_CHECK(std::fabs(a[piv * n + c]) > 1e-13 * scale, BRIDGE_EINVAL,
+             "Moebius D_ee is singular for these Ls, M5, b5, c5, mf");
+    if (piv != c)
+      for (int j = 0; j < n; ++j) {
+        std::swap(a[c * n + j], a[piv * n + j]);
+        std::swap(inv[c * n + j], inv[piv * n + j]);
+      }
+    const double d = 1.0 / a[c * n + c];
+    for (int j = 0; j < n; ++j) {
+      a[c * n + j] *= d;
+      inv[c * n + j] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = a[r * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        a[r * n + j] -= f * a[c * n + j];
+        inv[r * n + j] -= f * inv[c * n + j];
+      }
+    }
+  }
+  return inv;
+}
+
+}  // namespace
+
+std::shared_ptr<DwfSet> dwf_set(bridge_lattice_s* L, const bridge_op& op) {
+  check_mobius(op);
+  std::lock_guard<std::mutex> lk(L->dwf_mu);
+  for (size_t i = 0; i < L->dwf_sets.size(); ++i) {
+    auto& s = L->dwf_sets[i];
+    if (s->Ls == op.Ls && s->M5 == op.M5 && s->b == op.b5 && s->c == op.c5 && s->mf == op.mf) {
+      auto keep = s;
+      L->dwf_sets.erase(L->dwf_sets.begin() + i);
+      L->dwf_sets.insert(L->dwf_sets.begin(), keep);
+      return keep;
+    }
+  }
+  const int n = op.Ls;
+  const double alpha = 4.0 - op.M5;
+  std::vector<double> all((size_t)DWF_NMAT * 2 * n * n);
+  for (int chi = 0; chi < 2; ++chi) {
+    const Mat I = eye(n), S = shift(n, chi, op.mf);
+    const Mat A = axpy(op.b5 * alpha + 1.0, I, op.c5 * alpha - 1.0, S);
+    const Mat B = axpy(op.b5, I, op.c5, S);
+    const Mat Ai = inverse(A, n);
+    const Mat BAi = matmul(B, Ai, n);
+    const double g5 = chi == 0 ? 1.0 : -1.0;
+    Mat mats[DWF_NMAT];
+    mats[DM_B] = B;
+    mats[DM_BAINV] = BAi;
+    mats[DM_AINV] = Ai;
+    mats[DM_G5AINVT] = axpy(g5, transpose(Ai, n), 0.0, I);
+    mats[DM_AINVTBT] = transpose(BAi, n);
+    mats[DM_BTG5] = axpy(g5, transpose(B, n), 0.0, I);
+    mats[DM_A] = A;
+    mats[DM_MA] = axpy(-1.0, A, 0.0, I);
+    for (int m = 0; m < DWF_NMAT; ++m)
+      std::copy(mats[m].begin(), mats[m].end(), all.begin() + ((size_t)m * 2 + chi) * n * n);
+  }
+  auto set = std::make_shared<DwfSet>();
+  set->Ls = n;
+  set->M5 = op.M5;
+  set->b = op.b5;
+  set->c = op.c5;
+  set->mf = op.mf;
+  std::vector<float> allf(all.begin(), all.end());
+  set->mats[0].reset(new DevBuf(all.size() * sizeof(double)));
+  set->mats[1].reset(new DevBuf(allf.size() * sizeof(float)));
+  BR_CUDA(cudaMemcpy(set->mats[0]->ptr, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice));
+  BR_CUDA(cudaMemcpy(set->mats[1]->ptr, allf.data(), allf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  L->dwf_sets.insert(L->dwf_sets.begin(), set);
+  if (L->dwf_sets.size() > 4) L->dwf_sets.resize(4);
+  return set;
+}
+
+// ------------------------------------------------------------ launches
+namespace {
+
+long site_bytes(int prec) { return prec == P_F64 ? 192 : 96; }
+long link_bytes(int prec) { return prec == P_F64 ? 144 : 48; }
+
+int sites_per_block(int prec, int Ls) {
+  const int target = prec == P_F64 ? 128 : 256;
+  return std::max(1, target / Ls);
+}
+
+struct DwfHop {
+  int prec = P_F32, cls = K_DWF_HOP;
+  int out_parity = 0, Ls = 1, nrhs = 1;
+  int m1 = -1, m2 = -1;  // DwfMat ids, -1 = none
+  bool self_plain = false;
+  int epi = DE_NONE;
+  double scale = -0.5, s2 = 1.0, caux = 0.0;
+  const char *in = nullptr, *self = nullptr, *aux = nullptr, *p = nullptr;
+  char *out = nullptr, *x = nullptr, *r = nullptr;
+  long in_bs = 0, out_bs = 0, self_bs = 0, aux_bs = 0, cg_bs = 0;
+  RedArgs red{};
+};
+
+void run_dwf_hop(bridge_lattice_s* L, const DwfSet& set, const bridge_op& op, const DwfHop& c, cudaStream_t st) {
+  DwfArgs a;
+  std::memset(static_cast<void*>(&a), 0, sizeof(a));
+  a.g = L->g;
+  a.out_parity = c.out_parity;
+  a.Ls = c.Ls;
+  a.nrhs = c.nrhs;
+  a.ns = sites_per_block(c.prec, c.Ls);
+  a.nsb = (int)((L->vh + a.ns - 1) / a.ns);
+  a.scale = c.scale;
+  a.scalef = (float)c.scale;
+  a.s2 = c.s2;
+  a.s2f = (float)c.s2;
+  a.caux = c.caux;
+  a.cauxf = (float)c.caux;
+  for (int k = 0; k < 4; ++k) {
+    a.bc[k] = op.bc[k];
+    a.bcf[k] = (float)op.bc[k];
+  }
+  a.in = c.in;
+  a.in_bs = c.in_bs;
+  a.out = c.out;
+  a.out_bs = c.out_bs;
+  a.self = c.self;
+  a.self_bs = c.self_bs;
+  a.aux = c.aux;
+  a.aux_bs = c.aux_bs;
+  a.x = c.x;
+  a.r = c.r;
+  a.p = c.p;
+  a.cg_bs = c.cg_bs;
+  a.gauge = gauge_ptr(L, c.prec);
+  a.m1 = c.m1 >= 0 ? set.mat(c.prec, c.m1) : nullptr;
+  a.m2 = c.m2 >= 0 ? set.mat(c.prec, c.m2) : nullptr;
+  a.red = c.red;
+  const int m2mode = c.self_plain ? DM2_PLAIN : c.m2 >= 0 ? DM2_DENSE : DM2_NONE;
+  if (c.epi != DE_NONE && a.red.partials == nullptr) {
+    ensure_red_scratch(L, (long)a.nsb * c.nrhs, c.nrhs);
+    a.red.partials = reinterpret_cast<double*>(L->red_partials->ptr);
+    a.red.counter = reinterpret_cast<unsigned*>(L->red_counter->ptr);
+    a.red.result = reinterpret_cast<double*>(L->red_result->ptr);
+    if (a.red.fin == FIN_NONE) a.red.fin = FIN_STORE;
+  }
+  // algorithmic cost: every operand read once and the output written once
+  // per (site, slice); links once per four-dimensional site
+  const double S = (double)site_bytes(c.prec);
+  double per = 2 * S;
+  double fl = 1320 + 24;
+  if (c.m1 >= 0) fl += 48.0 * c.Ls;
+  if (m2mode == DM2_PLAIN) per += S, fl += 48;
+  if (m2mode == DM2_DENSE) per += S, fl += 48.0 * c.Ls;
+  if (c.aux) per += S, fl += 48;
+  if (c.epi == DE_NORM) fl += 48;
+  if (c.epi == DE_CGUPD) per += 4 * S, fl += 144;  // x, r read and written, p read; out not stored
+  const double sites5 = (double)L->vh * c.Ls * c.nrhs;
+  const double bytes = sites5 * per + (double)L->vh * 8 * link_bytes(c.prec);
+  note_launch(L, c.cls, bytes, sites5 * fl, st, true);
+  BR_CHECK(launch_dwf_hop(c.prec, c.m1 >= 0, m2mode, c.epi, a, st), BRIDGE_EINVAL,
+           "domain-wall hop variant not instantiated");
+  note_launch(L, c.cls, bytes, sites5 * fl, st, false);
+  BR_CUDA(cudaGetLastError());
+}
+
+struct DwfMix {
+  int prec = P_F32, mode = DX_PLAIN, Ls = 1, nrhs = 1, m = DM_B;
+  const char* in = nullptr;
+  const char* r = nullptr;
+  char *out = nullptr, *p = nullptr;
+  long in_bs = 0, out_bs = 0, cg_bs = 0;
+  RedArgs red{};
+};
+
+void run_dwf_mix(bridge_lattice_s* L, const DwfSet& set, const DwfMix& c, cudaStream_t st) {
+  DwfMixArgs a;
+  std::memset(static_cast<void*>(&a), 0, sizeof(a));
+  a.vh = (uint32_t)L->vh;
+  a.Ls = c.Ls;
+  a.nrhs = c.nrhs;
+  a.ns = sites_per_block(c.prec, c.Ls);
+  a.nsb = (int)((L->vh + a.ns - 1) / a.ns);
+  a.in_bs = c.in_bs;
+  a.out_bs = c.out_bs;
+  a.cg_bs = c.cg_bs;
+  a.out = c.out;
+  a.in = c.in;
+  a.p = c.p;
+  a.r = c.r;
+  a.m = set.mat(c.prec, c.m);
+  a.red = c.red;
+  const double S = (double)site_bytes(c.prec);
+  const double sites5 = (double)L->vh * c.Ls * c.nrhs;
+  const double bytes = sites5 * (c.mode == DX_CGP ? 4 : 2) * S;
+  const double fl = sites5 * (48.0 * c.Ls + (c.mode == DX_CGP ? 48 : 0));
+  note_launch(L, K_DWF_MIX, bytes, fl, st, true);
+  BR_CHECK(launch_dwf_mix(c.prec, c.mode, a, st), BRIDGE_EINVAL, "domain-wall mix precision");
+  note_launch(L, K_DWF_MIX, bytes, fl, st, false);
+  BR_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ operators
+void dwf_apply_deo(bridge_lattice_s* L, const bridge_op& op, int q, const Field& out, const Field& in,
+                   cudaStream_t st) {
+  auto set = dwf_set(L, op);
+  const int nrhs = in.nrhs / op.Ls;
+  Field& tmp = workspace(L, "dwf_b", in.prec, 1 - q, in.nrhs);
+  DwfMix m;
+  m.prec = in.prec;
+  m.Ls = op.Ls;
+  m.nrhs = nrhs;
+  m.m = DM_B;
+  m.in = in.ptr(1 - q);
+  m.in_bs = in.rs;
+  m.out = tmp.ptr(1 - q);
+  m.out_bs = tmp.rs;
+  run_dwf_mix(L, *set, m, st);
+  DwfHop h;
+  h.prec = in.prec;
+  h.cls = K_DWF_HOP;
+  h.out_parity = q;
+  h.Ls = op.Ls;
+  h.nrhs = nrhs;
+  h.scale = -0.5;
+  h.in = tmp.ptr(1 - q);
+  h.in_bs = tmp.rs;
+  h.out = out.ptr(q);
+  h.out_bs = out.rs;
+  run_dwf_hop(L, *set, op, h, st);
+}
+
+void dwf_apply_d(bridge_lattice_s* L, const bridge_op& op, const Field& out, const Field& in, cudaStream_t st) {
+  auto set = dwf_set(L, op);
+  const int nrhs = in.nrhs / op.Ls;
+  Field& tmp = workspace(L, "dwf_bfull", in.prec, BRIDGE_FULL, in.nrhs);
+  for (int p = 0; p < 2; ++p) {
+    DwfMix m;
+    m.prec = in.prec;
+    m.Ls = op.Ls;
+    m.nrhs = nrhs;
+    m.m = DM_B;
+    m.in = in.ptr(p);
+    m.in_bs = in.rs;
+    m.out = tmp.ptr(p);
+    m.out_bs = tmp.rs;
+    run_dwf_mix(L, *set, m, st);
+  }
+  for (int q = 0; q < 2; ++q) {
+    DwfHop h;
+    h.prec = in.prec;
+    h.cls = K_DWF_HOP;
+    h.out_parity = q;
+    h.Ls = op.Ls;
+    h.nrhs = nrhs;
+    h.scale = -0.5;
+    h.in = tmp.ptr(1 - q);
+    h.in_bs = tmp.rs;
+    h.m2 = DM_A;
+    h.self = in.ptr(q);
+    h.self_bs = in.rs;
+    h.out = out.ptr(q);
+    h.out_bs = out.rs;
+    run_dwf_hop(L, *set, op, h, st);
+  }
+}
+
+// D^ (dagger = false) or D^dag on even fields: three launches through the
+// scratch fields xt (even) and t (odd).
+namespace {
+struct SchurIO {
+  int prec, Ls, nrhs;
+  const char* in;
+  long in_bs;
+  char* out;
+  long out_bs;
+  char* xt;
+  long xt_bs;
+  char* t;
+  long t_bs;
+};
+
+void schur_mix_and_pass1(bridge_lattice_s* L, const DwfSet& set, const bridge_op& op, const SchurIO& io, bool dagger,
+                         const RedArgs& red, cudaStream_t st) {
+  DwfMix m;
+  m.prec = io.prec;
+  m.Ls = io.Ls;
+  m.nrhs = io.nrhs;
+  m.m = dagger ? DM_G5AINVT : DM_B;
+  m.in = io.in;
+  m.in_bs = io.in_bs;
+  m.out = io.xt;
+  m.out_bs = io.xt_bs;
+  m.red = red;
+  run_dwf_mix(L, set, m, st);
+  DwfHop h;
+  h.prec = io.prec;
+  h.cls = K_DWF_SCHUR1;
+  h.out_parity = 1;
+  h.Ls = io.Ls;
+  h.nrhs = io.nrhs;
+  h.scale = -0.5;
+  h.m1 = dagger ? DM_AINVTBT : DM_BAINV;
+  h.in = io.xt;
+  h.in_bs = io.xt_bs;
+  h.out = io.t;
+  h.out_bs = io.t_bs;
+  h.red = red;
+  run_dwf_hop(L, set, op, h, st);
+}
+
+// Pass 2: out = in + M (H_eo / 2) t with M = A^-1 (D^) or B^T g5 (D^dag).
+DwfHop schur_pass2(const bridge_op& op, const SchurIO& io, bool dagger) {
+  DwfHop h;
+  h.prec = io.prec;
+  h.cls = K_DWF_SCHUR2;
+  h.out_parity = 0;
+  h.Ls = io.Ls;
+  h.nrhs = io.nrhs;
+  h.scale = 0.5;
+  h.m1 = dagger ? DM_BTG5 : DM_AINV;
+  h.self_plain = true;
+  h.s2 = 1.0;
+  h.self = io.in;
+  h.self_bs = io.in_bs;
+  h.in = io.t;
+  h.in_bs = io.t_bs;
+  h.out = io.out;
+  h.out_bs = io.out_bs;
+  (void)op;
+  return h;
+}
+}  // namespace
+
+void dwf_apply_dhat(bridge_lattice_s* L, const bridge_op& op, const Field& out, const Field& in, bool dagger,
+                    cudaStream_t st) {
+  auto set = dwf_set(L, op);
+  Field& xt = workspace(L, "dwf_xt", in.prec, BRIDGE_EVEN, in.nrhs);
+  Field& t = workspace(L, "dwf_t", in.prec, BRIDGE_ODD, in.nrhs);
+  SchurIO io{in.prec, op.Ls, in.nrhs / op.Ls, in.ptr(0), in.rs, out.ptr(0), out.rs, xt.ptr(0), xt.rs, t.ptr(1), t.rs};
+  schur_mix_and_pass1(L, *set, op, io, dagger, RedArgs{}, st);
+  run_dwf_hop(L, *set, op, schur_pass2(op, io, dagger), st);
+}
+
+// ------------------------------------------------------------ solver
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Per right-hand-side sums over its Ls slices of the per-slice |f|^2 of one
+// full five-dimensional field.
+std::vector<double> rhs_norms(bridge_lattice_s* L, const Field& f, int Ls, cudaStream_t st) {
+  const int nq = f.nrhs;
+  ensure_red_scratch(L, (L->vh + 255) / 256 * (long)nq, nq);
+  std::vector<double> out(nq / Ls, 0.0), h((size_t)nq * 4);
+  for (int p = 0; p < 2; ++p) {
+    RedArgs red;
+    red.partials = reinterpret_cast<double*>(L->red_partials->ptr);
+    red.counter = reinterpret_cast<unsigned*>(L->red_counter->ptr);
+    red.result = reinterpret_cast<double*>(L->red_result->ptr);
+    red.fin = FIN_STORE;
+    norm2_field(L, f, p, red, st);
+    BR_CUDA(cudaMemcpyAsync(h.data(), red.result, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    BR_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < nq; ++q) out[q / Ls] += h[(size_t)q * 4];
+  }
+  return out;
+}
+
+}  // namespace
+
+int dwf_solve(bridge_lattice_s* L, const bridge_op& op, const bridge_solver& prm, const double* b_dev, double* x_dev,
+              int nrhs, bridge_info* info_out) {
+  check_mobius(op);
+  const double t0 = now_s();
+  cudaStream_t st = L->stream;
+  const int Ls = op.Ls, nq = nrhs * Ls;
+  const int P = prm.mixed ? prm.inner_prec : P_F64;
+  BR_CHECK(P == P_F64 || P == P_F32, BRIDGE_EINVAL, "Moebius solves run their inner CG in F64 or F32");
+  const double inner_tol = prm.inner_tol > 0 ? prm.inner_tol : (P == P_F64 ? std::max(prm.tol * 0.1, 1e-14) : 1e-6);
+  const int max_outer = prm.max_outer > 0 ? prm.max_outer : 50;
+  const int check_every = prm.check_every > 0 ? prm.check_every : 16;
+  const long max_iter = prm.max_iter > 0 ? prm.max_iter : 20000;
+  auto set = dwf_set(L, op);
+  gauge_ptr(L, P_F64);
+  gauge_ptr(L, P);
+
+  // FP64 fields of the outer loop
+  Field b64 = make_field(P_F64, BRIDGE_FULL, nq, L->vh);
+  Field x64 = make_field(P_F64, BRIDGE_FULL, nq, L->vh);
+  Field r64 = make_field(P_F64, BRIDGE_FULL, nq, L->vh);
+  Field t64 = make_field(P_F64, BRIDGE_FULL, nq, L->vh);
+  canon_to_field(L, b_dev, b64, st);
+  canon_to_field(L, x_dev, x64, st);
+  // inner fields
+  Field rin = make_field(P, BRIDGE_FULL, nq, L->vh);
+  Field bh = make_field(P, BRIDGE_EVEN, nq, L->vh), cr = make_field(P, BRIDGE_EVEN, nq, L->vh);
+  Field xe = make_field(P, BRIDGE_EVEN, nq, L->vh), pe = make_field(P, BRIDGE_EVEN, nq, L->vh);
+  Field xt = make_field(P, BRIDGE_EVEN, nq, L->vh), qv = make_field(P, BRIDGE_EVEN, nq, L->vh);
+  Field to = make_field(P, BRIDGE_ODD, nq, L->vh), eo = make_field(P, BRIDGE_ODD, nq, L->vh);
+
+  // CG scalars and reduction scratch of this solve (sized for the FP64
+  // launches, which have the smaller blocks)
+  const int ns = std::min(sites_per_block(P, Ls), sites_per_block(P_F64, Ls));
+  const long nsb = (L->vh + ns - 1) / ns;
+  DevBuf sc(sizeof(CGScalars) * nrhs), partials(sizeof(double) * 4 * nsb * nrhs), counter(256);
+  DevBuf mask((size_t)nq * sizeof(int)), resbuf(sizeof(double) * 4 * nrhs * 2);
+  PinnedBuf h_sc(sizeof(CGScalars) * nrhs), h_res(sizeof(double) * 4 * nrhs * 2);
+  BR_CUDA(cudaMemsetAsync(counter.ptr, 0, 256, st));
+  auto red_of = [&](int fin, int check_done) {
+    RedArgs r;
+    r.partials = reinterpret_cast<double*>(partials.ptr);
+    r.counter = reinterpret_cast<unsigned*>(counter.ptr);
+    r.cg = reinterpret_cast<CGScalars*>(sc.ptr);
+    r.fin = fin;
+    r.check_done = check_done;
+    return r;
+  };
+
+  std::vector<double> b2 = rhs_norms(L, b64, Ls, st);
+  std::vector<double> x02 = rhs_norms(L, x64, Ls, st);
+  bool have_x = false;
+  for (double v : x02) have_x = have_x || v != 0.0;
+
+  std::vector<bridge_info> info(nrhs);
+  for (auto& i : info) std::memset(&i, 0, sizeof(i));
+  std::vector<int> done(nrhs, 0), failed(nrhs, 0);
+  std::vector<double> r2(nrhs, 0.0);
+  std::vector<int> hmask(nq);
+  long total_iters = 0;
+  // right-hand sides with b = 0 have x = 0
+  for (int r = 0; r < nrhs; ++r)
+    if (b2[r] == 0.0) {
+      for (int s = 0; s < Ls; ++s)
+        BR_CUDA(cudaMemsetAsync(x64.buf->ptr + (long)(r * Ls + s) * x64.rs, 0, x64.rs, st));
+      done[r] = 1;
+    }
+
+  for (int outer = 0;; ++outer) {
+    // ---- FP64 residual r = b - A x + (H/2) (B x)
+    const Field* defect = &b64;
+    if (outer > 0 || have_x) {
+      for (int p = 0; p < 2; ++p) {
+        DwfMix m;
+        m.prec = P_F64;
+        m.Ls = Ls;
+        m.nrhs = nrhs;
+        m.m = DM_B;
+        m.in = x64.ptr(p);
+        m.in_bs = x64.rs;
+        m.out = t64.ptr(p);
+        m.out_bs = t64.rs;
+        run_dwf_mix(L, *set, m, st);
+      }
+      for (int q = 0; q < 2; ++q) {
+        DwfHop h;
+        h.prec = P_F64;
+        h.cls = K_DWF_RESID;
+        h.out_parity = q;
+        h.Ls = Ls;
+        h.nrhs = nrhs;
+        h.scale = 0.5;
+        h.in = t64.ptr(1 - q);
+        h.in_bs = t64.rs;
+        h.m2 = DM_MA;
+        h.self = x64.ptr(q);
+        h.self_bs = x64.rs;
+        h.aux = b64.ptr(q);
+        h.aux_bs = b64.rs;
+        h.caux = 1.0;
+        h.out = r64.ptr(q);
+        h.out_bs = r64.rs;
+        h.epi = DE_NORM;
+        h.red = red_of(FIN_STORE, 0);
+        h.red.result = reinterpret_cast<double*>(resbuf.ptr) + q * 4 * nrhs;
+        run_dwf_hop(L, *set, op, h, st);
+      }
+      BR_CUDA(cudaMemcpyAsync(h_res.ptr, resbuf.ptr, sizeof(double) * 8 * nrhs, cudaMemcpyDeviceToHost, st));
+      BR_CUDA(cudaStreamSynchronize(st));
+      const double* hr = static_cast<const double*>(h_res.ptr);
+      for (int r = 0; r < nrhs; ++r) r2[r] = hr[r * 4] + hr[4 * nrhs + r * 4];
+      defect = &r64;
+    } else {
+      r2 = b2;
+    }
+    bool any = false;
+    for (int r = 0; r < nrhs; ++r) {
+      if (b2[r] == 0.0) {
+        info[r].true_rel_residual = 0.0;
+        continue;
+      }
+      const double rel = std::sqrt(r2[r] / b2[r]);
+      info[r].true_rel_residual = rel;
+      info[r].outer_iters = outer;
+      if (!std::isfinite(rel)) failed[r] = 1;
+      if (rel <= prm.tol) done[r] = 1;
+      if (!done[r] && !failed[r]) any = true;
+    }
+    if (!any || outer >= max_outer || total_iters >= max_iter) break;
+
+    // ---- inner solve of D e = defect for the active right-hand sides
+    for (int q = 0; q < nq; ++q) hmask[q] = (!done[q / Ls] && !failed[q / Ls]) ? 1 : 0;
+    BR_CUDA(cudaMemcpyAsync(mask.ptr, hmask.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, st));
+    const int* dmask = reinterpret_cast<const int*>(mask.ptr);
+    if (P == P_F64) {
+      // the FP64 inner solve reads the defect directly
+      BR_CUDA(cudaMemcpyAsync(rin.buf->ptr, defect->buf->ptr, rin.buf->bytes, cudaMemcpyDeviceToDevice, st));
+      for (int q = 0; q < nq; ++q)
+        if (!hmask[q]) BR_CUDA(cudaMemsetAsync(rin.buf->ptr + (long)q * rin.rs, 0, rin.rs, st));
+    } else {
+      convert_field(L, *defect, rin, 0, st, dmask);
+      convert_field(L, *defect, rin, 1, st, dmask);
+    }
+    // prepare: bh = A^-1 r_e + A^-1 (H_eo/2) (B A^-1 r_o)
+    {
+      DwfMix m;
+      m.prec = P;
+      m.Ls = Ls;
+      m.nrhs = nrhs;
+      m.m = DM_BAINV;
+      m.in = rin.ptr(1);
+      m.in_bs = rin.rs;
+      m.out = to.ptr(1);
+      m.out_bs = to.rs;
+      run_dwf_mix(L, *set, m, st);
+      DwfHop h;
+      h.prec = P;
+      h.cls = K_DWF_PREP;
+      h.out_parity = 0;
+      h.Ls = Ls;
+      h.nrhs = nrhs;
+      h.scale = 0.5;
+      h.m1 = DM_AINV;
+      h.m2 = DM_AINV;
+      h.self = rin.ptr(0);
+      h.self_bs = rin.rs;
+      h.in = to.ptr(1);
+      h.in_bs = to.rs;
+      h.out = bh.ptr(0);
+      h.out_bs = bh.rs;
+      run_dwf_hop(L, *set, op, h, st);
+    }
+    // CG scalars: tolerance and the iteration budget left
+    {
+      std::vector<CGScalars> hs(nrhs);
+      for (auto& g : hs) {
+        std::memset(&g, 0, sizeof(g));
+        g.tol2 = inner_tol * inner_tol;
+        g.max_iter = (int)std::max<long>(1, max_iter - total_iters);
+      }
+      BR_CUDA(cudaMemcpyAsync(sc.ptr, hs.data(), sizeof(CGScalars) * nrhs, cudaMemcpyHostToDevice, st));
+    }
+    // r = b' = D^dag bh, |b'|^2 -> FIN_CG_INIT; x = p = 0
+    SchurIO dag{P, Ls, nrhs, bh.ptr(0), bh.rs, cr.ptr(0), cr.rs, xt.ptr(0), xt.rs, to.ptr(1), to.rs};
+    schur_mix_and_pass1(L, *set, op, dag, true, RedArgs{}, st);
+    {
+      DwfHop h = schur_pass2(op, dag, true);
+      h.epi = DE_NORM;
+      h.red = red_of(FIN_CG_INIT, 0);
+      run_dwf_hop(L, *set, op, h, st);
+    }
+    BR_CUDA(cudaMemsetAsync(xe.buf->ptr, 0, xe.buf->bytes, st));
+    BR_CUDA(cudaMemsetAsync(pe.buf->ptr, 0, pe.buf->bytes, st));
+
+    const RedArgs skip = red_of(FIN_NONE, 1);
+    SchurIO fwd{P, Ls, nrhs, pe.ptr(0), pe.rs, qv.ptr(0), qv.rs, xt.ptr(0), xt.rs, to.ptr(1), to.rs};
+    SchurIO bwd{P, Ls, nrhs, qv.ptr(0), qv.rs, nullptr, 0, xt.ptr(0), xt.rs, to.ptr(1), to.rs};
+    auto iteration = [&]() {
+      // 1: p = r + beta p, xt = B p
+      DwfMix m;
+      m.prec = P;
+      m.mode = DX_CGP;
+      m.Ls = Ls;
+      m.nrhs = nrhs;
+      m.m = DM_B;
+      m.p = pe.ptr(0);
+      m.r = cr.ptr(0);
+      m.cg_bs = pe.rs;
+      m.out = xt.ptr(0);
+      m.out_bs = xt.rs;
+      m.red = skip;
+      run_dwf_mix(L, *set, m, st);
+      // 2, 3: q = D^ p, |q|^2 -> alpha
+      DwfHop h1;
+      h1.prec = P;
+      h1.cls = K_DWF_SCHUR1;
+      h1.out_parity = 1;
+      h1.Ls = Ls;
+      h1.nrhs = nrhs;
+      h1.scale = -0.5;
+      h1.m1 = DM_BAINV;
+      h1.in = xt.ptr(0);
+      h1.in_bs = xt.rs;
+      h1.out = to.ptr(1);
+      h1.out_bs = to.rs;
+      h1.red = skip;
+      run_dwf_hop(L, *set, op, h1, st);
+      DwfHop h2 = schur_pass2(op, fwd, false);
+      h2.epi = DE_NORM;
+      h2.red = red_of(FIN_CG_ALPHA, 1);
+      run_dwf_hop(L, *set, op, h2, st);
+      // 4, 5, 6: v = D^dag q; x += alpha p; r -= alpha v; |r|^2 -> beta
+      schur_mix_and_pass1(L, *set, op, bwd, true, skip, st);
+      DwfHop h3 = schur_pass2(op, bwd, true);
+      h3.cls = K_DWF_SCHUR2CG;
+      h3.out = nullptr;
+      h3.epi = DE_CGUPD;
+      h3.x = xe.ptr(0);
+      h3.r = cr.ptr(0);
+      h3.p = pe.ptr(0);
+      h3.cg_bs = xe.rs;
+      h3.red = red_of(FIN_CG_BETA, 1);
+      run_dwf_hop(L, *set, op, h3, st);
+    };
+    // iterate until every active right-hand side has stopped
+    for (;;) {
+      for (int k = 0; k < check_every; ++k) iteration();
+      BR_CUDA(cudaMemcpyAsync(h_sc.ptr, sc.ptr, sizeof(CGScalars) * nrhs, cudaMemcpyDeviceToHost, st));
+      BR_CUDA(cudaStreamSynchronize(st));
+      const CGScalars* g = static_cast<const CGScalars*>(h_sc.ptr);
+      bool running = false;
+      for (int r = 0; r < nrhs; ++r) running = running || g[r].done == RUNNING;
+      if (!running) break;
+    }
+    {
+      const CGScalars* g = static_cast<const CGScalars*>(h_sc.ptr);
+      long most = 0;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!hmask[r * Ls]) continue;
+        info[r].inner_iters += g[r].iter;
+        most = std::max<long>(most, g[r].iter);
+        if (g[r].done == BREAKDOWN) {
+          info[r].restarts += 1;
+          if (g[r].iter == 0) failed[r] = 1;
+        }
+      }
+      total_iters += most;
+    }
+    // reconstruct e_o = A^-1 r_o + A^-1 (H_oe/2) (B x_e), then x += e
+    {
+      DwfMix m;
+      m.prec = P;
+      m.Ls = Ls;
+      m.nrhs = nrhs;
+      m.m = DM_B;
+      m.in = xe.ptr(0);
+      m.in_bs = xe.rs;
+      m.out = xt.ptr(0);
+      m.out_bs = xt.rs;
+      run_dwf_mix(L, *set, m, st);
+      DwfHop h;
+      h.prec = P;
+      h.cls = K_DWF_PREP;
+      h.out_parity = 1;
+      h.Ls = Ls;
+      h.nrhs = nrhs;
+      h.scale = 0.5;
+      h.m1 = DM_AINV;
+      h.m2 = DM_AINV;
+      h.self = rin.ptr(1);
+      h.self_bs = rin.rs;
+      h.in = xt.ptr(0);
+      h.in_bs = xt.rs;
+      h.out = eo.ptr(1);
+      h.out_bs = eo.rs;
+      run_dwf_hop(L, *set, op, h, st);
+    }
+    accumulate64(L, xe, 0, x64, 0, st, dmask);
+    accumulate64(L, eo, 1, x64, 1, st, dmask);
+  }
+
+  field_to_canon(L, x64, x_dev, st);
+  BR_CUDA(cudaStreamSynchronize(st));
+  const double secs = now_s() - t0;
+  int status = BRIDGE_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    info[r].seconds = secs;
+    if (done[r]) info[r].status = BRIDGE_OK;
+    else if (failed[r]) info[r].status = BRIDGE_EBREAKDOWN;
+    else info[r].status = BRIDGE_ENOCONV;
+    if (info[r].status != BRIDGE_OK)
+      status = (status == BRIDGE_OK || info[r].status == BRIDGE_EBREAKDOWN) ? info[r].status : status;
+    if (info_out) info_out[r] = info[r];
+  }
+  return status;
+}
+
+}  // namespace bridge

@@ -1,0 +1,296 @@
+// Moebius domain-wall kernels: the four-dimensional hopping term applied to
+// every fifth-dimension slice, with the site-local fifth-dimension matrices
+// fused into the epilogue.
+//
+// Operator (Sec. 2 of the paper implements Moebius domain-wall fermions and
+// their even-odd blocks, Eq. 1, keeping the fifth coordinate s as an inner
+// index of each four-dimensional site; the formula is the standard Moebius
+// one):
+//   D psi = (b W + 1) psi + (c W - 1) P psi,   W = (4 - M5) - H / 2,
+//   (P psi)_s = P_- psi_{s+1} + P_+ psi_{s-1}   (wraps carry -m_f),
+// so that, with the site-local A = (b(4-M5) + 1) + (c(4-M5) - 1) P and
+// B = b + c P, D_ee = D_oo = A and D_eo, D_oe = -(1/2) H B.  Every
+// site-local map is block diagonal in chirality (spins 0, 1: P_+; spins 2, 3:
+// P_-) and acts on s through a real Ls x Ls matrix, the same at every site.
+//
+// A block of threads holds ns four-dimensional sites times all Ls slices
+// (thread t: site t % ns, slice t / ns; the block is rounded up to whole
+// warps, and threads past ns * Ls only join the barriers and reductions).  Each thread computes the hopping
+// term of its (site, slice) with spin projection, exactly as the Wilson
+// stencil does, and leaves it in shared memory; after one barrier each
+// thread forms its output slice as a row of the s-matrix times the Ls hop
+// results of its site.  The Ls threads of a site read the same eight links,
+// which L1 serves after the first.
+//
+//   out_s = sum_t M1[s][t] (scale * H in)_t          (or scale * H in)
+//         + s2 * self_s | sum_t M2[s][t] self_t      (optional)
+//         + caux * aux_s                             (optional, aux != null)
+//
+// Epilogues: none, |out|^2 per right-hand side into a fused reduction, or
+// the CG update x += alpha p, r -= alpha out with |r|^2 (out not stored).
+#pragma once
+
+#include "dslash.cuh"
+
+namespace bridge {
+
+enum DwfM2 { DM2_NONE = 0, DM2_PLAIN = 1, DM2_DENSE = 2 };
+enum DwfEpi { DE_NONE = 0, DE_NORM = 1, DE_CGUPD = 2 };
+enum DwfMixMode { DX_PLAIN = 0, DX_CGP = 1 };
+
+struct DwfArgs {
+  Geom g;
+  int out_parity;
+  int Ls, nrhs;
+  int ns;   // four-dimensional sites per block (blockDim = ns * Ls rounded up to 32, <= 256)
+  int nsb;  // site blocks per right-hand side (grid = nsb * nrhs)
+  double scale, s2, caux;
+  float scalef, s2f, cauxf;
+  double bc[4];
+  float bcf[4];
+  // bytes between consecutive slices (slice q = rhs * Ls + s) of each operand;
+  // x, r and p of the CG update share cg_bs
+  long in_bs, out_bs, self_bs, aux_bs, cg_bs;
+  char* out;
+  const char* in;
+  const char* self;
+  const char* aux;
+  char* x;  // CG update epilogue
+  char* r;
+  const char* p;
+  const char* gauge;  // [parity][mu] link blocks
+  const void* m1;     // [2][Ls][Ls] in the compute precision (chirality +, then -)
+  const void* m2;
+  RedArgs red;
+};
+
+struct DwfMixArgs {
+  uint32_t vh;
+  int Ls, nrhs, ns, nsb;
+  long in_bs, out_bs, cg_bs;  // slice strides (cg_bs for p and r)
+  char* out;        // out = M in (DX_PLAIN) or M p (DX_CGP)
+  const char* in;
+  char* p;          // DX_CGP: p = r + beta p, stored
+  const char* r;
+  const void* m;
+  RedArgs red;      // DX_CGP: beta and done flags from red.cg
+  double s0;        // DX_PLAIN: out = s0 * in + M in when s0 != 0
+  float s0f;
+};
+
+BR_HD int dwf_threads(int ns, int Ls) { return (ns * Ls + 31) / 32 * 32; }
+
+// Dynamic shared memory of one block: the s-matrices and ns * Ls spinors
+// per staged operand.
+BR_HD long dwf_hop_smem(int prec, int Ls, int ns, bool m1, bool m2dense) {
+  const long R = prec == P_F64 ? 8 : 4;
+  const long mats = (m1 ? 1 : 0) + (m2dense ? 1 : 0);
+  const long vecs = (m1 ? 1 : 0) + (m2dense ? 1 : 0);
+  return mats * 2 * Ls * Ls * R + vecs * (long)Ls * 12 * ns * 2 * R;
+}
+BR_HD long dwf_mix_smem(int prec, int Ls, int ns) {
+  const long R = prec == P_F64 ? 8 : 4;
+  return 2L * Ls * Ls * R + (long)Ls * 12 * ns * 2 * R;
+}
+
+// Row s of the chirality-blocked s-matrix applied to the Ls staged spinors
+// of one site: res[k] = sum_t M[chi(k)][s][t] sh[t][k].
+template <class R>
+BR_D void smix_row(const R* mat, const cx<R>* sh, int Ls, int ns, int s, int sl, cx<R> res[12]) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) res[k] = czero<R>();
+  const R* rp = mat + (long)s * Ls;            // chirality + (spins 0, 1)
+  const R* rm = mat + (long)(Ls + s) * Ls;     // chirality - (spins 2, 3)
+  for (int t = 0; t < Ls; ++t) {
+    const R a = rp[t], b = rm[t];
+    const cx<R>* v = sh + (long)t * 12 * ns + sl;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) res[k] = res[k] + a * v[k * ns];
+#pragma unroll
+    for (int k = 6; k < 12; ++k) res[k] = res[k] + b * v[k * ns];
+  }
+}
+
+template <class R>
+BR_D void stage_row(cx<R>* sh, int ns, int s, int sl, const cx<R> v[12]) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) sh[((long)s * 12 + k) * ns + sl] = v[k];
+}
+
+template <int P, int MU, bool ST>
+BR_D void dwf_hop_dir(const DwfArgs& a, const char* in, const char* g_out, const char* g_in, long lbb, uint32_t ih,
+                      const int c[4], uint32_t xh, cx<typename Tr<P>::R> acc[12]) {
+  using R = typename Tr<P>::R;
+  uint32_t f, b;
+  bool wf, wb;
+  neighbours<MU>(a.g, ih, c, xh, f, b, wf, wb);
+  const R bc = pick<R>(a.bc[MU], a.bcf[MU]);
+  hop_one<P, MU, true, ST>(in, g_out + MU * lbb, a.g.vh, f, ih, wf, bc, acc);
+  hop_one<P, MU, false, ST>(in, g_in + MU * lbb, a.g.vh, b, b, wb, bc, acc);
+}
+
+template <int P, bool M1, int M2, int EPI>
+__global__ void __launch_bounds__(256) dwf_hop_kernel(const DwfArgs a) {
+  using R = typename Tr<P>::R;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int Ls = a.Ls, ns = a.ns;
+  const int nm = 2 * Ls * Ls;
+  R* mat1 = reinterpret_cast<R*>(dsm);
+  R* mat2 = mat1 + (M1 ? nm : 0);
+  cx<R>* shh = reinterpret_cast<cx<R>*>(mat2 + (M2 == DM2_DENSE ? nm : 0));
+  cx<R>* shs = shh + (M1 ? (long)Ls * 12 * ns : 0);
+
+  const int rhs = blockIdx.x % a.nrhs;
+  const int sb = blockIdx.x / a.nrhs;
+  const int sl = threadIdx.x % ns, s = threadIdx.x / ns;
+  const uint32_t ih = (uint32_t)sb * ns + sl;
+  const long vh = a.g.vh;
+  const bool live = s < Ls;
+  const bool skip = a.red.check_done && a.red.cg != nullptr && a.red.cg[rhs].done != RUNNING;
+  const bool valid = live && ih < (uint32_t)vh && !skip;
+  const long q = (long)rhs * Ls + s;
+
+  if (M1)
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) mat1[i] = reinterpret_cast<const R*>(a.m1)[i];
+  if (M2 == DM2_DENSE)
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) mat2[i] = reinterpret_cast<const R*>(a.m2)[i];
+
+  const int p = a.out_parity;
+  cx<R> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = czero<R>();
+  if (valid) {
+    const long lbb = link_block_bytes(P, vh);
+    const char* g_out = a.gauge + (long)p * 4 * lbb;
+    const char* g_in = a.gauge + (long)(1 - p) * 4 * lbb;
+    const char* in = a.in + q * a.in_bs;
+    int c[4];
+    uint32_t xh;
+    site_coords(a.g, ih, p, c, xh);
+    dwf_hop_dir<P, 0, false>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+    dwf_hop_dir<P, 1, false>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+    dwf_hop_dir<P, 2, false>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+    dwf_hop_dir<P, 3, false>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+    const R sc = pick<R>(a.scale, a.scalef);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = sc * acc[k];
+  }
+  if (M1 && live) stage_row(shh, ns, s, sl, acc);
+  if (M2 == DM2_DENSE && live) {
+    cx<R> v[12];
+    if (valid) {
+      load_spinor<P>(a.self + q * a.self_bs, vh, ih, v);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = czero<R>();
+    }
+    stage_row(shs, ns, s, sl, v);
+  }
+  if (M1 || M2 == DM2_DENSE) __syncthreads();
+
+  R nrm = R(0);
+  if (valid) {
+    cx<R> v[12];
+    if (M1) {
+      smix_row(mat1, shh, Ls, ns, s, sl, v);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = acc[k];
+    }
+    if (M2 == DM2_PLAIN) {
+      cx<R> w[12];
+      load_spinor<P>(a.self + q * a.self_bs, vh, ih, w);
+      const R s2 = pick<R>(a.s2, a.s2f);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = v[k] + s2 * w[k];
+    } else if (M2 == DM2_DENSE) {
+      cx<R> w[12];
+      smix_row(mat2, shs, Ls, ns, s, sl, w);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = v[k] + w[k];
+    }
+    if (a.aux != nullptr) {
+      cx<R> w[12];
+      load_spinor<P>(a.aux + q * a.aux_bs, vh, ih, w);
+      const R ca = pick<R>(a.caux, a.cauxf);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = v[k] + ca * w[k];
+    }
+    if (EPI == DE_CGUPD) {
+      const R alpha = (R)a.red.cg[rhs].alpha;
+      cx<R> xv[12], rv[12], pv[12];
+      load_spinor<P, false>(a.x + q * a.cg_bs, vh, ih, xv);
+      load_spinor<P, false>(a.r + q * a.cg_bs, vh, ih, rv);
+      load_spinor<P>(a.p + q * a.cg_bs, vh, ih, pv);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        xv[k] = xv[k] + alpha * pv[k];
+        rv[k] = rv[k] - alpha * v[k];
+        nrm += rv[k].r * rv[k].r + rv[k].i * rv[k].i;
+      }
+      store_spinor<P>(a.x + q * a.cg_bs, vh, ih, xv);
+      store_spinor<P>(a.r + q * a.cg_bs, vh, ih, rv);
+    } else {
+      store_spinor<P>(a.out + q * a.out_bs, vh, ih, v);
+      if (EPI == DE_NORM)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) nrm += v[k].r * v[k].r + v[k].i * v[k].i;
+    }
+  }
+  if (EPI != DE_NONE) {
+    double rv[1] = {(double)nrm};
+    reduce_finalize<1>(a.red, rhs, sb, a.nsb, a.nrhs, rv);
+  }
+}
+
+// out = M in per site (DX_PLAIN, optionally + s0 in), or the CG direction
+// update p = r + beta p followed by out = M p (DX_CGP).
+template <int P, int MODE>
+__global__ void __launch_bounds__(256) dwf_mix_kernel(const DwfMixArgs a) {
+  using R = typename Tr<P>::R;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int Ls = a.Ls, ns = a.ns;
+  const int nm = 2 * Ls * Ls;
+  R* mat = reinterpret_cast<R*>(dsm);
+  cx<R>* sh = reinterpret_cast<cx<R>*>(mat + nm);
+  const int rhs = blockIdx.x % a.nrhs;
+  const int sb = blockIdx.x / a.nrhs;
+  const int sl = threadIdx.x % ns, s = threadIdx.x / ns;
+  const uint32_t ih = (uint32_t)sb * ns + sl;
+  const bool live = s < Ls;
+  const bool skip = MODE == DX_CGP && a.red.cg != nullptr && a.red.cg[rhs].done != RUNNING;
+  const bool valid = live && ih < a.vh && !skip;
+  const long q = (long)rhs * Ls + s;
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) mat[i] = reinterpret_cast<const R*>(a.m)[i];
+  cx<R> v[12];
+  if (valid) {
+    if (MODE == DX_CGP) {
+      const R beta = (R)a.red.cg[rhs].beta;
+      cx<R> rv[12];
+      load_spinor<P>(a.r + q * a.cg_bs, a.vh, ih, rv);
+      load_spinor<P, false>(a.p + q * a.cg_bs, a.vh, ih, v);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = rv[k] + beta * v[k];
+      store_spinor<P>(a.p + q * a.cg_bs, a.vh, ih, v);
+    } else {
+      load_spinor<P>(a.in + q * a.in_bs, a.vh, ih, v);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = czero<R>();
+  }
+  if (live) stage_row(sh, ns, s, sl, v);
+  __syncthreads();
+  if (valid) {
+    cx<R> w[12];
+    smix_row(mat, sh, Ls, ns, s, sl, w);
+    if (MODE == DX_PLAIN && a.s0 != 0.0) {
+      const R s0 = pick<R>(a.s0, a.s0f);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) w[k] = w[k] + s0 * v[k];
+    }
+    store_spinor<P>(a.out + q * a.out_bs, a.vh, ih, w);
+  }
+}
+
+}  // namespace bridge

@@ -50,6 +50,13 @@ enum KClass {
   K_NORM,
   K_CLOVER,
   K_SETUP,
+  K_DWF_MIX,       // Moebius: fifth-dimension matrix on every site
+  K_DWF_HOP,       // Moebius: D_eo / D_oe and the full operator
+  K_DWF_SCHUR1,    // Moebius Schur pass 1 (and of its adjoint)
+  K_DWF_SCHUR2,    // Moebius Schur pass 2 (and of its adjoint)
+  K_DWF_SCHUR2CG,  // adjoint pass 2 fused with the CG update of x and r
+  K_DWF_PREP,      // Moebius even-odd prepare / reconstruct
+  K_DWF_RESID,     // Moebius FP64 residual b - D x with |r|^2
   K_NCLASS
 };
 const char* kclass_name(int k);
@@ -122,6 +129,29 @@ struct CloverSet {
   std::mutex mu;
 };
 
+// Fifth-dimension matrices of one Moebius parameter set (Ls, M5, b, c, m_f):
+// DWF_NMAT real [2][Ls][Ls] matrices (chirality +, then -) in FP64 and FP32.
+enum DwfMat {
+  DM_B = 0,     // B = b + c P
+  DM_BAINV,     // B A^-1
+  DM_AINV,      // A^-1
+  DM_G5AINVT,   // gamma_5 A^-T
+  DM_AINVTBT,   // A^-T B^T
+  DM_BTG5,      // B^T gamma_5
+  DM_A,         // A = (b alpha + 1) + (c alpha - 1) P
+  DM_MA,        // -A
+  DWF_NMAT
+};
+struct DwfSet {
+  int Ls = 0;
+  double M5 = 0, b = 0, c = 0, mf = 0;
+  std::unique_ptr<DevBuf> mats[2];  // [0] FP64, [1] FP32
+  const void* mat(int prec, int id) const {
+    const size_t per = (size_t)2 * Ls * Ls * (prec == P_F64 ? 8 : 4);
+    return mats[prec == P_F64 ? 0 : 1]->ptr + id * per;
+  }
+};
+
 }  // namespace bridge
 
 // ------------------------------------------------------------- lattice
@@ -137,6 +167,8 @@ struct bridge_lattice_s {
   // clover sets for the most recently used values of kappa * c_sw
   std::vector<std::shared_ptr<bridge::CloverSet>> clovers;
   std::mutex clover_mu;
+  std::vector<std::shared_ptr<bridge::DwfSet>> dwf_sets;  // recently used Moebius parameter sets
+  std::mutex dwf_mu;
   std::atomic<int> in_flight{0};  // engine requests currently holding this lattice
   // reduction scratch for the operator entry points
   std::unique_ptr<bridge::DevBuf> red_partials, red_result;
@@ -168,6 +200,8 @@ struct HopCost {
 };
 HopCost hop_cost(int prec, int flags, int red);
 int sm_count();
+// Reduction scratch of the lattice's operator entry points, grown on demand.
+void ensure_red_scratch(bridge_lattice_s* L, long n_partials, int nrhs);
 
 // gauge / clover on demand
 const char* gauge_ptr(bridge_lattice_s* L, int prec);

@@ -12,15 +12,26 @@
 
 namespace bridge {
 
-enum FinMode { FIN_NONE = 0, FIN_STORE = 1, FIN_ALPHA = 2, FIN_OMEGA = 3, FIN_RHO = 4, FIN_INIT = 5 };
+enum FinMode {
+  FIN_NONE = 0,
+  FIN_STORE = 1,
+  FIN_ALPHA = 2,
+  FIN_OMEGA = 3,
+  FIN_RHO = 4,
+  FIN_INIT = 5,
+  FIN_CG_INIT = 6,   // s[0] = |b|^2 of the CG system
+  FIN_CG_ALPHA = 7,  // s[0] = |D p|^2
+  FIN_CG_BETA = 8    // s[0] = |r|^2 after the update
+};
 
 struct RedArgs {
-  double* partials;       // [nrhs][nblk][4]
-  unsigned int* counter;  // one ticket counter per launch site, reset by the last block
-  BiCGScalars* sc;        // per right-hand side (may be null)
-  double* result;         // [nrhs][4] for FIN_STORE
-  int fin;                // FinMode
-  int check_done;         // blocks of a right-hand side with sc[rhs].done != 0 skip their work
+  double* partials = nullptr;       // [nrhs][nblk][4]
+  unsigned int* counter = nullptr;  // one ticket counter per launch site, reset by the last block
+  BiCGScalars* sc = nullptr;        // per right-hand side (may be null)
+  CGScalars* cg = nullptr;          // per right-hand side, CG finalizers (may be null)
+  double* result = nullptr;         // [nrhs][4] for FIN_STORE
+  int fin = FIN_NONE;               // FinMode
+  int check_done = 0;               // blocks of a right-hand side whose solve has ended skip their work
 };
 
 // Complex helpers on the scalar struct (FP64, one thread).
@@ -98,6 +109,42 @@ __device__ inline void finalize(const RedArgs& ra, int rhs, const double s[4]) {
         q->rho_r = rho_new.r;
         q->rho_i = rho_new.i;
         if (q->iter >= q->max_iter) q->done = MAXITER;
+      }
+      break;
+    }
+    case FIN_CG_INIT: {  // r = p = b, x = 0
+      CGScalars* g = ra.cg + rhs;
+      g->b2 = s[0];
+      g->rr = s[0];
+      g->alpha = g->beta = 0.0;
+      g->iter = 0;
+      g->tol2 = g->tol2 * s[0];
+      g->done = !isfinite(s[0]) ? BREAKDOWN : (s[0] == 0.0 || s[0] <= g->tol2) ? CONVERGED : RUNNING;
+      break;
+    }
+    case FIN_CG_ALPHA: {
+      CGScalars* g = ra.cg + rhs;
+      if (g->done) break;
+      g->pq = s[0];
+      if (!(s[0] > 0.0) || !isfinite(s[0]))
+        g->done = BREAKDOWN;
+      else
+        g->alpha = g->rr / s[0];
+      break;
+    }
+    case FIN_CG_BETA: {
+      CGScalars* g = ra.cg + rhs;
+      if (g->done) break;
+      g->iter += 1;
+      if (!isfinite(s[0])) {
+        g->done = BREAKDOWN;
+      } else {
+        g->beta = s[0] / g->rr;
+        g->rr = s[0];
+        if (s[0] <= g->tol2)
+          g->done = CONVERGED;
+        else if (g->iter >= g->max_iter)
+          g->done = MAXITER;
       }
       break;
     }

@@ -21,7 +21,9 @@ const char* kclass_name(int k) {
   static const char* names[K_NCLASS] = {"hop_deo",      "dirac_full",    "schur_pass1", "schur_pass2",
                                         "schur_pass2_alpha", "schur_pass2_omega", "evenodd_prep", "residual64",
                                         "blas_init",    "blas_s",        "blas_xr",     "blas_p",
-                                        "convert",      "norm",          "clover_site", "setup"};
+                                        "convert",      "norm",          "clover_site", "setup",
+                                        "dwf_mix",      "dwf_hop",       "dwf_schur_pass1", "dwf_schur_pass2",
+                                        "dwf_schur_pass2_cg", "dwf_evenodd_prep", "dwf_residual64"};
   return (k >= 0 && k < K_NCLASS) ? names[k] : "?";
 }
 
@@ -140,7 +142,7 @@ LaunchShape shape_for(bridge_lattice_s* L, const std::string& key, long vh, int 
   return s;
 }
 
-static void ensure_red_scratch(bridge_lattice_s* L, long n_partials, int nrhs) {
+void ensure_red_scratch(bridge_lattice_s* L, long n_partials, int nrhs) {
   size_t need = (size_t)n_partials * 4 * sizeof(double);
   if (!L->red_partials || L->red_partials->bytes < need) L->red_partials.reset(new DevBuf(need));
   size_t rneed = (size_t)(nrhs > 0 ? nrhs : 1) * 4 * sizeof(double);

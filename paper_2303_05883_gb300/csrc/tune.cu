@@ -291,6 +291,10 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
 extern "C" int bridge_tune(bridge_lattice L, const bridge_op* op, int prec, int nrhs) {
   try {
     if (!L || !op || nrhs < 1 || prec < BRIDGE_F64 || prec > BRIDGE_BF16) return BRIDGE_EINVAL;
+    if (op->kind != BRIDGE_WILSON && op->kind != BRIDGE_CLOVER) {
+      set_error(BRIDGE_EINVAL, "bridge_tune takes WILSON and CLOVER operators");
+      return BRIDGE_EINVAL;
+    }
     if (!L->have_gauge) return BRIDGE_ESTATE;
     std::lock_guard<std::mutex> lk(L->api_mu);
     tune_solver_kernels(L, *op, prec, nrhs);

@@ -240,3 +240,42 @@ WORKLOADS = {
         "clover_48x48x48x96_12rhs", (48, 48, 48, 96), "clover", 0.125, 1.0, 0.2, 3, 12, "point", 1e-10, inner="f16"
     ),
 }
+
+
+@dataclass(frozen=True)
+class MobiusWorkload:
+    """One synthetic configuration of the Moebius domain-wall solver path."""
+
+    name: str
+    dims: tuple
+    Ls: int
+    M5: float
+    b5: float
+    c5: float
+    mf: float
+    eps: float
+    seed: int
+    nrhs: int
+    tol: float
+    bc: tuple = field(default=(1, 1, 1, -1))
+    inner: str = "f32"
+    kind: str = "mobius"
+
+    @property
+    def volume(self) -> int:
+        return volume(self.dims)
+
+    def gauge(self) -> np.ndarray:
+        return gauge_field(self.dims, self.eps, self.seed)
+
+    def sources(self) -> np.ndarray:
+        """Gaussian five-dimensional sources shaped (nrhs, Ls, V, 4, 3)."""
+        b = gaussian_spinor(self.dims, self.seed, nrhs=self.nrhs * self.Ls)
+        return b.reshape((self.nrhs, self.Ls) + b.shape[1:])
+
+
+# Moebius domain wall on 24^3x48 with Ls = 16, M5 = 1.8, b = 1.5, c = 0.5,
+# m_f = 0.01: CG on the normal equations, FP32 inner / FP64 outer to 1e-10.
+WORKLOADS["mobius_24x24x24x48x16"] = MobiusWorkload(
+    "mobius_24x24x24x48x16", (24, 24, 24, 48), 16, 1.8, 1.5, 0.5, 0.01, 0.2, 5, 1, 1e-10
+)
