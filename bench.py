@@ -23,6 +23,12 @@ against the HBM peak.  Beside it the line reports:
 * cpu_baseline: the FP64 numpy oracle on a bounded sample of the workload.
 
 ``--impl reference`` times only the oracle (the reference for this path).
+
+``--workload mobius_24x24x24x48x16`` runs the same measurements for the
+Moebius domain-wall operator (Ls = 16, M5 = 1.8, b = 1.5, c = 0.5,
+m_f = 0.01): a step is one mixed-precision CG solve on the normal equations
+of the even-odd system (FP32 inner, FP64 defect correction, 1e-10), beside
+D_eo alone and a plain FP64 CG solve.
 """
 
 from __future__ import annotations
@@ -60,6 +66,8 @@ def parse():
     ap.add_argument("--rate-factors", type=float, nargs="+", default=[0.5, 0.9],
                     help="serving workload: arrival rates as fractions of the saturated rate")
     ap.add_argument("--oracle-sites", type=int, default=16384, help="sites per oracle sample")
+    ap.add_argument("--deo-only", action="store_true",
+                    help="Moebius workload: only the operator legs (one Schur operator, then D_eo), for profiler captures")
     return ap.parse_args()
 
 
@@ -139,14 +147,15 @@ def traffic_for(kernel: str, workload: str):
     text = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
-    if not m or not h or h.group(1) != kernel_source_hash():
+    if not m or not h or h.group(1) != kernel_source_hash(kernel):
         return None
     return float(m.group(1))
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(kernel: str = "") -> str:
     d = hashlib.sha256()
-    for f in ("common.cuh", "dslash.cuh", "reduce.cuh"):
+    files = ["common.cuh", "dslash.cuh", "reduce.cuh"] + (["dwf.cuh"] if kernel.startswith("dwf") else [])
+    for f in files:
         d.update(open(os.path.join(ROOT, "paper_2303_05883_gb300", "csrc", f), "rb").read())
     return d.hexdigest()[:16]
 
@@ -621,6 +630,216 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def mobius_oracle_sample(w, U, b, nsites, seed):
+    """The FP64 oracle's Moebius D at random four-dimensional sites (all Ls slices)."""
+    from oracle import domainwall
+    from oracle.lattice import Lattice
+
+    lat = Lattice(w.dims)
+    orc = domainwall.Mobius(U, lat, w.Ls, w.M5, w.b5, w.c5, w.mf, w.bc)
+    sites = np.sort(np.random.default_rng(seed).choice(lat.V, nsites, replace=False))
+    _, secs, cores = cpu_cores_used(lambda: orc.full(b, sites=sites))
+    # per five-dimensional site: spinor in (plus P psi), 8 links, spinor out
+    per_site = 192 + 8 * 144 / w.Ls + 192
+    return nsites * w.Ls * per_site / secs / 1e9, secs, cores
+
+
+def mobius_operator_leg(api, h, op, w, b_dev, stream):
+    """One Schur operator application, then D_eo (B mix + hop) alone on
+    resident FP32 fields, timed with CUDA events on the library stream."""
+    import torch
+
+    peak, _ = peaks()
+    nrhs = w.nrhs
+    nq = nrhs * w.Ls
+    fo = api.bridge_field_create(h, "f32", 1, nq)
+    fe = api.bridge_field_create(h, "f32", 0, nq)
+    fe2 = api.bridge_field_create(h, "f32", 0, nq)
+    half = b_dev.reshape(nq, w.volume // 2, 2, 4, 3)
+    par = torch.from_numpy(_parity_odd_index(w.dims)).to(b_dev.device)
+    src_odd = torch.gather(half, 2, par.view(1, -1, 1, 1, 1).expand(nq, -1, 1, 4, 3)).squeeze(2).contiguous()
+    api.bridge_field_import(fo, src_odd)
+    del src_odd, half
+    api.bridge_sync(h)
+    api.bridge_apply(h, op, 1, fe, fo)  # D_oe: an even input for the Schur operator
+    api.bridge_apply(h, op, 3, fe2, fe)  # D^ once (its kernels come first in a profiler capture)
+    for _ in range(3):
+        api.bridge_apply(h, op, 1, fe, fo)
+    reps = 30
+    api.bridge_stats_reset(h)
+    api.bridge_profile(h, True)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        api.bridge_apply(h, op, 1, fe, fo)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    api.bridge_profile(h, False)
+    dst = api.bridge_stats(h)
+    deo_ms = a0.elapsed_time(a1) / reps
+    deo_bytes = (dst["dwf_hop"]["bytes"] + dst["dwf_mix"]["bytes"]) / reps
+    hop = dst["dwf_hop"]
+    out = {"ops": "B mix + hop", "prec": "f32", "slices": nq, "gbs": deo_bytes / (deo_ms * 1e-3) / 1e9,
+           "us_per_apply": deo_ms * 1e3, "bytes_per_apply": deo_bytes, "frac": deo_bytes / (deo_ms * 1e-3) / 1e9 / peak,
+           "hop_gbs": hop["bytes"] / (hop["ms"] * 1e-3) / 1e9, "hop_frac": hop["bytes"] / (hop["ms"] * 1e-3) / 1e9 / peak,
+           "hop_us": 1e3 * hop["ms"] / reps, "hop_bytes": hop["bytes"] / reps,
+           "hop_gflops": hop["flops"] / (hop["ms"] * 1e-3) / 1e9}
+    for f in (fo, fe, fe2):
+        api.bridge_field_destroy(f)
+    return out
+
+
+def run_mobius(args):
+    """Moebius domain wall: mixed CG solve steps, D_eo alone, FP64 CG, e2e, oracle."""
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__ as g
+
+    if rank == 0:
+        g.build()
+    if world > 1:
+        dist.barrier()
+    from ctypes import byref, c_void_p
+
+    import synth
+    from paper_2303_05883_gb300 import _abi, api
+
+    w = synth.WORKLOADS[args.workload]
+    U = w.gauge()
+    b_host = w.sources()  # (nrhs, Ls, V, 4, 3)
+    b_dev = torch.from_numpy(b_host).to(f"cuda:{local}")
+    x_dev = torch.zeros_like(b_dev)
+    op = api.make_mobius(w.Ls, w.M5, w.b5, w.c5, w.mf, bc=w.bc)
+    L = api.Lattice(w.dims)
+    L.upload(U)
+    h = L.handle
+    stream = L.stream
+    solver = api.make_solver(tol=w.tol, inner_prec="f32", mixed=1)
+    nrhs = w.nrhs
+    api.bridge_tune(h, op, "f32", nrhs)
+    if args.deo_only:
+        print(json.dumps({"workload": args.workload, "deo": mobius_operator_leg(api, h, op, w, b_dev, stream),
+                          "launch_shapes": {k: {"threads": v[0], "variant": v[2]}
+                                            for k, v in api.bridge_tune_table(h).items() if k.startswith("dwf")}}),
+              flush=True)
+        L.close()
+        return
+
+    def solve_dev(prm):
+        x_dev.zero_()
+        torch.cuda.current_stream().synchronize()
+        info = (_abi.bridge_info * nrhs)()
+        st = _abi.load().bridge_solve_dev(h, byref(op), byref(prm), c_void_p(b_dev.data_ptr()),
+                                          c_void_p(x_dev.data_ptr()), nrhs, info)
+        _abi.check(st, "bridge_solve_dev")
+        return max((info[k] for k in range(nrhs)), key=lambda i: i.true_rel_residual)
+
+    for _ in range(args.warmup):
+        solve_dev(solver)
+    torch.cuda.synchronize()
+    api.bridge_stats_reset(h)
+    l0 = api.bridge_launch_count()
+    infos = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(solve_dev(solver))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = api.bridge_launch_count() - l0
+    st = api.bridge_stats(h)
+    total_bytes = sum(v["bytes"] for v in st.values())
+    ms, total_bytes = aggregate_ranks(ms, total_bytes, device=f"cuda:{local}")
+    value = total_bytes / (ms * 1e-3) / 1e9
+    res = max(i.true_rel_residual for i in infos)
+    iters = statistics.median(i.inner_iters for i in infos)
+    outer = statistics.median(i.outer_iters for i in infos)
+
+    # ---- one event-profiled step
+    api.bridge_stats_reset(h)
+    api.bridge_profile(h, True)
+    solve_dev(solver)
+    torch.cuda.synchronize()
+    api.bridge_profile(h, False)
+    pst = api.bridge_stats(h)
+    step_ms_prof = sum(v["ms"] for v in pst.values())
+    dom = max(pst, key=lambda k: pst[k]["ms"])
+    d = pst[dom]
+    peak, peak_kind = peaks()
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    roofline = {
+        "bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+        "frac": achieved / peak, "traffic": traffic_for(dom, args.workload),
+        "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]), "launches": d["launches"],
+        "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
+        "share_of_step": d["ms"] / step_ms_prof if step_ms_prof else None,
+    }
+    shares = {k: round(v["ms"] / step_ms_prof, 4) for k, v in pst.items() if v["ms"] > 0}
+    per_kernel = {k: {"launches": v["launches"], "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
+                      "tflops": v["flops"] / (v["ms"] * 1e-3) / 1e12}
+                  for k, v in pst.items() if v["ms"] > 0}
+
+    deo = mobius_operator_leg(api, h, op, w, b_dev, stream)
+    peak, peak_kind = peaks()
+
+    solve = {"mixed_ms": ms / args.steps, "mixed_cg_iters": iters, "mixed_outer": outer,
+             "mixed_true_rel_residual": res, "inner_prec": "f32"}
+    if not args.no_fp64:
+        s64 = api.make_solver(tol=w.tol, mixed=0, max_iter=100000)
+        t0 = time.perf_counter()
+        i64 = solve_dev(s64)
+        t64 = time.perf_counter() - t0
+        solve.update({"fp64_ms": t64 * 1e3, "fp64_cg_iters": i64.inner_iters,
+                      "fp64_true_rel_residual": i64.true_rel_residual, "speedup": t64 * 1e3 / (ms / args.steps)})
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, h, op, solver, b_dev, b_host, nrhs, total_bytes, world)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        n = max(16, args.oracle_sites // 64)
+        v, secs, cores = mobius_oracle_sample(w, U, b_host[0], n, seed=0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"FP64 numpy oracle: Moebius D at {n} random four-dimensional sites x Ls = {w.Ls} of the "
+                         f"{args.workload} lattice ({secs:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {
+                "workload": args.workload, "lattice": "x".join(map(str, w.dims)) + f"x{w.Ls}",
+                "operator": f"Moebius domain wall, M5={w.M5}, b={w.b5}, c={w.c5}, m_f={w.mf}, bc={list(w.bc)}",
+                "links": f"exp({w.eps} i A), seed {w.seed}", "source": "gaussian", "nrhs": nrhs,
+                "solver": "even-odd CG on the normal equations, f32 inner, f64 defect correction", "tol": w.tol,
+                "l2": "inputs larger than L2 (one five-dimensional FP32 field is 1 GB)",
+                "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            },
+            "roofline": roofline, "kernel_shares": shares, "per_kernel": per_kernel, "deo": deo, "solve": solve,
+            "launch_shapes": {k: {"threads": v[0], "variant": v[2]}
+                              for k, v in api.bridge_tune_table(h).items() if k.startswith("dwf")},
+            "e2e": e2e, "gpu_launches": launches, "inner_iters": iters, "true_rel_residual": res,
+            "clocks": clk.summary(), "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    L.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_serving(args):
     """The request stream alone: lattices {8^4, 16^4, 24^3x48, 32^3x64},
     kappa in [0.11, 0.13], 1-12 right-hand sides, Wilson or clover."""
@@ -666,6 +885,8 @@ def main():
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload.startswith("mobius"):
+        run_mobius(args)
     else:
         run_ours(args)
 

@@ -105,8 +105,9 @@ typedef struct {
    * for an operator or solve call is multiplied by Ls.  Computed in FP64 or
    * FP32 (prec / inner_prec F16 and BF16 return EINVAL); the solver is CG on
    * the normal equations of D^(eo) (Sec. 3 / Fig. 7 of the paper use CG for
-   * this operator) inside the same FP64 defect correction.  Not accepted by
-   * bridge_apply, bridge_mult_Dhat_noalloc, bridge_tune or bridge_submit. */
+   * this operator) inside the same FP64 defect correction.  bridge_apply
+   * takes fields of nrhs x Ls slices.  Not accepted by
+   * bridge_mult_Dhat_noalloc, bridge_tune or bridge_submit. */
   int Ls;       /* fifth extent, 1 .. 32 */
   double M5;    /* domain-wall height */
   double b5, c5; /* Moebius coefficients */

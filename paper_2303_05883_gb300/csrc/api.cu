@@ -426,13 +426,36 @@ int bridge_apply(bridge_lattice L, const bridge_op* op, int which, bridge_field 
   BR_API_BEGIN
   check_lat(L, true);
   check_op(op);
-  check_not_mobius(op, "bridge_apply");
   BR_CHECK(out != nullptr && in != nullptr, BRIDGE_EINVAL, "NULL field");
   BR_CHECK(out->L == L && in->L == L, BRIDGE_EINVAL, "field belongs to another lattice");
   BR_CHECK(out->f.prec == in->f.prec, BRIDGE_EINVAL, "fields differ in precision");
   BR_CHECK(out->f.nrhs == in->f.nrhs, BRIDGE_EINVAL, "fields differ in nrhs");
   BR_CHECK(out->f.buf != in->f.buf, BRIDGE_EINVAL, "in and out must differ");
   std::lock_guard<std::mutex> lk(L->api_mu);
+  if (op_is_mobius(*op)) {
+    BR_CHECK(in->f.nrhs % op->Ls == 0, BRIDGE_EINVAL, "MOBIUS fields hold a multiple of Ls slices");
+    BR_CHECK(in->f.prec == BRIDGE_F64 || in->f.prec == BRIDGE_F32, BRIDGE_EINVAL, "MOBIUS operators run in F64 or F32");
+    switch (which) {
+      case BRIDGE_APPLY_D:
+        BR_CHECK(in->f.subset == BRIDGE_FULL && out->f.subset == BRIDGE_FULL, BRIDGE_EINVAL, "D needs FULL fields");
+        dwf_apply_d(L, *op, out->f, in->f, L->stream);
+        break;
+      case BRIDGE_APPLY_DEO:
+      case BRIDGE_APPLY_DOE: {
+        const int q = which == BRIDGE_APPLY_DEO ? 0 : 1;
+        BR_CHECK(in->f.subset != q && out->f.subset != 1 - q, BRIDGE_EINVAL, "hopping block maps between parities");
+        dwf_apply_deo(L, *op, q, out->f, in->f, L->stream);
+        break;
+      }
+      case BRIDGE_APPLY_DHAT:
+        BR_CHECK(in->f.subset != BRIDGE_ODD && out->f.subset != BRIDGE_ODD, BRIDGE_EINVAL, "D^ acts on even fields");
+        dwf_apply_dhat(L, *op, out->f, in->f, false, L->stream);
+        break;
+      default:
+        throw Error{BRIDGE_EINVAL, "unknown operator"};
+    }
+    return BRIDGE_OK;
+  }
   switch (which) {
     case BRIDGE_APPLY_D:
       BR_CHECK(in->f.subset == BRIDGE_FULL && out->f.subset == BRIDGE_FULL, BRIDGE_EINVAL, "D needs FULL fields");

@@ -22,6 +22,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 
@@ -173,9 +175,33 @@ namespace {
 long site_bytes(int prec) { return prec == P_F64 ? 192 : 96; }
 long link_bytes(int prec) { return prec == P_F64 ? 144 : 48; }
 
-int sites_per_block(int prec, int Ls) {
-  const int target = prec == P_F64 ? 128 : 256;
-  return std::max(1, target / Ls);
+// Threads per block are ns * Ls rounded up to whole warps, ns four-dimensional
+// sites per block; the tuner picks 128 or 256 (FP64: 128).
+int sites_per_block(int threads, int Ls) { return std::max(1, threads / Ls); }
+constexpr int kMinThreads = 128;
+
+std::string dims_tag(const bridge_lattice_s* L) {
+  return std::to_string(L->dims[0]) + "x" + std::to_string(L->dims[1]) + "x" + std::to_string(L->dims[2]) + "x" +
+         std::to_string(L->dims[3]);
+}
+std::string hop_key(const bridge_lattice_s* L, int prec, bool m1, int m2mode, int epi, int Ls, int nrhs) {
+  return "dwf/" + std::to_string(prec) + "/" + std::to_string(m1) + "/" + std::to_string(m2mode) + "/" +
+         std::to_string(epi) + "/Ls" + std::to_string(Ls) + "/" + dims_tag(L) + "/" + std::to_string(nrhs);
+}
+std::string mix_key(const bridge_lattice_s* L, int prec, int mode, int Ls, int nrhs) {
+  return "dwfmix/" + std::to_string(prec) + "/" + std::to_string(mode) + "/Ls" + std::to_string(Ls) + "/" +
+         dims_tag(L) + "/" + std::to_string(nrhs);
+}
+// Tuned (threads, variant) for a key; FP32 default 256 threads, variant 0.
+LaunchShape dwf_shape(bridge_lattice_s* L, int prec, const std::string& key) {
+  if (prec == P_F64) return LaunchShape{kMinThreads, 0, 0};
+  std::lock_guard<std::mutex> lk(L->tune_mu);
+  auto it = L->tuned.find(key);
+  if (it == L->tuned.end()) return LaunchShape{256, 0, 0};
+  LaunchShape s = it->second;  // (a hand-set entry may ask for fewer threads than the scratch is sized for)
+  s.block = std::max(s.block, kMinThreads);
+  if (s.variant < 0 || s.variant >= DWF_NVARIANT) s.variant = 0;
+  return s;
 }
 
 struct DwfHop {
@@ -189,16 +215,20 @@ struct DwfHop {
   char *out = nullptr, *x = nullptr, *r = nullptr;
   long in_bs = 0, out_bs = 0, self_bs = 0, aux_bs = 0, cg_bs = 0;
   RedArgs red{};
+  const LaunchShape* shape = nullptr;  // set by the tuner; else the shape table
 };
 
 void run_dwf_hop(bridge_lattice_s* L, const DwfSet& set, const bridge_op& op, const DwfHop& c, cudaStream_t st) {
+  const int m2mode = c.self_plain ? DM2_PLAIN : c.m2 >= 0 ? DM2_DENSE : DM2_NONE;
+  const LaunchShape sh =
+      c.shape ? *c.shape : dwf_shape(L, c.prec, hop_key(L, c.prec, c.m1 >= 0, m2mode, c.epi, c.Ls, c.nrhs));
   DwfArgs a;
   std::memset(static_cast<void*>(&a), 0, sizeof(a));
   a.g = L->g;
   a.out_parity = c.out_parity;
   a.Ls = c.Ls;
   a.nrhs = c.nrhs;
-  a.ns = sites_per_block(c.prec, c.Ls);
+  a.ns = sites_per_block(sh.block, c.Ls);
   a.nsb = (int)((L->vh + a.ns - 1) / a.ns);
   a.scale = c.scale;
   a.scalef = (float)c.scale;
@@ -226,7 +256,6 @@ void run_dwf_hop(bridge_lattice_s* L, const DwfSet& set, const bridge_op& op, co
   a.m1 = c.m1 >= 0 ? set.mat(c.prec, c.m1) : nullptr;
   a.m2 = c.m2 >= 0 ? set.mat(c.prec, c.m2) : nullptr;
   a.red = c.red;
-  const int m2mode = c.self_plain ? DM2_PLAIN : c.m2 >= 0 ? DM2_DENSE : DM2_NONE;
   if (c.epi != DE_NONE && a.red.partials == nullptr) {
     ensure_red_scratch(L, (long)a.nsb * c.nrhs, c.nrhs);
     a.red.partials = reinterpret_cast<double*>(L->red_partials->ptr);
@@ -248,7 +277,7 @@ void run_dwf_hop(bridge_lattice_s* L, const DwfSet& set, const bridge_op& op, co
   const double sites5 = (double)L->vh * c.Ls * c.nrhs;
   const double bytes = sites5 * per + (double)L->vh * 8 * link_bytes(c.prec);
   note_launch(L, c.cls, bytes, sites5 * fl, st, true);
-  BR_CHECK(launch_dwf_hop(c.prec, c.m1 >= 0, m2mode, c.epi, a, st), BRIDGE_EINVAL,
+  BR_CHECK(launch_dwf_hop(c.prec, c.m1 >= 0, m2mode, c.epi, a, st, sh.variant), BRIDGE_EINVAL,
            "domain-wall hop variant not instantiated");
   note_launch(L, c.cls, bytes, sites5 * fl, st, false);
   BR_CUDA(cudaGetLastError());
@@ -261,15 +290,17 @@ struct DwfMix {
   char *out = nullptr, *p = nullptr;
   long in_bs = 0, out_bs = 0, cg_bs = 0;
   RedArgs red{};
+  const LaunchShape* shape = nullptr;
 };
 
 void run_dwf_mix(bridge_lattice_s* L, const DwfSet& set, const DwfMix& c, cudaStream_t st) {
+  const LaunchShape sh = c.shape ? *c.shape : dwf_shape(L, c.prec, mix_key(L, c.prec, c.mode, c.Ls, c.nrhs));
   DwfMixArgs a;
   std::memset(static_cast<void*>(&a), 0, sizeof(a));
   a.vh = (uint32_t)L->vh;
   a.Ls = c.Ls;
   a.nrhs = c.nrhs;
-  a.ns = sites_per_block(c.prec, c.Ls);
+  a.ns = sites_per_block(sh.block, c.Ls);
   a.nsb = (int)((L->vh + a.ns - 1) / a.ns);
   a.in_bs = c.in_bs;
   a.out_bs = c.out_bs;
@@ -285,7 +316,7 @@ void run_dwf_mix(bridge_lattice_s* L, const DwfSet& set, const DwfMix& c, cudaSt
   const double bytes = sites5 * (c.mode == DX_CGP ? 4 : 2) * S;
   const double fl = sites5 * (48.0 * c.Ls + (c.mode == DX_CGP ? 48 : 0));
   note_launch(L, K_DWF_MIX, bytes, fl, st, true);
-  BR_CHECK(launch_dwf_mix(c.prec, c.mode, a, st), BRIDGE_EINVAL, "domain-wall mix precision");
+  BR_CHECK(launch_dwf_mix(c.prec, c.mode, a, st, sh.variant), BRIDGE_EINVAL, "domain-wall mix precision");
   note_launch(L, K_DWF_MIX, bytes, fl, st, false);
   BR_CUDA(cudaGetLastError());
 }
@@ -493,9 +524,9 @@ int dwf_solve(bridge_lattice_s* L, const bridge_op& op, const bridge_solver& prm
   Field xt = make_field(P, BRIDGE_EVEN, nq, L->vh), qv = make_field(P, BRIDGE_EVEN, nq, L->vh);
   Field to = make_field(P, BRIDGE_ODD, nq, L->vh), eo = make_field(P, BRIDGE_ODD, nq, L->vh);
 
-  // CG scalars and reduction scratch of this solve (sized for the FP64
-  // launches, which have the smaller blocks)
-  const int ns = std::min(sites_per_block(P, Ls), sites_per_block(P_F64, Ls));
+  // CG scalars and reduction scratch of this solve (sized for the smallest
+  // blocks any launch shape uses)
+  const int ns = sites_per_block(kMinThreads, Ls);
   const long nsb = (L->vh + ns - 1) / ns;
   DevBuf sc(sizeof(CGScalars) * nrhs), partials(sizeof(double) * 4 * nsb * nrhs), counter(256);
   DevBuf mask((size_t)nq * sizeof(int)), resbuf(sizeof(double) * 4 * nrhs * 2);
@@ -777,6 +808,212 @@ int dwf_solve(bridge_lattice_s* L, const bridge_op& op, const bridge_solver& prm
     if (info_out) info_out[r] = info[r];
   }
   return status;
+}
+
+// ------------------------------------------------------------ tuner
+void tune_dwf_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int nrhs) {
+  if (prec != P_F32) return;
+  auto set = dwf_set(L, op);
+  const int Ls = op.Ls, nq = nrhs * Ls;
+  cudaStream_t st = L->stream;
+  gauge_ptr(L, P_F32);
+  Field fe = make_field(P_F32, BRIDGE_EVEN, nq, L->vh), fe2 = make_field(P_F32, BRIDGE_EVEN, nq, L->vh);
+  Field fe3 = make_field(P_F32, BRIDGE_EVEN, nq, L->vh), fe4 = make_field(P_F32, BRIDGE_EVEN, nq, L->vh);
+  Field fx = make_field(P_F32, BRIDGE_EVEN, nq, L->vh), fo = make_field(P_F32, BRIDGE_ODD, nq, L->vh);
+  Field ff = make_field(P_F32, BRIDGE_FULL, nq, L->vh), ff2 = make_field(P_F32, BRIDGE_FULL, nq, L->vh);
+  uint32_t seed = 11;
+  for (const Field* f : {&fe, &fe2, &fe3, &fe4, &fx, &fo, &ff, &ff2}) fill_scratch(*f, seed++, st);
+  const long nsb = (L->vh + sites_per_block(kMinThreads, Ls) - 1) / sites_per_block(kMinThreads, Ls);
+  DevBuf sc(sizeof(CGScalars) * nrhs), partials(sizeof(double) * 4 * nsb * nrhs), counter(256);
+  BR_CUDA(cudaMemsetAsync(counter.ptr, 0, 256, st));
+  std::vector<CGScalars> hs(nrhs);
+  for (auto& g : hs) {
+    std::memset(&g, 0, sizeof(g));
+    g.rr = 1.0;
+    g.alpha = g.beta = 0.1;
+    g.max_iter = 1 << 30;  // tol2 = 0: never converged, so no launch skips its work
+  }
+  auto reset = [&] {
+    BR_CUDA(cudaMemcpyAsync(sc.ptr, hs.data(), sizeof(CGScalars) * nrhs, cudaMemcpyHostToDevice, st));
+  };
+  auto red = [&](int fin) {
+    RedArgs r;
+    r.partials = reinterpret_cast<double*>(partials.ptr);
+    r.counter = reinterpret_cast<unsigned*>(counter.ptr);
+    r.cg = reinterpret_cast<CGScalars*>(sc.ptr);
+    r.fin = fin;
+    r.check_done = 1;
+    return r;
+  };
+  cudaEvent_t ea, eb;
+  BR_CUDA(cudaEventCreate(&ea));
+  BR_CUDA(cudaEventCreate(&eb));
+  const bool verbose = std::getenv("BRIDGE_TUNE_VERBOSE") != nullptr;
+  std::vector<std::string> keys;
+  // time `launch(shape)` for every candidate shape; keep the fastest under key
+  auto tune = [&](const std::string& key, const std::function<void(const LaunchShape*)>& launch) {
+    float best = 1e30f;
+    LaunchShape pick{256, 0, 0};
+    for (int threads : {128, 256})
+      for (int v = 0; v < DWF_NVARIANT; ++v) {
+        LaunchShape cand{threads, 0, v};
+        reset();
+        launch(&cand);  // warm
+        BR_CUDA(cudaEventRecord(ea, st));
+        const int reps = 5;
+        for (int i = 0; i < reps; ++i) launch(&cand);
+        BR_CUDA(cudaEventRecord(eb, st));
+        BR_CUDA(cudaEventSynchronize(eb));
+        float ms = 0;
+        BR_CUDA(cudaEventElapsedTime(&ms, ea, eb));
+        ms /= reps;
+        if (verbose) std::fprintf(stderr, "tune %s threads=%d variant=%d %.1f us\n", key.c_str(), threads, v, 1e3f * ms);
+        if (ms < best) {
+          best = ms;
+          pick = cand;
+        }
+      }
+    {
+      std::lock_guard<std::mutex> lk(L->tune_mu);
+      L->tuned[key] = pick;
+    }
+    keys.push_back(key);
+  };
+  // the CG iteration: mix p / B p, the two Schur passes and the update pass
+  tune(mix_key(L, P_F32, DX_CGP, Ls, nrhs), [&](const LaunchShape* shp) {
+    DwfMix m;
+    m.prec = P_F32;
+    m.mode = DX_CGP;
+    m.Ls = Ls;
+    m.nrhs = nrhs;
+    m.m = DM_B;
+    m.p = fe.ptr(0);
+    m.r = fe2.ptr(0);
+    m.cg_bs = fe.rs;
+    m.out = fx.ptr(0);
+    m.out_bs = fx.rs;
+    m.red = red(FIN_NONE);
+    m.shape = shp;
+    run_dwf_mix(L, *set, m, st);
+  });
+  tune(mix_key(L, P_F32, DX_PLAIN, Ls, nrhs), [&](const LaunchShape* shp) {
+    DwfMix m;
+    m.prec = P_F32;
+    m.Ls = Ls;
+    m.nrhs = nrhs;
+    m.m = DM_G5AINVT;
+    m.in = fe3.ptr(0);
+    m.in_bs = fe3.rs;
+    m.out = fx.ptr(0);
+    m.out_bs = fx.rs;
+    m.shape = shp;
+    run_dwf_mix(L, *set, m, st);
+  });
+  auto hop = [&](bool m1, int m2, bool plain, int epi) {
+    DwfHop h;
+    h.prec = P_F32;
+    h.Ls = Ls;
+    h.nrhs = nrhs;
+    h.m1 = m1 ? DM_AINV : -1;
+    h.m2 = m2;
+    h.self_plain = plain;
+    h.epi = epi;
+    return h;
+  };
+  // pass 1 (and its adjoint): odd output, fifth-dimension matrix epilogue
+  tune(hop_key(L, P_F32, true, DM2_NONE, DE_NONE, Ls, nrhs), [&](const LaunchShape* shp) {
+    DwfHop h = hop(true, -1, false, DE_NONE);
+    h.out_parity = 1;
+    h.m1 = DM_BAINV;
+    h.in = fx.ptr(0);
+    h.in_bs = fx.rs;
+    h.out = fo.ptr(1);
+    h.out_bs = fo.rs;
+    h.red = red(FIN_NONE);
+    h.shape = shp;
+    run_dwf_hop(L, *set, op, h, st);
+  });
+  // pass 2 with |q|^2 -> alpha
+  tune(hop_key(L, P_F32, true, DM2_PLAIN, DE_NORM, Ls, nrhs), [&](const LaunchShape* shp) {
+    DwfHop h = hop(true, -1, true, DE_NORM);
+    h.scale = 0.5;
+    h.in = fo.ptr(1);
+    h.in_bs = fo.rs;
+    h.self = fe.ptr(0);
+    h.self_bs = fe.rs;
+    h.out = fe3.ptr(0);
+    h.out_bs = fe3.rs;
+    h.red = red(FIN_CG_ALPHA);
+    h.shape = shp;
+    run_dwf_hop(L, *set, op, h, st);
+  });
+  // adjoint pass 2 fused with the x, r update
+  tune(hop_key(L, P_F32, true, DM2_PLAIN, DE_CGUPD, Ls, nrhs), [&](const LaunchShape* shp) {
+    DwfHop h = hop(true, -1, true, DE_CGUPD);
+    h.m1 = DM_BTG5;
+    h.scale = 0.5;
+    h.in = fo.ptr(1);
+    h.in_bs = fo.rs;
+    h.self = fe3.ptr(0);
+    h.self_bs = fe3.rs;
+    h.x = fe4.ptr(0);
+    h.r = fe2.ptr(0);
+    h.p = fe.ptr(0);
+    h.cg_bs = fe.rs;
+    h.red = red(FIN_CG_BETA);
+    h.shape = shp;
+    run_dwf_hop(L, *set, op, h, st);
+  });
+  // pass 2 of the operator alone, prepare / reconstruct, D_eo and the full operator
+  tune(hop_key(L, P_F32, true, DM2_PLAIN, DE_NONE, Ls, nrhs), [&](const LaunchShape* shp) {
+    DwfHop h = hop(true, -1, true, DE_NONE);
+    h.scale = 0.5;
+    h.in = fo.ptr(1);
+    h.in_bs = fo.rs;
+    h.self = fe.ptr(0);
+    h.self_bs = fe.rs;
+    h.out = fe3.ptr(0);
+    h.out_bs = fe3.rs;
+    h.shape = shp;
+    run_dwf_hop(L, *set, op, h, st);
+  });
+  tune(hop_key(L, P_F32, true, DM2_DENSE, DE_NONE, Ls, nrhs), [&](const LaunchShape* shp) {
+    DwfHop h = hop(true, DM_AINV, false, DE_NONE);
+    h.scale = 0.5;
+    h.in = fo.ptr(1);
+    h.in_bs = fo.rs;
+    h.self = ff.ptr(0);
+    h.self_bs = ff.rs;
+    h.out = fe3.ptr(0);
+    h.out_bs = fe3.rs;
+    h.shape = shp;
+    run_dwf_hop(L, *set, op, h, st);
+  });
+  tune(hop_key(L, P_F32, false, DM2_NONE, DE_NONE, Ls, nrhs), [&](const LaunchShape* shp) {
+    DwfHop h = hop(false, -1, false, DE_NONE);
+    h.out_parity = 1;
+    h.in = fx.ptr(0);
+    h.in_bs = fx.rs;
+    h.out = fo.ptr(1);
+    h.out_bs = fo.rs;
+    h.shape = shp;
+    run_dwf_hop(L, *set, op, h, st);
+  });
+  tune(hop_key(L, P_F32, false, DM2_DENSE, DE_NONE, Ls, nrhs), [&](const LaunchShape* shp) {
+    DwfHop h = hop(false, DM_A, false, DE_NONE);
+    h.in = ff.ptr(1);
+    h.in_bs = ff.rs;
+    h.self = ff.ptr(0);
+    h.self_bs = ff.rs;
+    h.out = ff2.ptr(0);
+    h.out_bs = ff2.rs;
+    h.shape = shp;
+    run_dwf_hop(L, *set, op, h, st);
+  });
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+  BR_CUDA(cudaStreamSynchronize(st));
+  tune_cache_save(L, keys);
 }
 
 }  // namespace bridge

@@ -129,8 +129,10 @@ BR_D void dwf_hop_dir(const DwfArgs& a, const char* in, const char* g_out, const
   hop_one<P, MU, false, ST>(in, g_in + MU * lbb, a.g.vh, b, b, wb, bc, acc);
 }
 
-template <int P, bool M1, int M2, int EPI>
-__global__ void __launch_bounds__(256) dwf_hop_kernel(const DwfArgs a) {
+// MINB: resident 256-thread blocks per SM the register allocation must allow
+// (2: <= 128 registers, 3: <= 85, 4: <= 64); picked per kernel by the tuner.
+template <int P, bool M1, int M2, int EPI, int MINB = 2>
+__global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
   using R = typename Tr<P>::R;
   extern __shared__ __align__(16) unsigned char dsm[];
   const int Ls = a.Ls, ns = a.ns;
@@ -245,8 +247,8 @@ __global__ void __launch_bounds__(256) dwf_hop_kernel(const DwfArgs a) {
 
 // out = M in per site (DX_PLAIN, optionally + s0 in), or the CG direction
 // update p = r + beta p followed by out = M p (DX_CGP).
-template <int P, int MODE>
-__global__ void __launch_bounds__(256) dwf_mix_kernel(const DwfMixArgs a) {
+template <int P, int MODE, int MINB = 2>
+__global__ void __launch_bounds__(256, MINB) dwf_mix_kernel(const DwfMixArgs a) {
   using R = typename Tr<P>::R;
   extern __shared__ __align__(16) unsigned char dsm[];
   const int Ls = a.Ls, ns = a.ns;

@@ -22,6 +22,11 @@ void dwf_apply_deo(bridge_lattice_s* L, const bridge_op& op, int out_parity, con
 void dwf_apply_dhat(bridge_lattice_s* L, const bridge_op& op, const Field& out, const Field& in, bool dagger,
                     cudaStream_t st);
 
+// Time the launch shapes (threads per block, register budget) of the FP32
+// kernels a solve with nrhs right-hand sides launches and keep the fastest
+// in the lattice's shape table (no-op for FP64, whose kernels have one shape).
+void tune_dwf_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int nrhs);
+
 // Solve D x = b for nrhs five-dimensional right-hand sides: canonical FP64
 // fields on the device (x: initial guess in, solution out).  Blocking.
 // Returns the overall status and fills info[nrhs].

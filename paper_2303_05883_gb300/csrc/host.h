@@ -243,6 +243,11 @@ void norm2_field(bridge_lattice_s* L, const Field& f, int parity, RedArgs red, c
 void clover_site(bridge_lattice_s* L, int prec, bool inverse, double kcsw, int parity, const Field& src, int sp,
                  const Field& dst, int dp, int nrhs, cudaStream_t st, CloverSet* set = nullptr);
 
+// Scratch data for timing runs: pseudo-random values in [-1, 1).
+void fill_scratch(const Field& f, uint32_t seed, cudaStream_t st);
+// Append the shape-table entries `keys` to the tuning cache file, if one is set.
+void tune_cache_save(bridge_lattice_s* L, const std::vector<std::string>& keys);
+
 // Reusable field of this lattice (allocated on first use).
 Field& workspace(bridge_lattice_s* L, const std::string& name, int prec, int subset, int nrhs);
 

@@ -15,8 +15,11 @@ bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, c
 // Combinations instantiated (m1, m2, epi): (1, NONE, NONE), (1, PLAIN, NONE),
 // (1, PLAIN, NORM), (1, PLAIN, CGUPD), (1, DENSE, NONE), (0, NONE, NONE),
 // (0, DENSE, NONE), (0, DENSE, NORM); F64 and F32.  false for any other.
-bool launch_dwf_hop(int prec, bool m1, int m2, int epi, const DwfArgs& a, cudaStream_t st);
-bool launch_dwf_mix(int prec, int mode, const DwfMixArgs& a, cudaStream_t st);
+// variant: register budget of the FP32 kernels, 0/1/2 = at most 128/85/64
+// registers per thread (FP64: one variant).
+constexpr int DWF_NVARIANT = 3;
+bool launch_dwf_hop(int prec, bool m1, int m2, int epi, const DwfArgs& a, cudaStream_t st, int variant = 0);
+bool launch_dwf_mix(int prec, int mode, const DwfMixArgs& a, cudaStream_t st, int variant = 0);
 
 // ----------------------------------------------------- BiCGStab vectors
 enum BlasOp { B_INIT = 0, B_S = 1, B_XR = 2, B_P = 3 };

@@ -16,6 +16,7 @@
 #include <fstream>
 #include <sstream>
 
+#include "dwf.h"
 #include "host.h"
 
 using namespace bridge;
@@ -52,7 +53,7 @@ void tune_cache_load(bridge_lattice_s* L) {
     if (dev == tag) L->tuned[key] = LaunchShape{block, nblk, variant};
 }
 
-static void tune_cache_save(bridge_lattice_s* L, const std::vector<std::string>& keys) {
+void tune_cache_save(bridge_lattice_s* L, const std::vector<std::string>& keys) {
   const std::string path = cache_path();
   if (path.empty()) return;
   std::ofstream f(path, std::ios::app);
@@ -77,7 +78,7 @@ __global__ void k_fill(float* p, size_t n, uint32_t seed) {
   }
 }
 
-static void fill(const Field& f, uint32_t seed, cudaStream_t st) {
+void fill_scratch(const Field& f, uint32_t seed, cudaStream_t st) {
   const size_t n = f.buf->bytes / sizeof(float);
   k_fill<<<(unsigned)std::min<size_t>((n + 255) / 256, 152 * 32), 256, 0, st>>>(reinterpret_cast<float*>(f.buf->ptr), n, seed);
 }
@@ -140,10 +141,10 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
   cudaStream_t st = L->stream;
   Field fin = make_field(prec, BRIDGE_FULL, nrhs, vh), fout = make_field(prec, BRIDGE_FULL, nrhs, vh);
   Field f2 = make_field(prec, BRIDGE_FULL, nrhs, vh), fx = make_field(px, BRIDGE_EVEN, nrhs, vh);
-  fill(fin, 1u, st);
-  fill(f2, 2u, st);
-  fill(fx, 3u, st);
-  fill(fout, 4u, st);
+  fill_scratch(fin, 1u, st);
+  fill_scratch(f2, 2u, st);
+  fill_scratch(fx, 3u, st);
+  fill_scratch(fout, 4u, st);
   BR_CUDA(cudaGetLastError());
   DevBuf partials((size_t)nrhs * ((vh + 63) / 64) * 4 * sizeof(double)), counter(256),
       scal(sizeof(BiCGScalars) * nrhs), result(sizeof(double) * 4 * nrhs);
@@ -291,13 +292,18 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
 extern "C" int bridge_tune(bridge_lattice L, const bridge_op* op, int prec, int nrhs) {
   try {
     if (!L || !op || nrhs < 1 || prec < BRIDGE_F64 || prec > BRIDGE_BF16) return BRIDGE_EINVAL;
-    if (op->kind != BRIDGE_WILSON && op->kind != BRIDGE_CLOVER) {
-      set_error(BRIDGE_EINVAL, "bridge_tune takes WILSON and CLOVER operators");
+    if (op->kind != BRIDGE_WILSON && op->kind != BRIDGE_CLOVER && op->kind != BRIDGE_MOBIUS) {
+      set_error(BRIDGE_EINVAL, "op.kind");
       return BRIDGE_EINVAL;
     }
     if (!L->have_gauge) return BRIDGE_ESTATE;
     std::lock_guard<std::mutex> lk(L->api_mu);
-    tune_solver_kernels(L, *op, prec, nrhs);
+    if (op->kind == BRIDGE_MOBIUS) {
+      check_mobius(*op);
+      tune_dwf_kernels(L, *op, prec, nrhs);
+    } else {
+      tune_solver_kernels(L, *op, prec, nrhs);
+    }
   } catch (const Error& e) {
     set_error(e.code, e.msg);
     return e.code;
