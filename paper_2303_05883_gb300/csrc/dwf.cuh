@@ -19,8 +19,9 @@
 // term of its (site, slice) with spin projection, exactly as the Wilson
 // stencil does, and leaves it in shared memory; after one barrier each
 // thread forms its output slice as a row of the s-matrix times the Ls hop
-// results of its site.  The Ls threads of a site read the same eight links,
-// which L1 serves after the first.
+// results of its site.  The eight links of each site (row 2 rebuilt) and its
+// neighbour indices are staged in shared memory once per block and read by
+// all Ls slices of the site.
 //
 //   out_s = sum_t M1[s][t] (scale * H in)_t          (or scale * H in)
 //         + s2 * self_s | sum_t M2[s][t] self_t      (optional)
@@ -86,7 +87,8 @@ BR_HD long dwf_hop_smem(int prec, int Ls, int ns, bool m1, bool m2dense) {
   const long R = prec == P_F64 ? 8 : 4;
   const long mats = (m1 ? 1 : 0) + (m2dense ? 1 : 0);
   const long vecs = (m1 ? 1 : 0) + (m2dense ? 1 : 0);
-  return mats * 2 * Ls * Ls * R + vecs * (long)Ls * 12 * ns * 2 * R;
+  const long links = 8L * 9 * ns * 2 * R + 8L * ns * 4;  // staged links and neighbour words
+  return links + mats * 2 * Ls * Ls * R + vecs * (long)Ls * 12 * ns * 2 * R;
 }
 BR_HD long dwf_mix_smem(int prec, int Ls, int ns) {
   const long R = prec == P_F64 ? 8 : 4;
@@ -117,16 +119,73 @@ BR_D void stage_row(cx<R>* sh, int ns, int s, int sl, const cx<R> v[12]) {
   for (int k = 0; k < 12; ++k) sh[((long)s * 12 + k) * ns + sl] = v[k];
 }
 
-template <int P, int MU, bool ST>
-BR_D void dwf_hop_dir(const DwfArgs& a, const char* in, const char* g_out, const char* g_in, long lbb, uint32_t ih,
-                      const int c[4], uint32_t xh, cx<typename Tr<P>::R> acc[12]) {
+// One hop from shared data: the link (9 complex entries, stride ns) and the
+// neighbour index with its wrap flag in bit 31, staged once per site.
+template <int P, int MU, bool FWD>
+BR_D void hop_shared(const char* in, long vh, uint32_t nbw, const cx<typename Tr<P>::R>* lk, int ns,
+                     typename Tr<P>::R bc, cx<typename Tr<P>::R> acc[12]) {
   using R = typename Tr<P>::R;
-  uint32_t f, b;
-  bool wf, wb;
-  neighbours<MU>(a.g, ih, c, xh, f, b, wf, wb);
-  const R bc = pick<R>(a.bc[MU], a.bcf[MU]);
-  hop_one<P, MU, true, ST>(in, g_out + MU * lbb, a.g.vh, f, ih, wf, bc, acc);
-  hop_one<P, MU, false, ST>(in, g_in + MU * lbb, a.g.vh, b, b, wb, bc, acc);
+  const uint32_t nb = nbw & 0x7fffffffu;
+  cx<R> h[2][3];
+  {
+    cx<R> psi[12];
+    load_spinor<P>(in, vh, nb, psi);
+    project<R, MU, FWD>(psi, h);
+  }
+  if (nbw >> 31) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) h[k][c] = bc * h[k][c];
+  }
+  cx<R> U[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) U[k] = lk[k * ns];
+  cx<R> u[2][3];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (FWD)
+        u[k][r] = U[3 * r] * h[k][0] + U[3 * r + 1] * h[k][1] + U[3 * r + 2] * h[k][2];
+      else
+        u[k][r] = cmul_conj(U[r], h[k][0]) + cmul_conj(U[3 + r], h[k][1]) + cmul_conj(U[6 + r], h[k][2]);
+    }
+  reconstruct<R, MU, FWD>(u, acc);
+}
+
+// Stage the links and neighbour indices of the block's ns sites: entry
+// d = 2 mu + (0 forward, 1 backward) holds U_mu(x) or U_mu(x - mu) with all 9
+// entries (row 2 rebuilt for 12-real storage) at shl[(d * 9 + k) * ns + site].
+template <int P>
+BR_D void stage_links(const DwfArgs& a, int sb, cx<typename Tr<P>::R>* shl, uint32_t* shn) {
+  using R = typename Tr<P>::R;
+  const int ns = a.ns, p = a.out_parity;
+  const long vh = a.g.vh;
+  const long lbb = link_block_bytes(P, vh);
+  const char* g_out = a.gauge + (long)p * 4 * lbb;
+  const char* g_in = a.gauge + (long)(1 - p) * 4 * lbb;
+  for (int i = threadIdx.x; i < 8 * ns; i += blockDim.x) {
+    const int sl = i % ns, d = i / ns, mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    const uint32_t ih = (uint32_t)sb * ns + sl;
+    if (ih >= (uint32_t)vh) continue;
+    int c[4];
+    uint32_t xh, f, b;
+    bool wf, wb;
+    site_coords(a.g, ih, p, c, xh);
+    switch (mu) {
+      case 0: neighbours<0>(a.g, ih, c, xh, f, b, wf, wb); break;
+      case 1: neighbours<1>(a.g, ih, c, xh, f, b, wf, wb); break;
+      case 2: neighbours<2>(a.g, ih, c, xh, f, b, wf, wb); break;
+      default: neighbours<3>(a.g, ih, c, xh, f, b, wf, wb); break;
+    }
+    Link<R> U;
+    load_link<P, true>((fwd ? g_out : g_in) + mu * lbb, vh, fwd ? ih : b, U);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) shl[((long)d * 9 + k) * ns + sl] = U.m[k / 3][k % 3];
+    shn[d * ns + sl] = (fwd ? f : b) | ((fwd ? wf : wb) ? 0x80000000u : 0u);
+  }
 }
 
 // MINB: resident 256-thread blocks per SM the register allocation must allow
@@ -137,7 +196,9 @@ __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const int Ls = a.Ls, ns = a.ns;
   const int nm = 2 * Ls * Ls;
-  R* mat1 = reinterpret_cast<R*>(dsm);
+  cx<R>* shl = reinterpret_cast<cx<R>*>(dsm);                 // [8][9][ns] links
+  uint32_t* shn = reinterpret_cast<uint32_t*>(shl + 72L * ns);  // [8][ns] neighbours
+  R* mat1 = reinterpret_cast<R*>(shn + 8L * ns);
   R* mat2 = mat1 + (M1 ? nm : 0);
   cx<R>* shh = reinterpret_cast<cx<R>*>(mat2 + (M2 == DM2_DENSE ? nm : 0));
   cx<R>* shs = shh + (M1 ? (long)Ls * 12 * ns : 0);
@@ -156,23 +217,24 @@ __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
     for (int i = threadIdx.x; i < nm; i += blockDim.x) mat1[i] = reinterpret_cast<const R*>(a.m1)[i];
   if (M2 == DM2_DENSE)
     for (int i = threadIdx.x; i < nm; i += blockDim.x) mat2[i] = reinterpret_cast<const R*>(a.m2)[i];
+  if (!skip) stage_links<P>(a, sb, shl, shn);
+  __syncthreads();
 
-  const int p = a.out_parity;
   cx<R> acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = czero<R>();
   if (valid) {
-    const long lbb = link_block_bytes(P, vh);
-    const char* g_out = a.gauge + (long)p * 4 * lbb;
-    const char* g_in = a.gauge + (long)(1 - p) * 4 * lbb;
     const char* in = a.in + q * a.in_bs;
-    int c[4];
-    uint32_t xh;
-    site_coords(a.g, ih, p, c, xh);
-    dwf_hop_dir<P, 0, false>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
-    dwf_hop_dir<P, 1, false>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
-    dwf_hop_dir<P, 2, false>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
-    dwf_hop_dir<P, 3, false>(a, in, g_out, g_in, lbb, ih, c, xh, acc);
+    const cx<R>* lk = shl + sl;
+    const uint32_t* nw = shn + sl;
+    hop_shared<P, 0, true>(in, vh, nw[0 * ns], lk + 0 * 9 * ns, ns, pick<R>(a.bc[0], a.bcf[0]), acc);
+    hop_shared<P, 0, false>(in, vh, nw[1 * ns], lk + 1 * 9 * ns, ns, pick<R>(a.bc[0], a.bcf[0]), acc);
+    hop_shared<P, 1, true>(in, vh, nw[2 * ns], lk + 2 * 9 * ns, ns, pick<R>(a.bc[1], a.bcf[1]), acc);
+    hop_shared<P, 1, false>(in, vh, nw[3 * ns], lk + 3 * 9 * ns, ns, pick<R>(a.bc[1], a.bcf[1]), acc);
+    hop_shared<P, 2, true>(in, vh, nw[4 * ns], lk + 4 * 9 * ns, ns, pick<R>(a.bc[2], a.bcf[2]), acc);
+    hop_shared<P, 2, false>(in, vh, nw[5 * ns], lk + 5 * 9 * ns, ns, pick<R>(a.bc[2], a.bcf[2]), acc);
+    hop_shared<P, 3, true>(in, vh, nw[6 * ns], lk + 6 * 9 * ns, ns, pick<R>(a.bc[3], a.bcf[3]), acc);
+    hop_shared<P, 3, false>(in, vh, nw[7 * ns], lk + 7 * 9 * ns, ns, pick<R>(a.bc[3], a.bcf[3]), acc);
     const R sc = pick<R>(a.scale, a.scalef);
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = sc * acc[k];
