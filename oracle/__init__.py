@@ -20,6 +20,8 @@ paper is silent, the docstring states the reading taken):
                   blocks over four-dimensional parity with the fifth
                   coordinate as an inner index, the Schur operator and its
                   adjoint;
+* ``staggered`` -- the staggered operator (Sec. 2) with its even-odd blocks
+                  and the Hermitian positive definite even system solved by CG;
 * ``solvers``  -- BiCGStab (van der Vorst) as named in Sec. 3, CG and CG on
                   the normal equations (the domain-wall solver of Fig. 7),
                   dense matrices by their matrix elements and dense LU solves.
@@ -35,7 +37,10 @@ clover term, which is a convention the paper does not state (the abelian-flux
 closed form pins the reading taken, not the paper).  The domain-wall operator
 is pinned by the overlap relation (its boundary-field operator equals the
 polar approximation of the sign function of the Moebius kernel), in the free
-field against the Fourier symbol and on random gauge fields.
+field against the Fourier symbol and on random gauge fields.  The staggered
+operator is pinned by the free-field closed form of D^dagger D on plane
+waves, anti-hermiticity of its hopping term, gauge covariance, and the dense
+matrix filled from its matrix elements (Schur complement, LU solve).
 """
 
-from . import lattice, gamma, dirac, evenodd, domainwall, solvers  # noqa: F401
+from . import lattice, gamma, dirac, evenodd, domainwall, staggered, solvers  # noqa: F401

@@ -10,7 +10,7 @@ from __future__ import annotations
 import numpy as np
 
 import synth
-from oracle import dirac, domainwall, evenodd, gamma, solvers
+from oracle import dirac, domainwall, evenodd, gamma, solvers, staggered
 from oracle.lattice import Lattice
 
 
@@ -397,3 +397,91 @@ def cg_error(n=48, seed=91, maxiter=400):
     bh = gen.standard_normal((3, op.lat.V // 2, 4, 3)) + 1j * gen.standard_normal((3, op.lat.V // 2, 4, 3))
     xe, _ = solvers.cgnr(op.schur, op.schur_dag, bh, tol=1e-13, maxiter=maxiter)
     return max(err, rel(xe.reshape(-1), np.linalg.solve(S, bh.reshape(-1))))
+
+
+# --- staggered --------------------------------------------------------------------------
+
+
+def staggered_free_field_error(dims=(4, 6, 4, 8), mass=0.05, modes=((0, 0, 0, 0), (1, 2, 3, 1), (3, 5, 1, 6)), seed=101):
+    """Free field: D^dagger D = m^2 + sum_mu sin^2 p_mu on plane waves, with
+    D^dagger = 2m - D (the hopping term is anti-Hermitian)."""
+    lat = Lattice(dims)
+    U = synth.unit_gauge(dims)
+    op = staggered.Staggered(U, lat, mass)
+    gen = np.random.default_rng(seed)
+    L = lat.dims
+    err = 0.0
+    for n in modes:
+        p = [2 * np.pi * n[k] / L[k] for k in range(3)] + [(2 * n[3] + 1) * np.pi / L[3]]
+        phase = np.exp(1j * sum(p[mu] * lat.coords[mu] for mu in range(4)))
+        u = gen.standard_normal(3) + 1j * gen.standard_normal(3)
+        chi = phase[:, None] * u[None]
+        Dchi = op.full(chi)
+        DdD = 2 * mass * Dchi - op.full(Dchi)
+        want = (mass**2 + sum(np.sin(q) ** 2 for q in p)) * chi
+        err = max(err, rel(DdD, want))
+    return err
+
+
+def staggered_antihermitian_error(dims=(4, 4, 6, 4), eps=0.5, seed=103):
+    """<u, H v> = -<H u, v> for the hopping term on a random gauge field."""
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    gen = np.random.default_rng(seed)
+    u = gen.standard_normal((lat.V, 3)) + 1j * gen.standard_normal((lat.V, 3))
+    v = gen.standard_normal((lat.V, 3)) + 1j * gen.standard_normal((lat.V, 3))
+    lhs = np.vdot(u, staggered.hop(U, v, lat))
+    rhs = -np.vdot(staggered.hop(U, u, lat), v)
+    return abs(lhs - rhs) / (np.linalg.norm(u) * np.linalg.norm(v))
+
+
+def staggered_covariance_error(dims=(4, 6, 4, 4), mass=0.1, eps=0.5, seed=105):
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    gen = np.random.default_rng(seed)
+    Om = random_su3(lat.V, gen)
+    Ug = gauge_transform(U, lat, Om)
+    chi = gen.standard_normal((lat.V, 3)) + 1j * gen.standard_normal((lat.V, 3))
+    rot = lambda v: np.einsum("nab,nb->na", Om, v)  # noqa: E731
+    return rel(staggered.Staggered(Ug, lat, mass).full(rot(chi)), rot(staggered.Staggered(U, lat, mass).full(chi)))
+
+
+def dense_staggered(U, lat: Lattice, mass: float, bc=(1, 1, 1, -1)) -> np.ndarray:
+    """D as a dense (3V x 3V) matrix filled from its matrix elements with explicit loops:
+    m on the diagonal, +eta bc U_mu(x)/2 at y = x + mu, -eta bc U_mu(x - mu)^dag / 2 at y = x - mu."""
+    V = lat.V
+    M = np.zeros((3 * V, 3 * V), dtype=np.complex128)
+    for x in range(V):
+        M[3 * x : 3 * x + 3, 3 * x : 3 * x + 3] += mass * np.eye(3)
+        c = lat.coords[:, x]
+        for mu in range(4):
+            e = (-1.0) ** int(sum(c[:mu]))
+            (y,), (w,) = lat.neighbor(np.array([x]), mu, +1)
+            ph = bc[mu] if w else 1.0
+            M[3 * x : 3 * x + 3, 3 * y : 3 * y + 3] += 0.5 * e * ph * U[mu][x]
+            (y,), (w,) = lat.neighbor(np.array([x]), mu, -1)
+            ph = bc[mu] if w else 1.0
+            M[3 * x : 3 * x + 3, 3 * y : 3 * y + 3] -= 0.5 * e * ph * U[mu][y].conj().T
+    return M
+
+
+def staggered_dense_error(dims=(2, 2, 2, 4), mass=0.1, eps=0.5, seed=107):
+    """The stencil against the dense matrix; the Schur operator against the dense
+    Schur complement; the even-odd CG solve against LU."""
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    op = staggered.Staggered(U, lat, mass)
+    M = dense_staggered(U, lat, mass)
+    Mb = solvers.dense_matrix(lambda v: op.full(v.reshape(-1, 3)).reshape(-1), 3 * lat.V)
+    err = rel(Mb, M)
+    e = np.concatenate([np.arange(3 * s, 3 * s + 3) for s in lat.even])
+    o = np.concatenate([np.arange(3 * s, 3 * s + 3) for s in lat.odd])
+    Mee, Meo, Moe, Moo = M[np.ix_(e, e)], M[np.ix_(e, o)], M[np.ix_(o, e)], M[np.ix_(o, o)]
+    S = np.linalg.solve(Mee, Mee - Meo @ np.linalg.solve(Moo, Moe))
+    Sb = solvers.dense_matrix(lambda v: op.schur(v.reshape(-1, 3)).reshape(-1), len(e))
+    err = max(err, rel(Sb, S))
+    gen = np.random.default_rng(seed)
+    b = gen.standard_normal((lat.V, 3)) + 1j * gen.standard_normal((lat.V, 3))
+    x_lu = np.linalg.solve(M, b.reshape(-1)).reshape(b.shape)
+    xe, _ = solvers.cg(op.normal_even, op.prepare(b), tol=1e-14, maxiter=2000)
+    return max(err, rel(op.reconstruct(xe, b), x_lu))

@@ -62,6 +62,18 @@ MUTANTS = [
     ("domainwall", "return _mix(self.B[0].T, self.B[1].T, _g5(h))", "return _mix(self.B[0].T, self.B[1].T, h)",
      pins.mobius_adjoint_error, 1e-10),
     ("solvers", "p = r + (rr_new / rr) * p", "p = r", pins.cg_error, 1e-10),
+    # staggered
+    ("staggered", "for nu in range(mu):", "for nu in range(mu + 1):", pins.staggered_free_field_error, 1e-10),
+    ("staggered", "out -= 0.5 * e * np.einsum", "out += 0.5 * e * np.einsum", pins.staggered_free_field_error, 1e-10),
+    ("staggered", "out += 0.5 * e * np.einsum(\"nab,nb->na\", U[mu][sites]", "out += e * np.einsum(\"nab,nb->na\", U[mu][sites]",
+     pins.staggered_free_field_error, 1e-10),
+    ("staggered", "_dag(U[mu][j]), ph * chi[j]", "U[mu][j], ph * chi[j]", pins.staggered_antihermitian_error, 1e-10),
+    ("staggered", "np.einsum(\"nab,nb->na\", U[mu][sites], ph * chi[j])", "np.einsum(\"nba,nb->na\", U[mu][sites], ph * chi[j])",
+     pins.staggered_covariance_error, 1e-10),
+    ("staggered", "return self.m * b[lat.even] - self.D_hop(0, b[lat.odd])", "return self.m * b[lat.even] + self.D_hop(0, b[lat.odd])",
+     pins.staggered_dense_error, 1e-10),
+    ("staggered", "x[lat.odd] = (b[lat.odd] - self.D_hop(1, x_e)) / self.m", "x[lat.odd] = (b[lat.odd] - self.D_hop(1, x_e))",
+     pins.staggered_dense_error, 1e-10),
     ("solvers", "alpha = rr / dot(p, Ap).real", "alpha = rr / dot(Ap, Ap).real", pins.cg_error, 1e-10),
 ]
 

@@ -184,3 +184,32 @@ def test_mobius_blocks_reassemble_full_operator():
         s = lat.sites_of(p)
         full[:, s] = op.D_pp(psi[:, s]) + op.D_hop(p, psi[:, lat.sites_of(1 - p)])
     assert pins.rel(full, op.full(psi)) < 1e-14
+
+
+# --- staggered (Sec. 2 operators) --------------------------------------------------------
+
+
+def test_staggered_free_field_normal_operator_closed_form():
+    assert pins.staggered_free_field_error() < 1e-13
+
+
+def test_staggered_hopping_antihermitian():
+    assert pins.staggered_antihermitian_error() < 1e-15
+
+
+def test_staggered_gauge_covariance():
+    assert pins.staggered_covariance_error() < 1e-13
+
+
+def test_staggered_dense_schur_and_evenodd_solve():
+    assert pins.staggered_dense_error() < 1e-12
+
+
+def test_staggered_phases():
+    from oracle import staggered
+
+    lat = Lattice((4, 2, 2, 2))
+    c = lat.coords
+    assert np.all(staggered.eta(lat, 0) == 1)
+    assert np.all(staggered.eta(lat, 1) == (-1.0) ** c[0])
+    assert np.all(staggered.eta(lat, 3) == (-1.0) ** (c[0] + c[1] + c[2]))
