@@ -72,7 +72,7 @@ enum bridge_status {
  * blocks as plain 16-bit values, and compute in FP32. */
 enum bridge_prec { BRIDGE_F64 = 0, BRIDGE_F32 = 1, BRIDGE_F16 = 2, BRIDGE_BF16 = 3 };
 
-enum bridge_kind { BRIDGE_WILSON = 0, BRIDGE_CLOVER = 1, BRIDGE_MOBIUS = 2 };
+enum bridge_kind { BRIDGE_WILSON = 0, BRIDGE_CLOVER = 1, BRIDGE_MOBIUS = 2, BRIDGE_STAGGERED = 3 };
 
 /* Site subset of a field: one parity (half lattice) or the full lattice. */
 enum bridge_subset { BRIDGE_EVEN = 0, BRIDGE_ODD = 1, BRIDGE_FULL = 2 };
@@ -112,6 +112,19 @@ typedef struct {
   double M5;    /* domain-wall height */
   double b5, c5; /* Moebius coefficients */
   double mf;    /* quark mass */
+  /* STAGGERED only (Sec. 2: the staggered action).  With eta_0 = 1,
+   * eta_1 = (-1)^x, eta_2 = (-1)^(x+y), eta_3 = (-1)^(x+y+z):
+   *   D chi(x) = mass chi(x) + (1/2) sum_mu eta_mu(x) [U_mu(x) chi(x+mu)
+   *                                                   - U_mu(x-mu)^dag chi(x-mu)],
+   * boundary phases bc as above.  Spinor arguments hold one colour vector
+   * per site: canonical layout [rhs][t][z][y][x][colour 3][re,im] (6 doubles
+   * per site instead of 24).  Even-odd blocks (Eq. 1): D_ee = D_oo = mass,
+   * D^(eo) = 1 - D_eo D_oe / mass^2.  The solver is CG on the Hermitian
+   * positive definite mass^2 - D_eo D_oe (the even block of the normal
+   * equations) inside the FP64 defect correction; F64 or F32 only.  Not
+   * accepted by bridge_apply, bridge_mult_Dhat_noalloc, bridge_tune or
+   * bridge_submit. */
+  double mass;
 } bridge_op;
 
 typedef struct {

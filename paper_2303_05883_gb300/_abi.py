@@ -24,7 +24,7 @@ BRIDGE_ECUDA = -6
 BRIDGE_ESTATE = -7
 
 BRIDGE_F64, BRIDGE_F32, BRIDGE_F16, BRIDGE_BF16 = 0, 1, 2, 3
-BRIDGE_WILSON, BRIDGE_CLOVER, BRIDGE_MOBIUS = 0, 1, 2
+BRIDGE_WILSON, BRIDGE_CLOVER, BRIDGE_MOBIUS, BRIDGE_STAGGERED = 0, 1, 2, 3
 BRIDGE_EVEN, BRIDGE_ODD, BRIDGE_FULL = 0, 1, 2
 BRIDGE_APPLY_D, BRIDGE_APPLY_DEO, BRIDGE_APPLY_DOE, BRIDGE_APPLY_DHAT = 0, 1, 2, 3
 BRIDGE_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -41,6 +41,7 @@ class bridge_op(ctypes.Structure):
         ("b5", c_double),
         ("c5", c_double),
         ("mf", c_double),
+        ("mass", c_double),
     ]
 
 

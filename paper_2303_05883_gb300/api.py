@@ -17,7 +17,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import _abi
-from ._abi import BRIDGE_CLOVER, BRIDGE_MOBIUS, BRIDGE_WILSON, bridge_info, bridge_kstat, bridge_op, bridge_solver, check
+from ._abi import BRIDGE_CLOVER, BRIDGE_MOBIUS, BRIDGE_STAGGERED, BRIDGE_WILSON, bridge_info, bridge_kstat, bridge_op, bridge_solver, check
 
 PRECISIONS = {"f64": _abi.BRIDGE_F64, "f32": _abi.BRIDGE_F32, "f16": _abi.BRIDGE_F16, "bf16": _abi.BRIDGE_BF16}
 
@@ -26,10 +26,17 @@ def _prec(p) -> int:
     return PRECISIONS[p] if isinstance(p, str) else int(p)
 
 
-def make_op(kind="wilson", kappa=0.12, csw=0.0, bc=(1, 1, 1, -1), Ls=0, M5=0.0, b5=0.0, c5=0.0, mf=0.0) -> bridge_op:
-    k = {"wilson": BRIDGE_WILSON, "clover": BRIDGE_CLOVER, "mobius": BRIDGE_MOBIUS}.get(kind, kind)
+def make_op(kind="wilson", kappa=0.12, csw=0.0, bc=(1, 1, 1, -1), Ls=0, M5=0.0, b5=0.0, c5=0.0, mf=0.0,
+            mass=0.0) -> bridge_op:
+    k = {"wilson": BRIDGE_WILSON, "clover": BRIDGE_CLOVER, "mobius": BRIDGE_MOBIUS, "staggered": BRIDGE_STAGGERED}.get(
+        kind, kind)
     return bridge_op(int(k), float(kappa), float(csw), (c_int * 4)(*[int(b) for b in bc]), int(Ls), float(M5),
-                     float(b5), float(c5), float(mf))
+                     float(b5), float(c5), float(mf), float(mass))
+
+
+def make_staggered(mass, bc=(1, 1, 1, -1)) -> bridge_op:
+    """Staggered operator with quark mass ``mass``; fields hold one colour vector per site."""
+    return make_op("staggered", bc=bc, mass=mass)
 
 
 def make_mobius(Ls, M5, b5, c5, mf, bc=(1, 1, 1, -1)) -> bridge_op:
@@ -39,7 +46,10 @@ def make_mobius(Ls, M5, b5, c5, mf, bc=(1, 1, 1, -1)) -> bridge_op:
 
 def _nrhs(op, a) -> int:
     """Right-hand sides in a canonical array: its leading dimensions count
-    four-dimensional fields, Ls of them per right-hand side for MOBIUS."""
+    four-dimensional fields, Ls of them per right-hand side for MOBIUS;
+    STAGGERED fields end in (sites, 3)."""
+    if op.kind == BRIDGE_STAGGERED:
+        return int(np.prod(a.shape[:-2])) if a.ndim > 2 else 1
     n4 = int(np.prod(a.shape[:-3])) if a.ndim > 3 else 1
     if op.kind == BRIDGE_MOBIUS and op.Ls >= 1:  # (Ls < 1 is left to the library to refuse)
         if n4 % op.Ls:
@@ -286,8 +296,8 @@ def bridge_request_release(req: Request) -> None:
 
 
 def bridge_stats(lat):
-    arr = (bridge_kstat * 32)()
-    n = _abi.load().bridge_stats(lat, arr, 32)
+    arr = (bridge_kstat * 64)()
+    n = _abi.load().bridge_stats(lat, arr, 64)
     check(n, "bridge_stats")
     return {
         arr[k].name.decode(): dict(launches=arr[k].launches, bytes=arr[k].bytes, flops=arr[k].flops, ms=arr[k].ms)

@@ -6,6 +6,7 @@
 
 #include "dwf.h"
 #include "solver.h"
+#include "stag.h"
 
 using namespace bridge;
 
@@ -47,20 +48,28 @@ struct bridge_field_s {
 
 static void check_op(const bridge_op* op) {
   BR_CHECK(op != nullptr, BRIDGE_EINVAL, "op is NULL");
-  BR_CHECK(op->kind == BRIDGE_WILSON || op->kind == BRIDGE_CLOVER || op->kind == BRIDGE_MOBIUS, BRIDGE_EINVAL,
-           "op.kind");
+  BR_CHECK(op->kind == BRIDGE_WILSON || op->kind == BRIDGE_CLOVER || op->kind == BRIDGE_MOBIUS ||
+               op->kind == BRIDGE_STAGGERED,
+           BRIDGE_EINVAL, "op.kind");
   for (int k = 0; k < 4; ++k) BR_CHECK(op->bc[k] == 1 || op->bc[k] == -1, BRIDGE_EINVAL, "op.bc must be +1 or -1");
   if (op->kind == BRIDGE_MOBIUS)
     check_mobius(*op);
+  else if (op->kind == BRIDGE_STAGGERED)
+    check_staggered(*op);
   else
     BR_CHECK(std::isfinite(op->kappa) && std::isfinite(op->csw), BRIDGE_EINVAL, "op.kappa / op.csw not finite");
 }
-// Entry points that serve Wilson and clover only.
+// Entry points that serve only some operator kinds.
 static void check_not_mobius(const bridge_op* op, const char* what) {
   BR_CHECK(op->kind != BRIDGE_MOBIUS, BRIDGE_EINVAL, std::string(what) + " does not take MOBIUS operators");
 }
-// Four-dimensional slices per right-hand side.
-static int slices(const bridge_op& op) { return op.kind == BRIDGE_MOBIUS ? op.Ls : 1; }
+static void check_not_staggered(const bridge_op* op, const char* what) {
+  BR_CHECK(op->kind != BRIDGE_STAGGERED, BRIDGE_EINVAL, std::string(what) + " does not take STAGGERED operators");
+}
+// Doubles per site of one right-hand side of a canonical spinor argument.
+static long site_doubles(const bridge_op& op) {
+  return op.kind == BRIDGE_MOBIUS ? 24L * op.Ls : op.kind == BRIDGE_STAGGERED ? 6L : 24L;
+}
 static void check_prec(int prec) {
   BR_CHECK(prec >= BRIDGE_F64 && prec <= BRIDGE_BF16, BRIDGE_EINVAL, "precision");
 }
@@ -81,6 +90,31 @@ static char* stage(std::unique_ptr<DevBuf>& b, size_t n) {
 static void mult_dev(bridge_lattice_s* L, const bridge_op& op, int prec, int which, int out_parity, const double* in,
                      double* out, int nrhs) {
   cudaStream_t st = L->stream;
+  if (op_is_staggered(op)) {
+    BR_CHECK(prec == BRIDGE_F64 || prec == BRIDGE_F32, BRIDGE_EINVAL, "STAGGERED operators run in F64 or F32");
+    BR_CHECK(which != APPLY_DHAT_DAG, BRIDGE_EINVAL, "bridge_mult_Dhat_dag is provided for MOBIUS operators only");
+    if (which == BRIDGE_APPLY_D) {
+      Field& fi = stag_workspace(L, "mult_in", prec, BRIDGE_FULL, nrhs);
+      Field& fo = stag_workspace(L, "mult_out", prec, BRIDGE_FULL, nrhs);
+      stag_canon_to_field(L, in, fi, true, st);
+      stag_apply_d(L, op, fo, fi, st);
+      stag_field_to_canon(L, fo, out, true, st);
+    } else if (which == BRIDGE_APPLY_DEO) {
+      const int q = out_parity;
+      Field& fi = stag_workspace(L, "mult_in", prec, 1 - q, nrhs);
+      Field& fo = stag_workspace(L, "mult_out", prec, q, nrhs);
+      stag_canon_to_field(L, in, fi, false, st);
+      stag_apply_deo(L, op, q, fo, fi, st);
+      stag_field_to_canon(L, fo, out, false, st);
+    } else {
+      Field& fi = stag_workspace(L, "mult_in", prec, BRIDGE_EVEN, nrhs);
+      Field& fo = stag_workspace(L, "mult_out", prec, BRIDGE_EVEN, nrhs);
+      stag_canon_to_field(L, in, fi, false, st);
+      stag_apply_dhat(L, op, fo, fi, st);
+      stag_field_to_canon(L, fo, out, false, st);
+    }
+    return;
+  }
   if (op_is_mobius(op)) {
     BR_CHECK(prec == BRIDGE_F64 || prec == BRIDGE_F32, BRIDGE_EINVAL, "MOBIUS operators run in F64 or F32");
     const int nq = nrhs * op.Ls;
@@ -142,7 +176,7 @@ static int mult_common(bridge_lattice L, const bridge_op* op, int prec, int whic
   BR_CHECK(in != nullptr && out != nullptr, BRIDGE_EINVAL, "in/out is NULL");
   std::lock_guard<std::mutex> lk(L->api_mu);
   const long sites = which == BRIDGE_APPLY_D ? L->V : L->vh;
-  const size_t n = (size_t)nrhs * slices(*op) * sites * 24 * sizeof(double);
+  const size_t n = (size_t)nrhs * site_doubles(*op) * sites * sizeof(double);
   if (host) {
     double* din = reinterpret_cast<double*>(stage(L->stage_in, n));
     double* dout = reinterpret_cast<double*>(stage(L->stage_out, n));
@@ -169,7 +203,7 @@ static int solve_common(bridge_lattice L, const bridge_op* op, const bridge_solv
   if (nrhs == 0) return BRIDGE_OK;
   BR_CHECK(b != nullptr && x != nullptr, BRIDGE_EINVAL, "b/x is NULL");
   std::lock_guard<std::mutex> lk(L->api_mu);
-  const size_t n = (size_t)nrhs * slices(*op) * L->V * 24 * sizeof(double);
+  const size_t n = (size_t)nrhs * site_doubles(*op) * L->V * sizeof(double);
   const double* db = b;
   double* dx = x;
   if (host) {
@@ -181,6 +215,8 @@ static int solve_common(bridge_lattice L, const bridge_op* op, const bridge_solv
   int status;
   if (op_is_mobius(*op)) {
     status = dwf_solve(L, *op, *s, db, dx, nrhs, info);
+  } else if (op_is_staggered(*op)) {
+    status = stag_solve(L, *op, *s, db, dx, nrhs, info);
   } else {
     SolveState S(L, *op, *s, nrhs, L->stream, db, dx);
     while (!S.advance()) BR_CUDA(cudaEventSynchronize(S.wait_event()));
@@ -432,6 +468,7 @@ int bridge_apply(bridge_lattice L, const bridge_op* op, int which, bridge_field 
   BR_CHECK(out->f.nrhs == in->f.nrhs, BRIDGE_EINVAL, "fields differ in nrhs");
   BR_CHECK(out->f.buf != in->f.buf, BRIDGE_EINVAL, "in and out must differ");
   std::lock_guard<std::mutex> lk(L->api_mu);
+  check_not_staggered(op, "bridge_apply");
   if (op_is_mobius(*op)) {
     BR_CHECK(in->f.nrhs % op->Ls == 0, BRIDGE_EINVAL, "MOBIUS fields hold a multiple of Ls slices");
     BR_CHECK(in->f.prec == BRIDGE_F64 || in->f.prec == BRIDGE_F32, BRIDGE_EINVAL, "MOBIUS operators run in F64 or F32");
@@ -570,6 +607,7 @@ int bridge_submit(bridge_lattice L, const bridge_op* op, const bridge_solver* s,
   check_lat(L, true);
   check_op(op);
   check_not_mobius(op, "bridge_submit");
+  check_not_staggered(op, "bridge_submit");
   BR_CHECK(s != nullptr && b != nullptr && out != nullptr, BRIDGE_EINVAL, "NULL argument");
   BR_CHECK(s->tol > 0, BRIDGE_EINVAL, "tol must be > 0");
   if (s->mixed) check_prec(s->inner_prec);

@@ -57,6 +57,12 @@ enum KClass {
   K_DWF_SCHUR2CG,  // adjoint pass 2 fused with the CG update of x and r
   K_DWF_PREP,      // Moebius even-odd prepare / reconstruct
   K_DWF_RESID,     // Moebius FP64 residual b - D x with |r|^2
+  K_STAG_HOP,      // staggered: D_eo / D_oe and the full operator
+  K_STAG_PASS1,    // staggered CG / Schur pass 1: D_oe p
+  K_STAG_PASS2,    // staggered CG / Schur pass 2 with Re <p, q> -> alpha
+  K_STAG_VEC,      // staggered vector kernels and conversions
+  K_STAG_PREP,     // staggered even-odd prepare / reconstruct
+  K_STAG_RESID,    // staggered FP64 residual with |r|^2
   K_NCLASS
 };
 const char* kclass_name(int k);

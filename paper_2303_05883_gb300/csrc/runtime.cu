@@ -23,7 +23,9 @@ const char* kclass_name(int k) {
                                         "blas_init",    "blas_s",        "blas_xr",     "blas_p",
                                         "convert",      "norm",          "clover_site", "setup",
                                         "dwf_mix",      "dwf_hop",       "dwf_schur_pass1", "dwf_schur_pass2",
-                                        "dwf_schur_pass2_cg", "dwf_evenodd_prep", "dwf_residual64"};
+                                        "dwf_schur_pass2_cg", "dwf_evenodd_prep", "dwf_residual64",
+                                        "stag_hop",     "stag_pass1",    "stag_pass2",  "stag_vec",
+                                        "stag_prep",    "stag_residual64"};
   return (k >= 0 && k < K_NCLASS) ? names[k] : "?";
 }
 

@@ -292,7 +292,7 @@ void tune_solver_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int
 extern "C" int bridge_tune(bridge_lattice L, const bridge_op* op, int prec, int nrhs) {
   try {
     if (!L || !op || nrhs < 1 || prec < BRIDGE_F64 || prec > BRIDGE_BF16) return BRIDGE_EINVAL;
-    if (op->kind != BRIDGE_WILSON && op->kind != BRIDGE_CLOVER && op->kind != BRIDGE_MOBIUS) {
+    if (op->kind != BRIDGE_WILSON && op->kind != BRIDGE_CLOVER && op->kind != BRIDGE_MOBIUS) {  // STAGGERED: no tunable shapes
       set_error(BRIDGE_EINVAL, "op.kind");
       return BRIDGE_EINVAL;
     }

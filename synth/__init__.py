@@ -279,3 +279,37 @@ class MobiusWorkload:
 WORKLOADS["mobius_24x24x24x48x16"] = MobiusWorkload(
     "mobius_24x24x24x48x16", (24, 24, 24, 48), 16, 1.8, 1.5, 0.5, 0.01, 0.2, 5, 1, 1e-10
 )
+
+
+@dataclass(frozen=True)
+class StaggeredWorkload:
+    """One synthetic configuration of the staggered solver path."""
+
+    name: str
+    dims: tuple
+    mass: float
+    eps: float
+    seed: int
+    nrhs: int
+    tol: float
+    bc: tuple = field(default=(1, 1, 1, -1))
+    inner: str = "f32"
+    kind: str = "staggered"
+
+    @property
+    def volume(self) -> int:
+        return volume(self.dims)
+
+    def gauge(self) -> np.ndarray:
+        return gauge_field(self.dims, self.eps, self.seed)
+
+    def sources(self) -> np.ndarray:
+        """Gaussian colour-vector sources shaped (nrhs, V, 3)."""
+        V = volume(self.dims)
+        gen = rng(self.seed, FIELD_SOURCE)
+        return gen.standard_normal((self.nrhs, V, 3, 2)).view(np.complex128)[..., 0]
+
+
+# Staggered on 64^4, m = 0.05, links exp(0.2 i A): CG on the even system,
+# FP32 inner / FP64 outer to 1e-10.
+WORKLOADS["staggered_64x64x64x64"] = StaggeredWorkload("staggered_64x64x64x64", (64, 64, 64, 64), 0.05, 0.2, 6, 1, 1e-10)
