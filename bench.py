@@ -28,7 +28,8 @@ against the HBM peak.  Beside it the line reports:
 Moebius domain-wall operator (Ls = 16, M5 = 1.8, b = 1.5, c = 0.5,
 m_f = 0.01): a step is one mixed-precision CG solve on the normal equations
 of the even-odd system (FP32 inner, FP64 defect correction, 1e-10), beside
-D_eo alone and a plain FP64 CG solve.
+D_eo alone and a plain FP64 CG solve.  ``--workload staggered_64x64x64x64``
+does the same for the staggered operator (m = 0.05, CG on the even system).
 """
 
 from __future__ import annotations
@@ -840,6 +841,179 @@ def run_mobius(args):
         dist.destroy_process_group()
 
 
+def staggered_oracle_sample(w, U, b, nsites, seed):
+    """The FP64 oracle's staggered D at random sites."""
+    from oracle import staggered
+    from oracle.lattice import Lattice
+
+    lat = Lattice(w.dims)
+    orc = staggered.Staggered(U, lat, w.mass, w.bc)
+    sites = np.sort(np.random.default_rng(seed).choice(lat.V, nsites, replace=False))
+    _, secs, cores = cpu_cores_used(lambda: orc.full(b, sites=sites))
+    per_site = 48 + 8 * 144 + 48  # vector in, 8 links, vector out (FP64)
+    return nsites * per_site / secs / 1e9, secs, cores
+
+
+def run_staggered(args):
+    """Staggered: mixed CG solve steps, D_eo alone, FP64 CG, e2e, oracle."""
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__ as g
+
+    if rank == 0:
+        g.build()
+    if world > 1:
+        dist.barrier()
+    from ctypes import byref, c_void_p
+
+    import synth
+    from paper_2303_05883_gb300 import _abi, api
+
+    w = synth.WORKLOADS[args.workload]
+    U = w.gauge()
+    b_host = w.sources()  # (nrhs, V, 3)
+    b_dev = torch.from_numpy(b_host).to(f"cuda:{local}")
+    x_dev = torch.zeros_like(b_dev)
+    op = api.make_staggered(w.mass, bc=w.bc)
+    L = api.Lattice(w.dims)
+    L.upload(U)
+    h = L.handle
+    stream = L.stream
+    nrhs = w.nrhs
+    solver = api.make_solver(tol=w.tol, inner_prec=w.inner, mixed=1)
+    peak, peak_kind = peaks()
+
+    def solve_dev(prm):
+        x_dev.zero_()
+        torch.cuda.current_stream().synchronize()
+        info = (_abi.bridge_info * nrhs)()
+        st = _abi.load().bridge_solve_dev(h, byref(op), byref(prm), c_void_p(b_dev.data_ptr()),
+                                          c_void_p(x_dev.data_ptr()), nrhs, info)
+        _abi.check(st, "bridge_solve_dev")
+        return max((info[k] for k in range(nrhs)), key=lambda i: i.true_rel_residual)
+
+    for _ in range(args.warmup):
+        solve_dev(solver)
+    torch.cuda.synchronize()
+    api.bridge_stats_reset(h)
+    l0 = api.bridge_launch_count()
+    infos = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(solve_dev(solver))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = api.bridge_launch_count() - l0
+    st = api.bridge_stats(h)
+    total_bytes = sum(v["bytes"] for v in st.values())
+    ms, total_bytes = aggregate_ranks(ms, total_bytes, device=f"cuda:{local}")
+    value = total_bytes / (ms * 1e-3) / 1e9
+    res = max(i.true_rel_residual for i in infos)
+    iters = statistics.median(i.inner_iters for i in infos)
+    outer = statistics.median(i.outer_iters for i in infos)
+
+    # ---- one event-profiled step
+    api.bridge_stats_reset(h)
+    api.bridge_profile(h, True)
+    solve_dev(solver)
+    torch.cuda.synchronize()
+    api.bridge_profile(h, False)
+    pst = api.bridge_stats(h)
+    step_ms_prof = sum(v["ms"] for v in pst.values())
+    dom = max(pst, key=lambda k: pst[k]["ms"])
+    d = pst[dom]
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    roofline = {
+        "bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+        "frac": achieved / peak, "traffic": traffic_for(dom, args.workload),
+        "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]), "launches": d["launches"],
+        "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
+        "share_of_step": d["ms"] / step_ms_prof if step_ms_prof else None,
+    }
+    shares = {k: round(v["ms"] / step_ms_prof, 4) for k, v in pst.items() if v["ms"] > 0}
+    per_kernel = {k: {"launches": v["launches"], "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
+                      "tflops": v["flops"] / (v["ms"] * 1e-3) / 1e12}
+                  for k, v in pst.items() if v["ms"] > 0}
+
+    # ---- D_eo alone: the hop kernel's event-timed launches inside bridge_mult_Deo_dev
+    odd = torch.zeros((nrhs, w.volume // 2, 3), dtype=torch.complex128, device=b_dev.device)
+    odd.real.normal_()
+    out = torch.empty_like(odd)
+    for prec in ("f32", "f32"):
+        _abi.check(_abi.load().bridge_mult_Deo_dev(h, byref(op), api._prec(prec), 0, c_void_p(odd.data_ptr()),
+                                                   c_void_p(out.data_ptr()), nrhs), "bridge_mult_Deo_dev")
+    api.bridge_sync(h)
+    api.bridge_stats_reset(h)
+    api.bridge_profile(h, True)
+    reps = 20
+    for _ in range(reps):
+        _abi.check(_abi.load().bridge_mult_Deo_dev(h, byref(op), api._prec("f32"), 0, c_void_p(odd.data_ptr()),
+                                                   c_void_p(out.data_ptr()), nrhs), "bridge_mult_Deo_dev")
+    api.bridge_sync(h)
+    api.bridge_profile(h, False)
+    hop = api.bridge_stats(h)["stag_hop"]
+    deo = {"kernel": "stag_hop", "prec": "f32", "gbs": hop["bytes"] / (hop["ms"] * 1e-3) / 1e9,
+           "frac": hop["bytes"] / (hop["ms"] * 1e-3) / 1e9 / peak, "us_per_launch": 1e3 * hop["ms"] / reps,
+           "bytes_per_launch": hop["bytes"] / reps, "gflops": hop["flops"] / (hop["ms"] * 1e-3) / 1e9}
+    del odd, out
+
+    solve = {"mixed_ms": ms / args.steps, "mixed_cg_iters": iters, "mixed_outer": outer,
+             "mixed_true_rel_residual": res, "inner_prec": w.inner}
+    if not args.no_fp64:
+        s64 = api.make_solver(tol=w.tol, mixed=0, max_iter=100000)
+        t0 = time.perf_counter()
+        i64 = solve_dev(s64)
+        t64 = time.perf_counter() - t0
+        solve.update({"fp64_ms": t64 * 1e3, "fp64_cg_iters": i64.inner_iters,
+                      "fp64_true_rel_residual": i64.true_rel_residual, "speedup": t64 * 1e3 / (ms / args.steps)})
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, h, op, solver, b_dev, b_host, nrhs, total_bytes, world)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        n = args.oracle_sites * 4
+        v, secs, cores = staggered_oracle_sample(w, U, b_host[0], n, seed=0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"FP64 numpy oracle: staggered D at {n} random sites of the {args.workload} lattice "
+                         f"({secs:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {
+                "workload": args.workload, "lattice": "x".join(map(str, w.dims)),
+                "operator": f"staggered, m={w.mass}, bc={list(w.bc)}", "links": f"exp({w.eps} i A), seed {w.seed}",
+                "source": "gaussian", "nrhs": nrhs,
+                "solver": "even-odd CG (m^2 - D_eo D_oe), f32 inner, f64 defect correction", "tol": w.tol,
+                "l2": "inputs larger than L2 (FP32 links 3.2 GB)",
+                "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            },
+            "roofline": roofline, "kernel_shares": shares, "per_kernel": per_kernel, "deo": deo, "solve": solve,
+            "e2e": e2e, "gpu_launches": launches, "inner_iters": iters, "true_rel_residual": res,
+            "clocks": clk.summary(), "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    L.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_serving(args):
     """The request stream alone: lattices {8^4, 16^4, 24^3x48, 32^3x64},
     kappa in [0.11, 0.13], 1-12 right-hand sides, Wilson or clover."""
@@ -887,6 +1061,8 @@ def main():
         run_serving(args)
     elif args.workload.startswith("mobius"):
         run_mobius(args)
+    elif args.workload.startswith("staggered"):
+        run_staggered(args)
     else:
         run_ours(args)
 

@@ -550,7 +550,8 @@ int dwf_solve(bridge_lattice_s* L, const bridge_op& op, const bridge_solver& prm
   std::vector<bridge_info> info(nrhs);
   for (auto& i : info) std::memset(&i, 0, sizeof(i));
   std::vector<int> done(nrhs, 0), failed(nrhs, 0);
-  std::vector<double> r2(nrhs, 0.0);
+  std::vector<double> r2(nrhs, 0.0), r2_prev(nrhs, 0.0), tau(nrhs, inner_tol);
+  std::vector<int> passes(nrhs, 0);
   std::vector<int> hmask(nq);
   long total_iters = 0;
   // right-hand sides with b = 0 have x = 0
@@ -668,9 +669,13 @@ int dwf_solve(bridge_lattice_s* L, const bridge_op& op, const bridge_solver& prm
     // CG scalars: tolerance and the iteration budget left
     {
       std::vector<CGScalars> hs(nrhs);
-      for (auto& g : hs) {
+      for (int r = 0; r < nrhs; ++r) {
+        CGScalars& g = hs[r];
         std::memset(&g, 0, sizeof(g));
-        g.tol2 = inner_tol * inner_tol;
+        tau[r] = next_inner_tol(inner_tol, prm.tol, b2[r], r2[r], r2_prev[r], tau[r], passes[r] == 0);
+        r2_prev[r] = r2[r];
+        passes[r] += 1;
+        g.tol2 = tau[r] * tau[r];
         g.max_iter = (int)std::max<long>(1, max_iter - total_iters);
       }
       BR_CUDA(cudaMemcpyAsync(sc.ptr, hs.data(), sizeof(CGScalars) * nrhs, cudaMemcpyHostToDevice, st));

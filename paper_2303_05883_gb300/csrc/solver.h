@@ -5,6 +5,7 @@
 #pragma once
 
 #include <chrono>
+#include <cmath>
 #include <vector>
 
 #include "host.h"
@@ -19,6 +20,23 @@ struct PinnedBuf {
   PinnedBuf(const PinnedBuf&) = delete;
   PinnedBuf& operator=(const PinnedBuf&) = delete;
 };
+
+// Inner tolerance of the next defect-correction pass of a CG solve on the
+// normal equations.  The first pass asks for `floor`; later passes ask only
+// for the reduction still needed, tol |b| / |r|, corrected by the ratio
+// `amp` between the reduction the true residual showed and the one the
+// previous pass asked of the CG residual (the normal-equation residual
+// under-reports the true one by up to the conditioning of the operator).
+inline double next_inner_tol(double floor, double tol, double b2, double r2, double r2_prev, double tau_prev,
+                             bool first) {
+  if (first || !(r2 > 0.0) || !(r2_prev > 0.0) || !(tau_prev > 0.0)) return floor;
+  double amp = std::sqrt(r2 / r2_prev) / tau_prev;
+  amp = amp < 1.0 ? 1.0 : amp > 1e6 ? 1e6 : amp;
+  const double want = tol * std::sqrt(b2 / r2);
+  double tau = 0.5 * want / amp;
+  if (tau > 0.1) tau = 0.1;
+  return tau > floor ? tau : floor;
+}
 
 // Device bytes a solve of nrhs right-hand sides will hold (used for admission).
 size_t solve_footprint(const bridge_lattice_s* L, const bridge_solver& prm, int nrhs);
