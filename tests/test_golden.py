@@ -20,7 +20,8 @@ def load(name):
     return a[:, 0] + 1j * a[:, 1]
 
 
-@pytest.mark.parametrize("name", ["wilson_D", "clover_D", "schur_Dhat", "solution"])
+@pytest.mark.parametrize("name", ["wilson_D", "clover_D", "schur_Dhat", "solution", "mobius_D", "mobius_Dhat_dag",
+                                  "staggered_D", "staggered_Dhat"])
 def test_oracle_matches_golden(name):
     got = np.asarray(make_golden.cases()[name]).reshape(-1)
     want = load(name)
