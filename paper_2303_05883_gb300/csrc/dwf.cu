@@ -20,6 +20,7 @@
 //   6 hop   v = q + B^T g5 (H_eo/2) t; x += alpha p; r -= alpha v; |r|^2 -> beta
 // with the scalars on the device and a host poll every check_every iterations.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -154,6 +155,37 @@ std::shared_ptr<DwfSet> dwf_set(bridge_lattice_s* L, const bridge_op& op) {
       std::copy(mats[m].begin(), mats[m].end(), all.begin() + ((size_t)m * 2 + chi) * n * n);
   }
   auto set = std::make_shared<DwfSet>();
+  // the factored forms: A = a0 + a1 S, B = b + c S per chirality; S runs
+  // along dir = -1 on P_+ and +1 on P_-, its transpose the other way
+  {
+    const double a0 = op.b5 * alpha + 1.0, a1 = op.c5 * alpha - 1.0;
+    auto put = [&](int id, int chi, std::initializer_list<std::array<double, 4>> fs, double sign) {
+      SProg& p = set->prog[id];
+      int f = 0;
+      for (const auto& x : fs) {
+        p.kind[chi][f] = (int)x[0];
+        p.d[chi][f] = x[1];
+        p.e[chi][f] = x[2];
+        p.dir[chi][f] = (int)x[3];
+        ++f;
+      }
+      p.nf[chi] = f;
+      p.sign[chi] = sign;
+    };
+    for (int chi = 0; chi < 2; ++chi) {
+      const double dir = chi == 0 ? -1.0 : 1.0, g5 = chi == 0 ? 1.0 : -1.0;
+      put(DM_B, chi, {{SF_MUL, op.b5, op.c5, dir}}, 1.0);
+      put(DM_AINV, chi, {{SF_SOLVE, a0, a1, dir}}, 1.0);
+      put(DM_BAINV, chi, {{SF_SOLVE, a0, a1, dir}, {SF_MUL, op.b5, op.c5, dir}}, 1.0);
+      put(DM_G5AINVT, chi, {{SF_SOLVE, a0, a1, -dir}}, g5);
+      put(DM_AINVTBT, chi, {{SF_MUL, op.b5, op.c5, -dir}, {SF_SOLVE, a0, a1, -dir}}, 1.0);
+      put(DM_BTG5, chi, {{SF_MUL, op.b5, op.c5, -dir}}, g5);
+      put(DM_A, chi, {{SF_MUL, a0, a1, dir}}, 1.0);
+      put(DM_MA, chi, {{SF_MUL, a0, a1, dir}}, -1.0);
+    }
+    const char* dense = std::getenv("BRIDGE_DWF_DENSE");
+    set->fact = a0 != 0.0 && std::fabs(a1) <= std::fabs(a0) && !(dense && dense[0] == '1');
+  }
   set->Ls = n;
   set->M5 = op.M5;
   set->b = op.b5;
@@ -255,6 +287,10 @@ void run_dwf_hop(bridge_lattice_s* L, const DwfSet& set, const bridge_op& op, co
   a.gauge = gauge_ptr(L, c.prec);
   a.m1 = c.m1 >= 0 ? set.mat(c.prec, c.m1) : nullptr;
   a.m2 = c.m2 >= 0 ? set.mat(c.prec, c.m2) : nullptr;
+  a.fact = set.fact ? 1 : 0;
+  a.mf = set.mf;
+  if (c.m1 >= 0) a.p1 = set.prog[c.m1];
+  if (c.m2 >= 0) a.p2 = set.prog[c.m2];
   a.red = c.red;
   if (c.epi != DE_NONE && a.red.partials == nullptr) {
     ensure_red_scratch(L, (long)a.nsb * c.nrhs, c.nrhs);
@@ -268,9 +304,10 @@ void run_dwf_hop(bridge_lattice_s* L, const DwfSet& set, const bridge_op& op, co
   const double S = (double)site_bytes(c.prec);
   double per = 2 * S;
   double fl = 1320 + 24;
-  if (c.m1 >= 0) fl += 48.0 * c.Ls;
+  const double mixfl = set.fact ? 192.0 : 48.0 * c.Ls;  // per fifth-dimension matrix
+  if (c.m1 >= 0) fl += mixfl;
   if (m2mode == DM2_PLAIN) per += S, fl += 48;
-  if (m2mode == DM2_DENSE) per += S, fl += 48.0 * c.Ls;
+  if (m2mode == DM2_DENSE) per += S, fl += mixfl;
   if (c.aux) per += S, fl += 48;
   if (c.epi == DE_NORM) fl += 48;
   if (c.epi == DE_CGUPD) per += 4 * S, fl += 144;  // x, r read and written, p read; out not stored
@@ -310,11 +347,14 @@ void run_dwf_mix(bridge_lattice_s* L, const DwfSet& set, const DwfMix& c, cudaSt
   a.p = c.p;
   a.r = c.r;
   a.m = set.mat(c.prec, c.m);
+  a.fact = set.fact ? 1 : 0;
+  a.mf = set.mf;
+  a.pm = set.prog[c.m];
   a.red = c.red;
   const double S = (double)site_bytes(c.prec);
   const double sites5 = (double)L->vh * c.Ls * c.nrhs;
   const double bytes = sites5 * (c.mode == DX_CGP ? 4 : 2) * S;
-  const double fl = sites5 * (48.0 * c.Ls + (c.mode == DX_CGP ? 48 : 0));
+  const double fl = sites5 * ((set.fact ? 192.0 : 48.0 * c.Ls) + (c.mode == DX_CGP ? 48 : 0));
   note_launch(L, K_DWF_MIX, bytes, fl, st, true);
   BR_CHECK(launch_dwf_mix(c.prec, c.mode, a, st, sh.variant), BRIDGE_EINVAL, "domain-wall mix precision");
   note_launch(L, K_DWF_MIX, bytes, fl, st, false);

@@ -39,6 +39,90 @@ enum DwfM2 { DM2_NONE = 0, DM2_PLAIN = 1, DM2_DENSE = 2 };
 enum DwfEpi { DE_NONE = 0, DE_NORM = 1, DE_CGUPD = 2 };
 enum DwfMixMode { DX_PLAIN = 0, DX_CGP = 1 };
 
+// A fifth-dimension matrix as a product of at most two cyclic bidiagonal
+// factors per chirality, applied right to left, then a sign:
+//   MUL   y_s = d x_s + e x_{s+dir}          (x_{Ls} -> -m_f x_0, x_{-1} -> -m_f x_{Ls-1})
+//   SOLVE d y_s + e y_{s+dir} = x_s          (the same cyclic system, solved)
+// A = d + e S and B = b + c S are of this form with dir = -1 on the P_+
+// components and +1 on the P_- ones (S the s-part of P); transposes flip
+// dir.  SOLVE runs a first-order recurrence in the direction that damps
+// (|e/d| <= 1, checked on the host; otherwise the dense matrix is used).
+enum SFacKind { SF_MUL = 0, SF_SOLVE = 1 };
+struct SProg {
+  int nf[2];  // factors per chirality (0 = identity)
+  int kind[2][2], dir[2][2];
+  double d[2][2], e[2][2];
+  double sign[2];
+};
+
+// In-place factors on one column x_0 .. x_{Ls-1} of a site's staged values
+// (elements `stride` apart in shared memory).
+template <class R>
+BR_D void col_mul(cx<R>* col, int stride, int Ls, R d, R e, int dir, R mf) {
+  if (dir < 0) {
+    const cx<R> last = col[(long)(Ls - 1) * stride];
+    for (int s = Ls - 1; s >= 1; --s) col[(long)s * stride] = d * col[(long)s * stride] + e * col[(long)(s - 1) * stride];
+    col[0] = d * col[0] + (-mf * e) * last;
+  } else {
+    const cx<R> first = col[0];
+    for (int s = 0; s < Ls - 1; ++s) col[(long)s * stride] = d * col[(long)s * stride] + e * col[(long)(s + 1) * stride];
+    col[(long)(Ls - 1) * stride] = d * col[(long)(Ls - 1) * stride] + (-mf * e) * first;
+  }
+}
+
+template <class R>
+BR_D void col_solve(cx<R>* col, int stride, int Ls, R d, R e, int dir, R mf) {
+  // With r = -e/d: the end value follows from the wrap equation in closed
+  // form, the rest from y = x/d + r y(previous) along dir.
+  const R r = -e / d, inv_d = R(1) / d;
+  cx<R> acc = czero<R>();
+  R w = R(1);
+  if (dir < 0) {
+    for (int t = Ls - 1; t >= 1; --t) {
+      acc = acc + w * col[(long)t * stride];
+      w *= r;
+    }
+    cx<R> y = (R(1) / (d - e * mf * w)) * (col[0] + (e * mf * inv_d) * acc);
+    col[0] = y;
+    for (int s = 1; s < Ls; ++s) {
+      y = inv_d * col[(long)s * stride] + r * y;
+      col[(long)s * stride] = y;
+    }
+  } else {
+    for (int t = 0; t <= Ls - 2; ++t) {
+      acc = acc + w * col[(long)t * stride];
+      w *= r;
+    }
+    cx<R> y = (R(1) / (d - e * mf * w)) * (col[(long)(Ls - 1) * stride] + (e * mf * inv_d) * acc);
+    col[(long)(Ls - 1) * stride] = y;
+    for (int s = Ls - 2; s >= 0; --s) {
+      y = inv_d * col[(long)s * stride] + r * y;
+      col[(long)s * stride] = y;
+    }
+  }
+}
+
+// Apply a program to every (site, component) column of sh[Ls][12][ns];
+// must be reached by every thread of the block (it ends with a barrier).
+template <class R>
+BR_D void prog_columns(const SProg& pg, cx<R>* sh, int Ls, int ns, R mf) {
+  for (int cidx = threadIdx.x; cidx < 12 * ns; cidx += blockDim.x) {
+    const int sl = cidx % ns, k = cidx / ns, chi = k < 6 ? 0 : 1;
+    cx<R>* col = sh + (long)k * ns + sl;
+    const int stride = 12 * ns;
+    for (int f = 0; f < pg.nf[chi]; ++f) {
+      if (pg.kind[chi][f] == SF_MUL)
+        col_mul<R>(col, stride, Ls, (R)pg.d[chi][f], (R)pg.e[chi][f], pg.dir[chi][f], mf);
+      else
+        col_solve<R>(col, stride, Ls, (R)pg.d[chi][f], (R)pg.e[chi][f], pg.dir[chi][f], mf);
+    }
+    const R sg = (R)pg.sign[chi];
+    if (sg != R(1))
+      for (int t = 0; t < Ls; ++t) col[(long)t * stride] = sg * col[(long)t * stride];
+  }
+  __syncthreads();
+}
+
 struct DwfArgs {
   Geom g;
   int out_parity;
@@ -62,6 +146,9 @@ struct DwfArgs {
   const char* gauge;  // [parity][mu] link blocks
   const void* m1;     // [2][Ls][Ls] in the compute precision (chirality +, then -)
   const void* m2;
+  int fact;           // 1: apply m1 / m2 by their bidiagonal factors p1 / p2 (no dense matrices staged)
+  double mf;
+  SProg p1, p2;
   RedArgs red;
 };
 
@@ -77,22 +164,25 @@ struct DwfMixArgs {
   RedArgs red;      // DX_CGP: beta and done flags from red.cg
   double s0;        // DX_PLAIN: out = s0 * in + M in when s0 != 0
   float s0f;
+  int fact;         // 1: apply m by its bidiagonal factors pm
+  double mf;
+  SProg pm;
 };
 
 BR_HD int dwf_threads(int ns, int Ls) { return (ns * Ls + 31) / 32 * 32; }
 
 // Dynamic shared memory of one block: the s-matrices and ns * Ls spinors
 // per staged operand.
-BR_HD long dwf_hop_smem(int prec, int Ls, int ns, bool m1, bool m2dense) {
+BR_HD long dwf_hop_smem(int prec, int Ls, int ns, bool m1, bool m2dense, bool fact) {
   const long R = prec == P_F64 ? 8 : 4;
-  const long mats = (m1 ? 1 : 0) + (m2dense ? 1 : 0);
+  const long mats = fact ? 0 : (m1 ? 1 : 0) + (m2dense ? 1 : 0);
   const long vecs = (m1 ? 1 : 0) + (m2dense ? 1 : 0);
   const long links = 8L * 9 * ns * 2 * R + 8L * ns * 4;  // staged links and neighbour words
   return links + mats * 2 * Ls * Ls * R + vecs * (long)Ls * 12 * ns * 2 * R;
 }
-BR_HD long dwf_mix_smem(int prec, int Ls, int ns) {
+BR_HD long dwf_mix_smem(int prec, int Ls, int ns, bool fact) {
   const long R = prec == P_F64 ? 8 : 4;
-  return 2L * Ls * Ls * R + (long)Ls * 12 * ns * 2 * R;
+  return (fact ? 0 : 2L * Ls * Ls * R) + (long)Ls * 12 * ns * 2 * R;
 }
 
 // Row s of the chirality-blocked s-matrix applied to the Ls staged spinors
@@ -198,9 +288,10 @@ __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
   const int nm = 2 * Ls * Ls;
   cx<R>* shl = reinterpret_cast<cx<R>*>(dsm);                 // [8][9][ns] links
   uint32_t* shn = reinterpret_cast<uint32_t*>(shl + 72L * ns);  // [8][ns] neighbours
+  const bool fact = a.fact != 0;
   R* mat1 = reinterpret_cast<R*>(shn + 8L * ns);
-  R* mat2 = mat1 + (M1 ? nm : 0);
-  cx<R>* shh = reinterpret_cast<cx<R>*>(mat2 + (M2 == DM2_DENSE ? nm : 0));
+  R* mat2 = mat1 + ((M1 && !fact) ? nm : 0);
+  cx<R>* shh = reinterpret_cast<cx<R>*>(mat2 + ((M2 == DM2_DENSE && !fact) ? nm : 0));
   cx<R>* shs = shh + (M1 ? (long)Ls * 12 * ns : 0);
 
   const int rhs = blockIdx.x % a.nrhs;
@@ -213,9 +304,9 @@ __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
   const bool valid = live && ih < (uint32_t)vh && !skip;
   const long q = (long)rhs * Ls + s;
 
-  if (M1)
+  if (M1 && !fact)
     for (int i = threadIdx.x; i < nm; i += blockDim.x) mat1[i] = reinterpret_cast<const R*>(a.m1)[i];
-  if (M2 == DM2_DENSE)
+  if (M2 == DM2_DENSE && !fact)
     for (int i = threadIdx.x; i < nm; i += blockDim.x) mat2[i] = reinterpret_cast<const R*>(a.m2)[i];
   if (!skip) stage_links<P>(a, sb, shl, shn);
   __syncthreads();
@@ -251,11 +342,18 @@ __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
     stage_row(shs, ns, s, sl, v);
   }
   if (M1 || M2 == DM2_DENSE) __syncthreads();
+  if (fact) {
+    if (M1) prog_columns<R>(a.p1, shh, Ls, ns, (R)a.mf);
+    if (M2 == DM2_DENSE) prog_columns<R>(a.p2, shs, Ls, ns, (R)a.mf);
+  }
 
   R nrm = R(0);
   if (valid) {
     cx<R> v[12];
-    if (M1) {
+    if (M1 && fact) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = shh[((long)s * 12 + k) * ns + sl];
+    } else if (M1) {
       smix_row(mat1, shh, Ls, ns, s, sl, v);
     } else {
 #pragma unroll
@@ -269,7 +367,12 @@ __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
       for (int k = 0; k < 12; ++k) v[k] = v[k] + s2 * w[k];
     } else if (M2 == DM2_DENSE) {
       cx<R> w[12];
-      smix_row(mat2, shs, Ls, ns, s, sl, w);
+      if (fact) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) w[k] = shs[((long)s * 12 + k) * ns + sl];
+      } else {
+        smix_row(mat2, shs, Ls, ns, s, sl, w);
+      }
 #pragma unroll
       for (int k = 0; k < 12; ++k) v[k] = v[k] + w[k];
     }
@@ -315,8 +418,9 @@ __global__ void __launch_bounds__(256, MINB) dwf_mix_kernel(const DwfMixArgs a) 
   extern __shared__ __align__(16) unsigned char dsm[];
   const int Ls = a.Ls, ns = a.ns;
   const int nm = 2 * Ls * Ls;
+  const bool fact = a.fact != 0;
   R* mat = reinterpret_cast<R*>(dsm);
-  cx<R>* sh = reinterpret_cast<cx<R>*>(mat + nm);
+  cx<R>* sh = reinterpret_cast<cx<R>*>(mat + (fact ? 0 : nm));
   const int rhs = blockIdx.x % a.nrhs;
   const int sb = blockIdx.x / a.nrhs;
   const int sl = threadIdx.x % ns, s = threadIdx.x / ns;
@@ -325,7 +429,8 @@ __global__ void __launch_bounds__(256, MINB) dwf_mix_kernel(const DwfMixArgs a) 
   const bool skip = MODE == DX_CGP && a.red.cg != nullptr && a.red.cg[rhs].done != RUNNING;
   const bool valid = live && ih < a.vh && !skip;
   const long q = (long)rhs * Ls + s;
-  for (int i = threadIdx.x; i < nm; i += blockDim.x) mat[i] = reinterpret_cast<const R*>(a.m)[i];
+  if (!fact)
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) mat[i] = reinterpret_cast<const R*>(a.m)[i];
   cx<R> v[12];
   if (valid) {
     if (MODE == DX_CGP) {
@@ -345,9 +450,15 @@ __global__ void __launch_bounds__(256, MINB) dwf_mix_kernel(const DwfMixArgs a) 
   }
   if (live) stage_row(sh, ns, s, sl, v);
   __syncthreads();
+  if (fact) prog_columns<R>(a.pm, sh, Ls, ns, (R)a.mf);
   if (valid) {
     cx<R> w[12];
-    smix_row(mat, sh, Ls, ns, s, sl, w);
+    if (fact) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) w[k] = sh[((long)s * 12 + k) * ns + sl];
+    } else {
+      smix_row(mat, sh, Ls, ns, s, sl, w);
+    }
     if (MODE == DX_PLAIN && a.s0 != 0.0) {
       const R s0 = pick<R>(a.s0, a.s0f);
 #pragma unroll

@@ -22,7 +22,7 @@ template <int P, bool M1, int M2, int EPI, int MINB>
 static bool go_hop1(const DwfArgs& a, cudaStream_t st) {
   static long limit[64] = {};
   auto k = dwf_hop_kernel<P, M1, M2, EPI, MINB>;
-  const long smem = dwf_hop_smem(P, a.Ls, a.ns, M1, M2 == DM2_DENSE);
+  const long smem = dwf_hop_smem(P, a.Ls, a.ns, M1, M2 == DM2_DENSE, a.fact != 0);
   allow_smem(k, smem, limit);
   k<<<a.nsb * a.nrhs, dwf_threads(a.ns, a.Ls), smem, st>>>(a);
   return true;
@@ -68,7 +68,7 @@ template <int P, int MODE, int MINB>
 static bool go_mix1(const DwfMixArgs& a, cudaStream_t st) {
   static long limit[64] = {};
   auto k = dwf_mix_kernel<P, MODE, MINB>;
-  const long smem = dwf_mix_smem(P, a.Ls, a.ns);
+  const long smem = dwf_mix_smem(P, a.Ls, a.ns, a.fact != 0);
   allow_smem(k, smem, limit);
   k<<<a.nsb * a.nrhs, dwf_threads(a.ns, a.Ls), smem, st>>>(a);
   return true;

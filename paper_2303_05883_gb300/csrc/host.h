@@ -152,6 +152,8 @@ struct DwfSet {
   int Ls = 0;
   double M5 = 0, b = 0, c = 0, mf = 0;
   std::unique_ptr<DevBuf> mats[2];  // [0] FP64, [1] FP32
+  SProg prog[DWF_NMAT];             // the same matrices as bidiagonal factors
+  bool fact = false;                // the factored form is stable for these parameters (and not disabled)
   const void* mat(int prec, int id) const {
     const size_t per = (size_t)2 * Ls * Ls * (prec == P_F64 ? 8 : 4);
     return mats[prec == P_F64 ? 0 : 1]->ptr + id * per;

@@ -190,3 +190,26 @@ def test_fullsize_24x24x24x48x16(api):
     r = b[:, s] - orc.full(x, sites=s)
     assert np.linalg.norm(r) / np.linalg.norm(b[:, s]) < 5 * w.tol
     L.close()
+
+
+@pytest.mark.parametrize("how", ["env_dense", "unstable_recurrence"])
+def test_dense_fifth_dimension_path(api, monkeypatch, how):
+    """The dense s-matrix epilogue: forced by BRIDGE_DWF_DENSE, and chosen when
+    |c(4-M5) - 1| > |b(4-M5) + 1| (the factored recurrence would grow)."""
+    dims, Ls = (4, 2, 4, 4), 6
+    if how == "env_dense":
+        monkeypatch.setenv("BRIDGE_DWF_DENSE", "1")
+        kw = {}
+    else:
+        kw = dict(b5=0.1, c5=1.5)
+    lat, U, orc, op, L = _setup(api, dims, Ls, 0.4, 61, **kw)
+    psi = synth.gaussian_spinor(dims, 62, nrhs=Ls)
+    assert rel(L.D(op, psi, "f64"), orc.full(psi)) < 1e-13
+    xe = np.ascontiguousarray(psi[:, lat.even])
+    assert rel(L.Dhat(op, xe, "f32"), orc.schur(xe)) < 2e-6
+    assert rel(L.Dhat_dag(op, xe, "f64"), orc.schur_dag(xe)) < 1e-13
+    if how == "env_dense":  # (the other parameter set makes D_ee nearly singular: operators only)
+        x, info = L.solve(op, psi, api.make_solver(tol=1e-10, inner_prec="f32"))
+        assert info[0]["status"] == 0
+        assert np.linalg.norm(psi - orc.full(x)) / np.linalg.norm(psi) < 1.5e-10
+    L.close()
