@@ -155,7 +155,8 @@ def traffic_for(kernel: str, workload: str):
 
 def kernel_source_hash(kernel: str = "") -> str:
     d = hashlib.sha256()
-    files = ["common.cuh", "dslash.cuh", "reduce.cuh"] + (["dwf.cuh"] if kernel.startswith("dwf") else [])
+    files = ["common.cuh", "dslash.cuh", "reduce.cuh"] + (["dwf.cuh"] if kernel.startswith("dwf") else []) + (
+        ["stag.cuh"] if kernel.startswith("stag") else [])
     for f in files:
         d.update(open(os.path.join(ROOT, "paper_2303_05883_gb300", "csrc", f), "rb").read())
     return d.hexdigest()[:16]
@@ -715,7 +716,7 @@ def run_mobius(args):
     U = w.gauge()
     b_host = w.sources()  # (nrhs, Ls, V, 4, 3)
     b_dev = torch.from_numpy(b_host).to(f"cuda:{local}")
-    x_dev = torch.zeros_like(b_dev)
+    x_dev = None if args.deo_only else torch.zeros_like(b_dev)
     op = api.make_mobius(w.Ls, w.M5, w.b5, w.c5, w.mf, bc=w.bc)
     L = api.Lattice(w.dims)
     L.upload(U)
@@ -854,6 +855,43 @@ def staggered_oracle_sample(w, U, b, nsites, seed):
     return nsites * per_site / secs / 1e9, secs, cores
 
 
+def staggered_operator_leg(api, h, op, w, b_dev):
+    """One Schur operator application (its two hop passes come first in a
+    profiler capture), then D_eo alone: the hop kernel's event-timed
+    launches inside bridge_mult_Deo_dev."""
+    from ctypes import byref, c_void_p
+
+    import torch
+
+    from paper_2303_05883_gb300 import _abi
+
+    peak, _ = peaks()
+    nrhs = w.nrhs
+    lib = _abi.load()
+    half = torch.zeros((nrhs, w.volume // 2, 3), dtype=torch.complex128, device=b_dev.device)
+    half.real.normal_()
+    out = torch.empty_like(half)
+    f32 = _abi.BRIDGE_F32
+    _abi.check(lib.bridge_mult_Dhat_dev(h, byref(op), f32, c_void_p(half.data_ptr()), c_void_p(out.data_ptr()), nrhs),
+               "bridge_mult_Dhat_dev")
+    for _ in range(2):
+        _abi.check(lib.bridge_mult_Deo_dev(h, byref(op), f32, 0, c_void_p(half.data_ptr()), c_void_p(out.data_ptr()),
+                                           nrhs), "bridge_mult_Deo_dev")
+    api.bridge_sync(h)
+    api.bridge_stats_reset(h)
+    api.bridge_profile(h, True)
+    reps = 20
+    for _ in range(reps):
+        _abi.check(lib.bridge_mult_Deo_dev(h, byref(op), f32, 0, c_void_p(half.data_ptr()), c_void_p(out.data_ptr()),
+                                           nrhs), "bridge_mult_Deo_dev")
+    api.bridge_sync(h)
+    api.bridge_profile(h, False)
+    hop = api.bridge_stats(h)["stag_hop"]
+    return {"kernel": "stag_hop", "prec": "f32", "gbs": hop["bytes"] / (hop["ms"] * 1e-3) / 1e9,
+            "frac": hop["bytes"] / (hop["ms"] * 1e-3) / 1e9 / peak, "us_per_launch": 1e3 * hop["ms"] / reps,
+            "bytes_per_launch": hop["bytes"] / reps, "gflops": hop["flops"] / (hop["ms"] * 1e-3) / 1e9}
+
+
 def run_staggered(args):
     """Staggered: mixed CG solve steps, D_eo alone, FP64 CG, e2e, oracle."""
     import torch
@@ -888,6 +926,10 @@ def run_staggered(args):
     nrhs = w.nrhs
     solver = api.make_solver(tol=w.tol, inner_prec=w.inner, mixed=1)
     peak, peak_kind = peaks()
+    if args.deo_only:
+        print(json.dumps({"workload": args.workload, "deo": staggered_operator_leg(api, h, op, w, b_dev)}), flush=True)
+        L.close()
+        return
 
     def solve_dev(prm):
         x_dev.zero_()
@@ -947,27 +989,7 @@ def run_staggered(args):
                       "tflops": v["flops"] / (v["ms"] * 1e-3) / 1e12}
                   for k, v in pst.items() if v["ms"] > 0}
 
-    # ---- D_eo alone: the hop kernel's event-timed launches inside bridge_mult_Deo_dev
-    odd = torch.zeros((nrhs, w.volume // 2, 3), dtype=torch.complex128, device=b_dev.device)
-    odd.real.normal_()
-    out = torch.empty_like(odd)
-    for prec in ("f32", "f32"):
-        _abi.check(_abi.load().bridge_mult_Deo_dev(h, byref(op), api._prec(prec), 0, c_void_p(odd.data_ptr()),
-                                                   c_void_p(out.data_ptr()), nrhs), "bridge_mult_Deo_dev")
-    api.bridge_sync(h)
-    api.bridge_stats_reset(h)
-    api.bridge_profile(h, True)
-    reps = 20
-    for _ in range(reps):
-        _abi.check(_abi.load().bridge_mult_Deo_dev(h, byref(op), api._prec("f32"), 0, c_void_p(odd.data_ptr()),
-                                                   c_void_p(out.data_ptr()), nrhs), "bridge_mult_Deo_dev")
-    api.bridge_sync(h)
-    api.bridge_profile(h, False)
-    hop = api.bridge_stats(h)["stag_hop"]
-    deo = {"kernel": "stag_hop", "prec": "f32", "gbs": hop["bytes"] / (hop["ms"] * 1e-3) / 1e9,
-           "frac": hop["bytes"] / (hop["ms"] * 1e-3) / 1e9 / peak, "us_per_launch": 1e3 * hop["ms"] / reps,
-           "bytes_per_launch": hop["bytes"] / reps, "gflops": hop["flops"] / (hop["ms"] * 1e-3) / 1e9}
-    del odd, out
+    deo = staggered_operator_leg(api, h, op, w, b_dev)
 
     solve = {"mixed_ms": ms / args.steps, "mixed_cg_iters": iters, "mixed_outer": outer,
              "mixed_true_rel_residual": res, "inner_prec": w.inner}

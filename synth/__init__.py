@@ -313,3 +313,5 @@ class StaggeredWorkload:
 # Staggered on 64^4, m = 0.05, links exp(0.2 i A): CG on the even system,
 # FP32 inner / FP64 outer to 1e-10.
 WORKLOADS["staggered_64x64x64x64"] = StaggeredWorkload("staggered_64x64x64x64", (64, 64, 64, 64), 0.05, 0.2, 6, 1, 1e-10)
+# The same on 32^4 (links above L2, a few GB in all) for profiler captures.
+WORKLOADS["staggered_32x32x32x32"] = StaggeredWorkload("staggered_32x32x32x32", (32, 32, 32, 32), 0.05, 0.2, 6, 1, 1e-10)
