@@ -22,6 +22,9 @@ paper is silent, the docstring states the reading taken):
                   adjoint;
 * ``staggered`` -- the staggered operator (Sec. 2) with its even-odd blocks
                   and the Hermitian positive definite even system solved by CG;
+* ``multigrid`` -- the two-level multigrid of Sec. 3 (aggregation by blocks
+                  and chirality, P^dag D P, SAP with minimal-residual block
+                  solves, the cycle, Flexible BiCGStab);
 * ``solvers``  -- BiCGStab (van der Vorst) as named in Sec. 3, CG and CG on
                   the normal equations (the domain-wall solver of Fig. 7),
                   dense matrices by their matrix elements and dense LU solves.
@@ -40,7 +43,13 @@ polar approximation of the sign function of the Moebius kernel), in the free
 field against the Fourier symbol and on random gauge fields.  The staggered
 operator is pinned by the free-field closed form of D^dagger D on plane
 waves, anti-hermiticity of its hopping term, gauge covariance, and the dense
-matrix filled from its matrix elements (Schur complement, LU solve).
+matrix filled from its matrix elements (Schur complement, LU solve).  The
+multigrid pieces are pinned to dense linear algebra: P^dag P = 1, the coarse
+operator against P^dag M P with the dense matrix-element form M, the block
+operator against M with inter-block entries removed, SAP and the cycle
+against block Gauss-Seidel half-sweeps written with dense block inverses,
+one minimal-residual step against least squares, and the FBiCGStab solve
+against LU.
 """
 
-from . import lattice, gamma, dirac, evenodd, domainwall, staggered, solvers  # noqa: F401
+from . import lattice, gamma, dirac, evenodd, domainwall, staggered, multigrid, solvers  # noqa: F401

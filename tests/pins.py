@@ -10,7 +10,7 @@ from __future__ import annotations
 import numpy as np
 
 import synth
-from oracle import dirac, domainwall, evenodd, gamma, solvers, staggered
+from oracle import dirac, domainwall, evenodd, gamma, multigrid, solvers, staggered
 from oracle.lattice import Lattice
 
 
@@ -485,3 +485,126 @@ def staggered_dense_error(dims=(2, 2, 2, 4), mass=0.1, eps=0.5, seed=107):
     x_lu = np.linalg.solve(M, b.reshape(-1)).reshape(b.shape)
     xe, _ = solvers.cg(op.normal_even, op.prepare(b), tol=1e-14, maxiter=2000)
     return max(err, rel(op.reconstruct(xe, b), x_lu))
+
+
+# --- two-level multigrid -------------------------------------------------------------------
+
+
+def _mg_case(dims=(4, 4, 4, 4), block=(2, 2, 2, 2), nv=3, kappa=0.12, csw=1.0, eps=0.4, seed=111):
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, eps, seed)
+    gen = np.random.default_rng(seed)
+    vs = gen.standard_normal((nv, lat.V, 4, 3)) + 1j * gen.standard_normal((nv, lat.V, 4, 3))
+    return lat, U, multigrid.Multigrid(U, lat, kappa, csw, block, vs)
+
+
+def _dense_P(mg):
+    """P as a dense (12V x 2 Nb Nv) matrix assembled from the aggregate bases."""
+    lat, nb, nv = mg.lat, mg.blocks.nblocks, mg.nv
+    P = np.zeros((12 * lat.V, nb * 2 * nv), dtype=np.complex128)
+    for b in range(nb):
+        s = mg.blocks.sites[b]
+        for chi in range(2):
+            rows = np.array([12 * x + 6 * chi + k for x in s for k in range(6)])
+            P[rows, (b * 2 + chi) * nv : (b * 2 + chi + 1) * nv] = mg.Q[b][chi]
+    return P
+
+
+def mg_transfer_error():
+    """P^dag P = 1; restrict / prolong agree with the dense P; the aggregate
+    bases span the null vectors restricted to each aggregate."""
+    lat, U, mg = _mg_case()
+    P = _dense_P(mg)
+    err = np.abs(P.conj().T @ P - np.eye(P.shape[1])).max()
+    gen = np.random.default_rng(5)
+    c = gen.standard_normal((mg.blocks.nblocks, 2, mg.nv)) + 1j * gen.standard_normal((mg.blocks.nblocks, 2, mg.nv))
+    err = max(err, rel(mg.prolong(c).reshape(-1), P @ c.reshape(-1)))
+    v = gen.standard_normal((lat.V, 4, 3)) + 1j * gen.standard_normal((lat.V, 4, 3))
+    err = max(err, rel(mg.restrict(v).reshape(-1), P.conj().T @ v.reshape(-1)))
+    return float(err)
+
+
+def mg_coarse_error():
+    """D_c from the oracle equals P^dag M P with M the dense matrix-element form of D,
+    and satisfies D_c^dag = G5 D_c G5 (G5 = +1 / -1 on the two chiral aggregates)."""
+    lat, U, mg = _mg_case()
+    P = _dense_P(mg)
+    M = solvers.dense_dirac(U, lat, mg.kappa, mg.csw)
+    Dc = mg.coarse_dense()
+    err = rel(Dc, P.conj().T @ M @ P)
+    g5 = np.tile(np.repeat([1.0, -1.0], mg.nv), mg.blocks.nblocks)
+    err = max(err, rel(Dc.conj().T, g5[:, None] * Dc * g5[None, :]))
+    return err
+
+
+def mg_block_operator_error():
+    """D_B equals the dense matrix with every entry between different blocks removed."""
+    lat, U, mg = _mg_case(dims=(4, 2, 2, 2), block=(2, 1, 1, 1))
+    M = solvers.dense_dirac(U, lat, mg.kappa, mg.csw)
+    same = np.repeat(mg.blocks.of_site, 12)
+    MB = M * (same[:, None] == same[None, :])
+    f = lambda v: multigrid.block_dirac(U, v.reshape(-1, 4, 3), lat, mg.blocks, mg.kappa, mg.csw, T=mg.T).reshape(-1)  # noqa: E731
+    return rel(solvers.dense_matrix(f, 12 * lat.V), MB)
+
+
+def mg_sap_error():
+    """With converged block solves, one SAP cycle is the two block-Gauss-Seidel
+    half-sweeps written with dense block inverses; one MR step is the
+    least-squares step on each block."""
+    lat, U, mg = _mg_case(kappa=0.1)
+    M = solvers.dense_dirac(U, lat, mg.kappa, mg.csw)
+    site_block = np.repeat(mg.blocks.of_site, 12)
+    gen = np.random.default_rng(9)
+    b = gen.standard_normal((lat.V, 4, 3)) + 1j * gen.standard_normal((lat.V, 4, 3))
+    bf = b.reshape(-1)
+    x = np.zeros_like(bf)
+    for colour in (0, 1):
+        r = bf - M @ x
+        for blk in np.nonzero(mg.blocks.colour == colour)[0]:
+            idx = np.nonzero(site_block == blk)[0]
+            x[idx] += np.linalg.solve(M[np.ix_(idx, idx)], r[idx])
+    err = rel(mg.sap(b, 1, 200).reshape(-1), x)
+    # one MR step on each colour-0 block against numpy's least squares
+    e = mg.mr(b, 0, 1).reshape(-1)
+    for blk in np.nonzero(mg.blocks.colour == 0)[0]:
+        idx = np.nonzero(site_block == blk)[0]
+        q = M[np.ix_(idx, idx)] @ bf[idx]
+        a = np.linalg.lstsq(q[:, None], bf[idx], rcond=None)[0][0]
+        err = max(err, rel(e[idx], a * bf[idx]))
+    return err
+
+
+def mg_cycle_error():
+    """The cycle composed from dense pieces: z = P (P^dag M P)^-1 P^dag r, then one
+    SAP cycle with converged block solves on r - M z."""
+    lat, U, mg = _mg_case(kappa=0.1)
+    M = solvers.dense_dirac(U, lat, mg.kappa, mg.csw)
+    P = _dense_P(mg)
+    site_block = np.repeat(mg.blocks.of_site, 12)
+    gen = np.random.default_rng(17)
+    r = gen.standard_normal((lat.V, 4, 3)) + 1j * gen.standard_normal((lat.V, 4, 3))
+    rf = r.reshape(-1)
+    z = P @ np.linalg.solve(P.conj().T @ M @ P, P.conj().T @ rf)
+    b2 = rf - M @ z
+    x = np.zeros_like(rf)
+    for colour in (0, 1):
+        res = b2 - M @ x
+        for blk in np.nonzero(mg.blocks.colour == colour)[0]:
+            idx = np.nonzero(site_block == blk)[0]
+            x[idx] += np.linalg.solve(M[np.ix_(idx, idx)], res[idx])
+    return rel(mg.cycle(r, 1, 200).reshape(-1), z + x)
+
+
+def mg_solve_error():
+    """FBiCGStab preconditioned by the two-level cycle (exact coarse solve)
+    reaches the LU solution; with M = 1 it takes the BiCGStab iterates."""
+    lat, U, mg = _mg_case(nv=4, kappa=0.124)
+    M = solvers.dense_dirac(U, lat, mg.kappa, mg.csw)
+    gen = np.random.default_rng(13)
+    b = gen.standard_normal((lat.V, 4, 3)) + 1j * gen.standard_normal((lat.V, 4, 3))
+    x_lu = np.linalg.solve(M, b.reshape(-1)).reshape(b.shape)
+    x, info = multigrid.fbicgstab(mg.D, lambda r: mg.cycle(r, 2, 4), b, tol=1e-12, maxiter=200)
+    err = rel(x, x_lu)
+    x1, i1 = multigrid.fbicgstab(mg.D, lambda r: r, b, tol=1e-12, maxiter=500)
+    x2, i2 = solvers.bicgstab(mg.D, b, tol=1e-12, maxiter=500)
+    return max(err, rel(x1, x_lu), float(abs(i1["iters"] - i2["iters"]) > 1))

@@ -62,6 +62,21 @@ MUTANTS = [
     ("domainwall", "return _mix(self.B[0].T, self.B[1].T, _g5(h))", "return _mix(self.B[0].T, self.B[1].T, h)",
      pins.mobius_adjoint_error, 1e-10),
     ("solvers", "p = r + (rr_new / rr) * p", "p = r", pins.cg_error, 1e-10),
+    # two-level multigrid
+    ("multigrid", "A[:, i] /= np.linalg.norm(A[:, i])", "A[:, i] /= 1.0", pins.mg_transfer_error, 1e-10),
+    ("multigrid", "out[b, chi] = self.Q[b][chi].conj().T @", "out[b, chi] = self.Q[b][chi].T @", pins.mg_transfer_error, 1e-10),
+    ("multigrid", "keep = (blocks.of_site[j] == blocks.of_site[x]) * np.where(wraps, bc[mu], 1.0)\n        chi = keep[:, None, None] * psi[j]\n        out -= kappa * np.einsum(\"st,ntc->nsc\", _g.I4 + g",
+     "keep = (blocks.of_site[j] != blocks.of_site[x]) * np.where(wraps, bc[mu], 1.0)\n        chi = keep[:, None, None] * psi[j]\n        out -= kappa * np.einsum(\"st,ntc->nsc\", _g.I4 + g",
+     pins.mg_block_operator_error, 1e-10),
+    ("multigrid", "chi @ np.conj(U[mu][j])", "chi @ U[mu][j]", pins.mg_block_operator_error, 1e-10),
+    ("multigrid", "alpha = np.vdot(q[s], rho[s]) / qq", "alpha = np.vdot(rho[s], q[s]) / qq", pins.mg_sap_error, 1e-10),
+    ("multigrid", "for colour in (0, 1):\n                x = x + self.mr(b - self.D(x), colour, mr_steps)",
+     "for colour in (1, 0):\n                x = x + self.mr(b - self.D(x), colour, mr_steps)", pins.mg_sap_error, 1e-10),
+    ("multigrid", "x = x + self.mr(b - self.D(x), colour, mr_steps)", "x = x + self.mr(b, colour, mr_steps)",
+     pins.mg_sap_error, 1e-10),
+    ("multigrid", "return z + self.sap(r - self.D(z), cycles, mr_steps)", "return z + self.sap(r, cycles, mr_steps)",
+     pins.mg_cycle_error, 1e-10),
+    ("multigrid", "x = x + alpha * ph + omega * sh", "x = x + alpha * p + omega * s", pins.mg_solve_error, 1e-10),
     # staggered
     ("staggered", "for nu in range(mu):", "for nu in range(mu + 1):", pins.staggered_free_field_error, 1e-10),
     ("staggered", "out -= 0.5 * e * np.einsum", "out += 0.5 * e * np.einsum", pins.staggered_free_field_error, 1e-10),

@@ -213,3 +213,30 @@ def test_staggered_phases():
     assert np.all(staggered.eta(lat, 0) == 1)
     assert np.all(staggered.eta(lat, 1) == (-1.0) ** c[0])
     assert np.all(staggered.eta(lat, 3) == (-1.0) ** (c[0] + c[1] + c[2]))
+
+
+# --- two-level multigrid (Sec. 3) -------------------------------------------------------
+
+
+def test_mg_transfer_operators():
+    assert pins.mg_transfer_error() < 1e-13
+
+
+def test_mg_coarse_operator_is_galerkin_and_g5_symmetric():
+    assert pins.mg_coarse_error() < 1e-13
+
+
+def test_mg_block_operator():
+    assert pins.mg_block_operator_error() < 1e-14
+
+
+def test_mg_sap_and_minimal_residual_step():
+    assert pins.mg_sap_error() < 1e-12
+
+
+def test_mg_cycle_composition():
+    assert pins.mg_cycle_error() < 1e-12
+
+
+def test_mg_fbicgstab_solve():
+    assert pins.mg_solve_error() < 1e-10
