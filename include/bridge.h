@@ -288,6 +288,64 @@ int bridge_field_export(bridge_field f, double* dst, int on_device);
  * on the lattice stream.  See bridge_apply_op for the subsets required. */
 int bridge_apply(bridge_lattice lat, const bridge_op* op, int which, bridge_field out, bridge_field in);
 
+/* ---- two-level multigrid ------------------------------------------------------- */
+
+/* The multigrid solver of Sec. 3 (a two-level DD-alpha-AMG variant): an outer
+ * Flexible BiCGStab in FP64 on D, preconditioned by an FP32 cycle made of a
+ * coarse-grid correction (BiCGStab on the coarse operator to coarse_tol) and
+ * SAP post-smoothing (sap_cycles cycles; blocks coloured by the parity of
+ * their block coordinates; each block system solved by mr_steps
+ * minimal-residual steps on D restricted to the block).  Aggregates are one
+ * block and one chirality; the prolongation's columns are the null vectors
+ * orthonormalised per aggregate (Gram-Schmidt in the given order); the
+ * coarse operator is P^dag D P (nine couplings per coarse site: the block
+ * and its eight neighbours).  WILSON and CLOVER operators. */
+typedef struct bridge_mg_s* bridge_mg; /* opaque, library-owned */
+
+typedef struct {
+  int block[4];       /* block extents; each divides the lattice with an even quotient; 2 .. 256 sites */
+  int nvec;           /* null vectors, 1 .. 32 */
+  double setup_tol;   /* tolerance of the generated null vectors' solves D v = eta (random eta) */
+  int sap_cycles;     /* SAP post-smoothing cycles per preconditioner application */
+  int mr_steps;       /* minimal-residual steps per block system */
+  double coarse_tol;  /* relative tolerance of the coarse BiCGStab */
+  int coarse_maxiter; /* iteration limit of the coarse BiCGStab */
+} bridge_mg_params;
+
+/* Defaults: blocks 4^4, 16 null vectors, setup_tol 5e-2, 2 SAP cycles,
+ * 4 MR steps, coarse_tol 5e-2, coarse_maxiter 200. */
+void bridge_mg_defaults(bridge_mg_params* p);
+/* Build the multigrid hierarchy for op on the lattice's gauge field.
+ * null_vectors: NULL to generate them (solves of random sources), or nvec
+ * canonical full spinors on the host (nvec*V*24 doubles), used as given.
+ * The handle keeps pointers to the lattice, which must outlive it.
+ * Synchronous.  Errors: EINVAL (blocks, counts, operator kind), ESTATE (no gauge). */
+int bridge_mg_setup(bridge_lattice lat, const bridge_op* op, const bridge_mg_params* p, const double* null_vectors,
+                    bridge_mg* out);
+int bridge_mg_destroy(bridge_mg mg);
+/* Solve D x = b for nrhs right-hand sides (host canonical buffers; x holds
+ * the initial guesses) to s->tol in the true FP64 residual, with at most
+ * s->max_iter outer iterations per right-hand side.  info[nrhs]: status,
+ * outer iterations in inner_iters, restarts, true residual, seconds.
+ * Synchronous. */
+int bridge_mg_solve(bridge_mg mg, const bridge_solver* s, const double* b, double* x, int nrhs, bridge_info* info);
+
+/* Pieces of the cycle, on host canonical buffers, for tests.  Coarse
+ * vectors are [block][chirality][vector] complex ([re, im] doubles), blocks
+ * ordered x fastest. */
+enum bridge_mg_apply_op {
+  BRIDGE_MG_RESTRICT = 0, /* fine in -> coarse out: P^dag in */
+  BRIDGE_MG_PROLONG = 1,  /* coarse in -> fine out: P in */
+  BRIDGE_MG_COARSE = 2,   /* coarse -> coarse: D_c in */
+  BRIDGE_MG_SAP = 3,      /* fine -> fine: sap_cycles SAP cycles on D x = in from x = 0 */
+  BRIDGE_MG_CYCLE = 4     /* fine -> fine: the preconditioner */
+};
+int bridge_mg_apply(bridge_mg mg, int which, const double* in, double* out);
+/* The coarse operator: [block][coupling 9][column][row] complex doubles;
+ * coupling 0 is the block itself, 1 + 2 mu / 2 + 2 mu the blocks at +mu / -mu. */
+int bridge_mg_coarse_matrix(bridge_mg mg, double* out);
+int bridge_mg_info(bridge_mg mg, int* nblocks, int* nvec);
+
 /* ---- serving: continuous batching of solve requests ------------------------- */
 
 /* Limits of the request engine: total device bytes that admitted requests

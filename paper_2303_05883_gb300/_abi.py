@@ -69,6 +69,21 @@ class bridge_info(ctypes.Structure):
     ]
 
 
+class bridge_mg_params(ctypes.Structure):
+    _fields_ = [
+        ("block", c_int * 4),
+        ("nvec", c_int),
+        ("setup_tol", c_double),
+        ("sap_cycles", c_int),
+        ("mr_steps", c_int),
+        ("coarse_tol", c_double),
+        ("coarse_maxiter", c_int),
+    ]
+
+
+BRIDGE_MG_RESTRICT, BRIDGE_MG_PROLONG, BRIDGE_MG_COARSE, BRIDGE_MG_SAP, BRIDGE_MG_CYCLE = 0, 1, 2, 3, 4
+
+
 class bridge_kstat(ctypes.Structure):
     _fields_ = [("name", c_char_p), ("launches", c_long), ("bytes", c_double), ("flops", c_double), ("ms", c_double)]
 
@@ -105,6 +120,13 @@ SIGNATURES = {
     "bridge_apply": (c_int, [_h, POINTER(bridge_op), c_int, _h, _h]),
     "bridge_engine_config": (c_int, [c_size_t, c_int]),
     "bridge_submit": (c_int, [_h, POINTER(bridge_op), POINTER(bridge_solver), _dp, c_int, POINTER(_h)]),
+    "bridge_mg_defaults": (None, [POINTER(bridge_mg_params)]),
+    "bridge_mg_setup": (c_int, [_h, POINTER(bridge_op), POINTER(bridge_mg_params), _dp, POINTER(_h)]),
+    "bridge_mg_destroy": (c_int, [_h]),
+    "bridge_mg_solve": (c_int, [_h, POINTER(bridge_solver), _dp, _dp, c_int, POINTER(bridge_info)]),
+    "bridge_mg_apply": (c_int, [_h, c_int, _dp, _dp]),
+    "bridge_mg_coarse_matrix": (c_int, [_h, _dp]),
+    "bridge_mg_info": (c_int, [_h, POINTER(c_int), POINTER(c_int)]),
     "bridge_poll": (c_int, [_h, _dp, POINTER(bridge_info)]),
     "bridge_wait": (c_int, [_h, c_int, _dp, POINTER(bridge_info)]),
     "bridge_request_release": (c_int, [_h]),

@@ -349,6 +349,75 @@ def bridge_strerror(status: int) -> str:
     return _abi.load().bridge_strerror(int(status)).decode()
 
 
+# --- two-level multigrid ------------------------------------------------------------------
+
+
+def make_mg_params(**kw) -> "_abi.bridge_mg_params":
+    p = _abi.bridge_mg_params()
+    _abi.load().bridge_mg_defaults(byref(p))
+    for k, v in kw.items():
+        if k == "block":
+            v = (c_int * 4)(*[int(b) for b in v])
+        setattr(p, k, v)
+    return p
+
+
+class Multigrid:
+    """Owning wrapper of a multigrid hierarchy (bridge_mg_setup .. bridge_mg_destroy)."""
+
+    def __init__(self, lattice, op, params=None, null_vectors=None):
+        lib = _abi.load()
+        self.lattice, self.op = lattice, op
+        self.params = params or make_mg_params()
+        h = c_void_p()
+        nv = None if null_vectors is None else _host(null_vectors)
+        check(lib.bridge_mg_setup(lattice.handle, byref(op), byref(self.params), None if nv is None else _dptr(nv),
+                                  byref(h)), "bridge_mg_setup")
+        self.handle = h.value
+        nb, nvec = c_int(), c_int()
+        check(lib.bridge_mg_info(self.handle, byref(nb), byref(nvec)), "bridge_mg_info")
+        self.nblocks, self.nvec = nb.value, nvec.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _abi.load().bridge_mg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, b, solver=None, x0=None, raise_on_fail=True):
+        lib = _abi.load()
+        solver = solver or make_solver()
+        bb = _host(b)
+        nrhs = 1 if bb.ndim == 3 else bb.shape[0]
+        x = np.zeros_like(bb) if x0 is None else _host(x0).copy()
+        info = (bridge_info * nrhs)()
+        st = lib.bridge_mg_solve(self.handle, byref(solver), _dptr(bb), _dptr(x), nrhs, info)
+        if raise_on_fail:
+            check(st, "bridge_mg_solve")
+        return x, _infos(info, nrhs)
+
+    def apply(self, which, v):
+        """One piece of the cycle (bridge_mg_apply_op) on a canonical array."""
+        fine_out = which in (_abi.BRIDGE_MG_PROLONG, _abi.BRIDGE_MG_SAP, _abi.BRIDGE_MG_CYCLE)
+        V = self.lattice.V
+        out = np.empty((V, 4, 3) if fine_out else (self.nblocks, 2, self.nvec), dtype=np.complex128)
+        vin = _host(v)
+        check(_abi.load().bridge_mg_apply(self.handle, int(which), _dptr(vin), _dptr(out)), "bridge_mg_apply")
+        return out
+
+    def coarse_matrix(self):
+        """[block][coupling][column][row] complex."""
+        n2 = 2 * self.nvec
+        out = np.empty((self.nblocks, 9, n2, n2), dtype=np.complex128)
+        check(_abi.load().bridge_mg_coarse_matrix(self.handle, _dptr(out)), "bridge_mg_coarse_matrix")
+        return out
+
+
 # --- convenience ---------------------------------------------------------------------------
 
 

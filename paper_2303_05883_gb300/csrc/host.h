@@ -63,6 +63,13 @@ enum KClass {
   K_STAG_VEC,      // staggered vector kernels and conversions
   K_STAG_PREP,     // staggered even-odd prepare / reconstruct
   K_STAG_RESID,    // staggered FP64 residual with |r|^2
+  K_MG_SAP,        // multigrid: SAP block minimal-residual solves
+  K_MG_RESID,      // multigrid: FP32 fine residual r - D x of the smoother
+  K_MG_TRANSFER,   // multigrid: restriction / prolongation
+  K_MG_COARSE,     // multigrid: coarse operator applications
+  K_MG_VEC,        // multigrid: vector updates and dot products (fine FP64 and coarse)
+  K_MG_OUTER,      // multigrid: FP64 operator of the outer FBiCGStab
+  K_MG_SETUP,      // multigrid: setup (null vectors, Gram-Schmidt, coarse operator)
   K_NCLASS
 };
 const char* kclass_name(int k);

@@ -1,0 +1,525 @@
+// Two-level multigrid kernels for the clover operator (Sec. 3 of the paper:
+// a DD-alpha-AMG variant with an SAP smoother, coarse BiCGStab and an outer
+// Flexible BiCGStab).
+//
+// Blocks (the SAP domains, which are also the aggregates) tile the lattice;
+// an aggregate is one block and one chirality (spins 0, 1 / 2, 3).  A CTA
+// works on one block: thread j <-> site j of the block in lexicographic
+// order of the block-local coordinates.  Fine fields are the usual
+// full-lattice FP32 fields (two parity blocks of SoA planes); coarse vectors
+// are [coarse site][chirality][vector] complex floats; the coarse operator is
+// [coarse site][9 couplings][column b][row a] complex floats with coupling 0
+// the block itself and 1 + 2 mu / 2 + 2 mu the blocks at +mu / -mu.
+#pragma once
+
+#include "dslash.cuh"
+
+namespace bridge {
+
+struct MgGeom {
+  Geom g;       // fine lattice
+  int b[4];     // block extents
+  int cd[4];    // blocks per direction (even)
+  int bsites;   // sites per block
+  int nblocks;  // coarse sites
+};
+
+// Fine site of block-local index j in block blk: parity, half-lattice index
+// and coordinates.
+BR_HD void mg_site(const MgGeom& m, int blk, int j, int c[4], int& parity, uint32_t& ih) {
+  int bc[4];
+  int r = blk;
+  for (int k = 0; k < 4; ++k) {
+    bc[k] = r % m.cd[k];
+    r /= m.cd[k];
+  }
+  int q = j;
+  for (int k = 0; k < 4; ++k) {
+    c[k] = bc[k] * m.b[k] + q % m.b[k];
+    q /= m.b[k];
+  }
+  const long lex = c[0] + (long)m.g.L[0] * (c[1] + (long)m.g.L[1] * (c[2] + (long)m.g.L[2] * c[3]));
+  parity = (c[0] + c[1] + c[2] + c[3]) & 1;
+  ih = (uint32_t)(lex >> 1);
+}
+
+BR_HD int mg_block_colour(const MgGeom& m, int blk) {
+  int s = 0, r = blk;
+  for (int k = 0; k < 4; ++k) {
+    s += r % m.cd[k];
+    r /= m.cd[k];
+  }
+  return s & 1;
+}
+
+// Coarse neighbour of block blk at +mu (dir = +1) or -mu (dir = -1), periodic.
+BR_HD int mg_block_nbr(const MgGeom& m, int blk, int mu, int dir) {
+  int bc[4], r = blk;
+  for (int k = 0; k < 4; ++k) {
+    bc[k] = r % m.cd[k];
+    r /= m.cd[k];
+  }
+  bc[mu] = (bc[mu] + dir + m.cd[mu]) % m.cd[mu];
+  return bc[0] + m.cd[0] * (bc[1] + m.cd[1] * (bc[2] + m.cd[2] * bc[3]));
+}
+
+// Block sum of one complex float over the CTA into thread 0 (all threads).
+BR_D cx<float> mg_block_sum(cx<float> v, float2* sh) {
+  for (int off = 16; off > 0; off >>= 1) {
+    v.r += __shfl_xor_sync(0xffffffffu, v.r, off);
+    v.i += __shfl_xor_sync(0xffffffffu, v.i, off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = make_float2(v.r, v.i);
+  __syncthreads();
+  cx<float> s = czero<float>();
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) s = s + cx<float>{sh[w].x, sh[w].y};
+  return s;
+}
+
+// Block sum broadcast to every thread.
+BR_D cx<float> mg_block_allsum(cx<float> v, float2* sh) {
+  cx<float> s = mg_block_sum(v, sh);
+  if (threadIdx.x == 0) sh[0] = make_float2(s.r, s.i);
+  __syncthreads();
+  s = {sh[0].x, sh[0].y};
+  __syncthreads();
+  return s;
+}
+
+struct MgTransferArgs {
+  MgGeom m;
+  int nv;
+  const char* V;   // nv FP32 full fields (the orthonormal aggregate bases)
+  long V_rs;       // bytes between them
+  long field_block;  // bytes of one parity block of a full FP32 field
+  const char* fine_in;  // restrict: fine input (full FP32 field)
+  char* fine_out;       // prolong: fine output
+  int add;              // prolong: out += P c instead of out = P c
+  const float2* coarse_in;  // prolong input [nblocks][2][nv]
+  float2* coarse_out;       // restrict output
+};
+
+// Restriction c = P^dag v: one CTA per block, one vector at a time.
+__global__ void __launch_bounds__(1024) mg_restrict_kernel(const MgTransferArgs a) {
+  __shared__ float2 sh[32];
+  const int blk = blockIdx.x, j = threadIdx.x;
+  const bool on = j < a.m.bsites;
+  cx<float> v[12];
+  int c[4], p = 0;
+  uint32_t ih = 0;
+  if (on) {
+    mg_site(a.m, blk, j, c, p, ih);
+    load_spinor<P_F32>(a.fine_in + p * a.field_block, a.m.g.vh, ih, v);
+  }
+  for (int i = 0; i < a.nv; ++i) {
+    cx<float> d0 = czero<float>(), d1 = czero<float>();
+    if (on) {
+      cx<float> w[12];
+      load_spinor<P_F32>(a.V + i * a.V_rs + p * a.field_block, a.m.g.vh, ih, w);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) d0 = d0 + cmul_conj(w[k], v[k]);
+#pragma unroll
+      for (int k = 6; k < 12; ++k) d1 = d1 + cmul_conj(w[k], v[k]);
+    }
+    const cx<float> s0 = mg_block_sum(d0, sh);
+    if (threadIdx.x == 0) a.coarse_out[((long)blk * 2 + 0) * a.nv + i] = make_float2(s0.r, s0.i);
+    const cx<float> s1 = mg_block_sum(d1, sh);
+    if (threadIdx.x == 0) a.coarse_out[((long)blk * 2 + 1) * a.nv + i] = make_float2(s1.r, s1.i);
+  }
+}
+
+// Prolongation v (+)= P c: one CTA per block.
+__global__ void __launch_bounds__(1024) mg_prolong_kernel(const MgTransferArgs a) {
+  const int blk = blockIdx.x, j = threadIdx.x;
+  if (j >= a.m.bsites) return;
+  int c[4], p;
+  uint32_t ih;
+  mg_site(a.m, blk, j, c, p, ih);
+  cx<float> out[12];
+  if (a.add) {
+    load_spinor<P_F32, false>(a.fine_out + p * a.field_block, a.m.g.vh, ih, out);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[k] = czero<float>();
+  }
+  const float2* cb = a.coarse_in + (long)blk * 2 * a.nv;
+  for (int i = 0; i < a.nv; ++i) {
+    cx<float> w[12];
+    load_spinor<P_F32>(a.V + i * a.V_rs + p * a.field_block, a.m.g.vh, ih, w);
+    const float2 c0 = cb[i], c1 = cb[a.nv + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[k] = out[k] + w[k] * cx<float>{c0.x, c0.y};
+#pragma unroll
+    for (int k = 6; k < 12; ++k) out[k] = out[k] + w[k] * cx<float>{c1.x, c1.y};
+  }
+  store_spinor<P_F32>(a.fine_out + p * a.field_block, a.m.g.vh, ih, out);
+}
+
+// Modified Gram-Schmidt of the nv vectors on every aggregate, in place, in
+// FP32 (the order of the vectors fixes the basis): one CTA per block,
+// chirality by chirality.
+__global__ void __launch_bounds__(1024) mg_orthonormalize_kernel(const MgTransferArgs a) {
+  __shared__ float2 sh[32];
+  const int blk = blockIdx.x, j = threadIdx.x;
+  const bool on = j < a.m.bsites;
+  int c[4], p = 0;
+  uint32_t ih = 0;
+  if (on) mg_site(a.m, blk, j, c, p, ih);
+  char* V = const_cast<char*>(a.V);
+  for (int chi = 0; chi < 2; ++chi) {
+    const int k0 = 6 * chi;
+    for (int i = 0; i < a.nv; ++i) {
+      cx<float> vi[12];
+      if (on) load_spinor<P_F32, false>(V + i * a.V_rs + p * a.field_block, a.m.g.vh, ih, vi);
+      for (int jj = 0; jj < i; ++jj) {
+        cx<float> d = czero<float>();
+        cx<float> vj[12];
+        if (on) {
+          load_spinor<P_F32, false>(V + jj * a.V_rs + p * a.field_block, a.m.g.vh, ih, vj);
+          for (int k = k0; k < k0 + 6; ++k) d = d + cmul_conj(vj[k], vi[k]);
+        }
+        d = mg_block_allsum(d, sh);
+        if (on)
+          for (int k = k0; k < k0 + 6; ++k) vi[k] = vi[k] - d * vj[k];
+      }
+      float n = 0.f;
+      if (on)
+        for (int k = k0; k < k0 + 6; ++k) n += vi[k].r * vi[k].r + vi[k].i * vi[k].i;
+      const cx<float> nn = mg_block_allsum(cx<float>{n, 0.f}, sh);
+      const float inv = nn.r > 0.f ? rsqrtf(nn.r) : 0.f;
+      if (on) {
+        // write back only this chirality's components
+        cx<float> full[12];
+        load_spinor<P_F32, false>(V + i * a.V_rs + p * a.field_block, a.m.g.vh, ih, full);
+        for (int k = k0; k < k0 + 6; ++k) full[k] = inv * vi[k];
+        store_spinor<P_F32>(V + i * a.V_rs + p * a.field_block, a.m.g.vh, ih, full);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Setup probe: y = D_B w (mode 0: the block-local operator, hops that leave
+// the block dropped) or the single hop -kappa (1 -+ gamma_mu) U ... w(x +- mu)
+// restricted to hops that cross into the neighbouring block (mode 1 + 2 mu
+// for +mu, 2 + 2 mu for -mu).  FP32, one CTA per block.
+struct MgProbeArgs {
+  MgGeom m;
+  int mode;
+  float kappa;
+  float bcf[4];
+  const char* w;  // full FP32 field
+  char* y;
+  long field_block;
+  const char* gauge;  // FP32 links
+  const char* clov;   // FP32 clover T (both parities), mode 0
+};
+
+template <int MU>
+BR_D void mg_probe_dir(const MgProbeArgs& a, int c[4], int p, uint32_t ih, bool do_fwd, bool do_bwd, cx<float> acc[12]) {
+  const Geom& g = a.m.g;
+  const long lbb = link_block_bytes(P_F32, g.vh);
+  const char* g_out = a.gauge + (long)p * 4 * lbb;
+  const char* g_in = a.gauge + (long)(1 - p) * 4 * lbb;
+  const char* in = a.w + (1 - p) * a.field_block;
+  uint32_t xh = (uint32_t)(c[0] >> 1);
+  uint32_t f, b;
+  bool wf, wb;
+  neighbours<MU>(g, ih, c, xh, f, b, wf, wb);
+  if (do_fwd) hop_one<P_F32, MU, true, false>(in, g_out + MU * lbb, g.vh, f, ih, wf, a.bcf[MU], acc);
+  if (do_bwd) hop_one<P_F32, MU, false, false>(in, g_in + MU * lbb, g.vh, b, b, wb, a.bcf[MU], acc);
+}
+
+__global__ void __launch_bounds__(1024) mg_probe_kernel(const MgProbeArgs a) {
+  const int blk = blockIdx.x, j = threadIdx.x;
+  if (j >= a.m.bsites) return;
+  int c[4], p;
+  uint32_t ih;
+  mg_site(a.m, blk, j, c, p, ih);
+  int lc[4], q = j;
+  for (int k = 0; k < 4; ++k) {
+    lc[k] = q % a.m.b[k];
+    q /= a.m.b[k];
+  }
+  // which hops stay in the block (blocks are at most half the lattice, so a
+  // hop that wraps always leaves its block)
+  bool fin[4], bin[4];
+  for (int k = 0; k < 4; ++k) {
+    fin[k] = lc[k] + 1 < a.m.b[k];
+    bin[k] = lc[k] > 0;
+  }
+  bool fsel[4], bsel[4];
+  for (int k = 0; k < 4; ++k) {
+    if (a.mode == 0) {
+      fsel[k] = fin[k];
+      bsel[k] = bin[k];
+    } else {
+      const int mu = (a.mode - 1) >> 1, dir = ((a.mode - 1) & 1) ? -1 : 1;
+      fsel[k] = k == mu && dir > 0 && !fin[k];
+      bsel[k] = k == mu && dir < 0 && !bin[k];
+    }
+  }
+  cx<float> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = czero<float>();
+  mg_probe_dir<0>(a, c, p, ih, fsel[0], bsel[0], acc);
+  mg_probe_dir<1>(a, c, p, ih, fsel[1], bsel[1], acc);
+  mg_probe_dir<2>(a, c, p, ih, fsel[2], bsel[2], acc);
+  mg_probe_dir<3>(a, c, p, ih, fsel[3], bsel[3], acc);
+  cx<float> out[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) out[k] = (-a.kappa) * acc[k];
+  if (a.mode == 0) {
+    cx<float> wv[12], tw[12];
+    load_spinor<P_F32>(a.w + p * a.field_block, a.m.g.vh, ih, wv);
+    clover_apply<P_F32>(a.clov + p * clover_block_bytes(P_F32, a.m.g.vh), a.m.g.vh, ih, wv, tw);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[k] = out[k] + tw[k];
+  }
+  store_spinor<P_F32>(a.y + p * a.field_block, a.m.g.vh, ih, out);
+}
+
+// Coarse operator application y = D_c x (or y = b - D_c x with b != null):
+// thread (coarse site, row a); rows of one site in consecutive threads.
+struct MgCoarseArgs {
+  MgGeom m;
+  int n2;  // 2 nv
+  const float2* Dc;
+  const float2* x;
+  const float2* b;
+  float2* y;
+};
+
+__global__ void __launch_bounds__(256) mg_coarse_kernel(const MgCoarseArgs a) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n2 = a.n2;
+  if (t >= (long)a.m.nblocks * n2) return;
+  const int X = (int)(t / n2), row = (int)(t % n2);
+  cx<float> s = czero<float>();
+  for (int d = 0; d < 9; ++d) {
+    const int Y = d == 0 ? X : mg_block_nbr(a.m, X, (d - 1) >> 1, ((d - 1) & 1) ? -1 : 1);
+    const float2* M = a.Dc + ((long)X * 9 + d) * n2 * n2 + row;
+    const float2* xv = a.x + (long)Y * n2;
+    for (int col = 0; col < n2; ++col) {
+      const float2 m = M[(long)col * n2], v = xv[col];
+      s = s + cx<float>{m.x, m.y} * cx<float>{v.x, v.y};
+    }
+  }
+  if (a.b) {
+    const float2 bb = a.b[t];
+    s = cx<float>{bb.x, bb.y} - s;
+  }
+  a.y[t] = make_float2(s.r, s.i);
+}
+
+// SAP block solve: `steps` minimal-residual steps on D_B e = r_B for every
+// block of one colour, then x_B += e.  One CTA per block (blocks of the other
+// colour return at once); rho in shared memory, q and e in registers.
+struct MgSapArgs {
+  MgGeom m;
+  int colour, steps;
+  float kappa;
+  const char* r;  // full FP32 field (the current residual)
+  char* x;        // full FP32 field, updated
+  long field_block;
+  const char* gauge;
+  const char* clov;
+};
+
+__global__ void __launch_bounds__(256) mg_sap_kernel(const MgSapArgs a) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ float2 sh[32];
+  const int blk = blockIdx.x;
+  if (mg_block_colour(a.m, blk) != a.colour) return;  // uniform per CTA
+  const int j = threadIdx.x, nsite = a.m.bsites;
+  const bool on = j < nsite;
+  cx<float>* rho = reinterpret_cast<cx<float>*>(dsm);  // [12][nsite]
+  const long vh = a.m.g.vh;
+  int c[4], p = 0;
+  uint32_t ih = 0;
+  int lc[4] = {0, 0, 0, 0};
+  int nbf[4], nbb[4];  // block-local neighbours (-1 outside)
+  uint32_t gf[4], gb[4];
+  cx<float> e[12], rr[12];
+  if (on) {
+    mg_site(a.m, blk, j, c, p, ih);
+    int q = j, stride = 1;
+    int st[4];
+    for (int k = 0; k < 4; ++k) {
+      lc[k] = q % a.m.b[k];
+      q /= a.m.b[k];
+      st[k] = stride;
+      stride *= a.m.b[k];
+    }
+    for (int k = 0; k < 4; ++k) {
+      nbf[k] = lc[k] + 1 < a.m.b[k] ? j + st[k] : -1;
+      nbb[k] = lc[k] > 0 ? j - st[k] : -1;
+    }
+    uint32_t xh = (uint32_t)(c[0] >> 1);
+    bool w1, w2;
+    neighbours<0>(a.m.g, ih, c, xh, gf[0], gb[0], w1, w2);
+    neighbours<1>(a.m.g, ih, c, xh, gf[1], gb[1], w1, w2);
+    neighbours<2>(a.m.g, ih, c, xh, gf[2], gb[2], w1, w2);
+    neighbours<3>(a.m.g, ih, c, xh, gf[3], gb[3], w1, w2);
+    load_spinor<P_F32>(a.r + p * a.field_block, vh, ih, rr);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      rho[k * nsite + j] = rr[k];
+      e[k] = czero<float>();
+    }
+  }
+  __syncthreads();
+  const long lbb = link_block_bytes(P_F32, vh);
+  const char* g_out = a.gauge + (long)p * 4 * lbb;
+  const char* g_in = a.gauge + (long)(1 - p) * 4 * lbb;
+  const char* clov = a.clov + p * clover_block_bytes(P_F32, vh);
+  for (int step = 0; step < a.steps; ++step) {
+    cx<float> qv[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) qv[k] = czero<float>();
+    if (on) {
+      // H_B rho: hops to neighbours inside the block, rho read from shared memory
+      cx<float> acc[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = czero<float>();
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+        for (int fb = 0; fb < 2; ++fb) {
+          const int nb = fb == 0 ? nbf[mu] : nbb[mu];
+          if (nb < 0) continue;
+          cx<float> psi[12], h[2][3], u[2][3];
+#pragma unroll
+          for (int k = 0; k < 12; ++k) psi[k] = rho[k * nsite + nb];
+          Link<float> U;
+          if (fb == 0)
+            load_link<P_F32>(g_out + mu * lbb, vh, ih, U);
+          else
+            load_link<P_F32>(g_in + mu * lbb, vh, gb[mu], U);
+          switch (mu * 2 + fb) {
+            case 0: project<float, 0, true>(psi, h); break;
+            case 1: project<float, 0, false>(psi, h); break;
+            case 2: project<float, 1, true>(psi, h); break;
+            case 3: project<float, 1, false>(psi, h); break;
+            case 4: project<float, 2, true>(psi, h); break;
+            case 5: project<float, 2, false>(psi, h); break;
+            case 6: project<float, 3, true>(psi, h); break;
+            default: project<float, 3, false>(psi, h); break;
+          }
+#pragma unroll
+          for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              if (fb == 0)
+                u[s][r] = U.m[r][0] * h[s][0] + U.m[r][1] * h[s][1] + U.m[r][2] * h[s][2];
+              else
+                u[s][r] = cmul_conj(U.m[0][r], h[s][0]) + cmul_conj(U.m[1][r], h[s][1]) + cmul_conj(U.m[2][r], h[s][2]);
+            }
+          switch (mu * 2 + fb) {
+            case 0: reconstruct<float, 0, true>(u, acc); break;
+            case 1: reconstruct<float, 0, false>(u, acc); break;
+            case 2: reconstruct<float, 1, true>(u, acc); break;
+            case 3: reconstruct<float, 1, false>(u, acc); break;
+            case 4: reconstruct<float, 2, true>(u, acc); break;
+            case 5: reconstruct<float, 2, false>(u, acc); break;
+            case 6: reconstruct<float, 3, true>(u, acc); break;
+            default: reconstruct<float, 3, false>(u, acc); break;
+          }
+        }
+      }
+      cx<float> mine[12], tr[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) mine[k] = rho[k * nsite + j];
+      clover_apply<P_F32>(clov, vh, ih, mine, tr);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) qv[k] = tr[k] - a.kappa * acc[k];
+    }
+    // alpha = <q, rho> / <q, q> over the block
+    cx<float> dqr = czero<float>();
+    float dqq = 0.f;
+    if (on) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const cx<float> rk = rho[k * nsite + j];
+        dqr = dqr + cmul_conj(qv[k], rk);
+        dqq += qv[k].r * qv[k].r + qv[k].i * qv[k].i;
+      }
+    }
+    const cx<float> sqr = mg_block_allsum(dqr, sh);
+    const cx<float> sqq = mg_block_allsum(cx<float>{dqq, 0.f}, sh);
+    const cx<float> alpha = sqq.r > 0.f ? (1.f / sqq.r) * sqr : czero<float>();
+    if (on) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const cx<float> rk = rho[k * nsite + j];
+        e[k] = e[k] + alpha * rk;
+        rho[k * nsite + j] = rk - alpha * qv[k];
+      }
+    }
+    __syncthreads();
+  }
+  if (on) {
+    cx<float> xv[12];
+    load_spinor<P_F32, false>(a.x + p * a.field_block, vh, ih, xv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) xv[k] = xv[k] + e[k];
+    store_spinor<P_F32>(a.x + p * a.field_block, vh, ih, xv);
+  }
+}
+
+// ------------------------------------------------------- flat vector kernels
+// y = a x + b y + c z over n complex numbers (b == 0: y is not read; z may be
+// null when c == 0), with T float2 or double2; and <x, y> partial sums.
+template <class T, class S>
+__global__ void __launch_bounds__(256) mg_axpbypcz_kernel(long n, cx<S> ca, const T* x, cx<S> cb, T* y, cx<S> cc,
+                                                         const T* z) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const T xv = x[i];
+    cx<S> v = ca * cx<S>{xv.x, xv.y};
+    if (cb.r != S(0) || cb.i != S(0)) {
+      const T yv = y[i];
+      v = v + cb * cx<S>{yv.x, yv.y};
+    }
+    if (z) {
+      const T zv = z[i];
+      v = v + cc * cx<S>{zv.x, zv.y};
+    }
+    T o;
+    o.x = v.r;
+    o.y = v.i;
+    y[i] = o;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) mg_dot_kernel(long n, const T* x, const T* y, double2* partial) {
+  __shared__ double sr[8], si[8];
+  double ar = 0, ai = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const T a = x[i], b = y[i];
+    ar += (double)a.x * b.x + (double)a.y * b.y;
+    ai += (double)a.x * b.y - (double)a.y * b.x;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    ar += __shfl_xor_sync(0xffffffffu, ar, off);
+    ai += __shfl_xor_sync(0xffffffffu, ai, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = ar;
+    si[threadIdx.x >> 5] = ai;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0, ti = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tr += sr[w];
+      ti += si[w];
+    }
+    partial[blockIdx.x] = make_double2(tr, ti);
+  }
+}
+
+}  // namespace bridge

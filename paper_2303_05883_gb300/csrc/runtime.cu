@@ -25,7 +25,9 @@ const char* kclass_name(int k) {
                                         "dwf_mix",      "dwf_hop",       "dwf_schur_pass1", "dwf_schur_pass2",
                                         "dwf_schur_pass2_cg", "dwf_evenodd_prep", "dwf_residual64",
                                         "stag_hop",     "stag_pass1",    "stag_pass2",  "stag_vec",
-                                        "stag_prep",    "stag_residual64"};
+                                        "stag_prep",    "stag_residual64",
+                                        "mg_sap",       "mg_residual32", "mg_transfer", "mg_coarse",
+                                        "mg_vec",       "mg_outer_dirac", "mg_setup"};
   return (k >= 0 && k < K_NCLASS) ? names[k] : "?";
 }
 
