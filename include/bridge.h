@@ -306,14 +306,17 @@ typedef struct {
   int block[4];       /* block extents; each divides the lattice with an even quotient; 2 .. 256 sites */
   int nvec;           /* null vectors, 1 .. 32 */
   double setup_tol;   /* tolerance of the generated null vectors' solves D v = eta (random eta) */
+  int setup_steps;    /* inverse-iteration steps per generated null vector (v <- D^-1 v / |v|) */
   int sap_cycles;     /* SAP post-smoothing cycles per preconditioner application */
   int mr_steps;       /* minimal-residual steps per block system */
   double coarse_tol;  /* relative tolerance of the coarse BiCGStab */
   int coarse_maxiter; /* iteration limit of the coarse BiCGStab */
+  int coarse_half;    /* 1: the coarse BiCGStab reads an FP16 copy of the coarse operator (FP32 math) */
 } bridge_mg_params;
 
-/* Defaults: blocks 4^4, 16 null vectors, setup_tol 5e-2, 2 SAP cycles,
- * 4 MR steps, coarse_tol 5e-2, coarse_maxiter 200. */
+/* Defaults: blocks 4^4, 16 null vectors, setup_tol 5e-2, 1 setup step,
+ * 2 SAP cycles, 4 MR steps, coarse_tol 5e-2, coarse_maxiter 200, FP16
+ * coarse operator in the coarse solver. */
 void bridge_mg_defaults(bridge_mg_params* p);
 /* Build the multigrid hierarchy for op on the lattice's gauge field.
  * null_vectors: NULL to generate them (solves of random sources), or nvec
@@ -324,9 +327,12 @@ int bridge_mg_setup(bridge_lattice lat, const bridge_op* op, const bridge_mg_par
                     bridge_mg* out);
 int bridge_mg_destroy(bridge_mg mg);
 /* Solve D x = b for nrhs right-hand sides (host canonical buffers; x holds
- * the initial guesses) to s->tol in the true FP64 residual, with at most
- * s->max_iter outer iterations per right-hand side.  info[nrhs]: status,
- * outer iterations in inner_iters, restarts, true residual, seconds.
+ * the initial guesses) to s->tol in the true FP64 residual: FP64 defect
+ * correction (at most s->max_outer passes) around FP32 FBiCGStab passes
+ * preconditioned by the cycle (at most s->max_iter FBiCGStab iterations in
+ * all; a pass stops at s->inner_tol, default 1e-6, or at the reduction the
+ * true residual still needs).  info[nrhs]: status, passes in outer_iters,
+ * FBiCGStab iterations in inner_iters, restarts, true residual, seconds.
  * Synchronous. */
 int bridge_mg_solve(bridge_mg mg, const bridge_solver* s, const double* b, double* x, int nrhs, bridge_info* info);
 
@@ -336,7 +342,7 @@ int bridge_mg_solve(bridge_mg mg, const bridge_solver* s, const double* b, doubl
 enum bridge_mg_apply_op {
   BRIDGE_MG_RESTRICT = 0, /* fine in -> coarse out: P^dag in */
   BRIDGE_MG_PROLONG = 1,  /* coarse in -> fine out: P in */
-  BRIDGE_MG_COARSE = 2,   /* coarse -> coarse: D_c in */
+  BRIDGE_MG_COARSE = 2,   /* coarse -> coarse: D_c in (the FP32 coarse operator) */
   BRIDGE_MG_SAP = 3,      /* fine -> fine: sap_cycles SAP cycles on D x = in from x = 0 */
   BRIDGE_MG_CYCLE = 4     /* fine -> fine: the preconditioner */
 };
@@ -345,6 +351,8 @@ int bridge_mg_apply(bridge_mg mg, int which, const double* in, double* out);
  * coupling 0 is the block itself, 1 + 2 mu / 2 + 2 mu the blocks at +mu / -mu. */
 int bridge_mg_coarse_matrix(bridge_mg mg, double* out);
 int bridge_mg_info(bridge_mg mg, int* nblocks, int* nvec);
+/* Coarse solves run so far and their BiCGStab iterations in total. */
+int bridge_mg_counters(bridge_mg mg, long* coarse_solves, long* coarse_iters);
 
 /* ---- serving: continuous batching of solve requests ------------------------- */
 

@@ -74,10 +74,12 @@ class bridge_mg_params(ctypes.Structure):
         ("block", c_int * 4),
         ("nvec", c_int),
         ("setup_tol", c_double),
+        ("setup_steps", c_int),
         ("sap_cycles", c_int),
         ("mr_steps", c_int),
         ("coarse_tol", c_double),
         ("coarse_maxiter", c_int),
+        ("coarse_half", c_int),
     ]
 
 
@@ -127,6 +129,7 @@ SIGNATURES = {
     "bridge_mg_apply": (c_int, [_h, c_int, _dp, _dp]),
     "bridge_mg_coarse_matrix": (c_int, [_h, _dp]),
     "bridge_mg_info": (c_int, [_h, POINTER(c_int), POINTER(c_int)]),
+    "bridge_mg_counters": (c_int, [_h, POINTER(c_long), POINTER(c_long)]),
     "bridge_poll": (c_int, [_h, _dp, POINTER(bridge_info)]),
     "bridge_wait": (c_int, [_h, c_int, _dp, POINTER(bridge_info)]),
     "bridge_request_release": (c_int, [_h]),

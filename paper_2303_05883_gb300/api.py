@@ -410,6 +410,12 @@ class Multigrid:
         check(_abi.load().bridge_mg_apply(self.handle, int(which), _dptr(vin), _dptr(out)), "bridge_mg_apply")
         return out
 
+    def counters(self):
+        """(coarse solves, coarse BiCGStab iterations) so far."""
+        a, b = c_long(), c_long()
+        check(_abi.load().bridge_mg_counters(self.handle, byref(a), byref(b)), "bridge_mg_counters")
+        return a.value, b.value
+
     def coarse_matrix(self):
         """[block][coupling][column][row] complex."""
         n2 = 2 * self.nvec

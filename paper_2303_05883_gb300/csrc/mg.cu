@@ -12,7 +12,10 @@
 //           couplings across block faces, each restricted to the aggregates;
 //   cycle   e_c = BiCGStab(D_c, P^dag r) to a loose tolerance; z = P e_c;
 //           SAP cycles on the remaining residual (post-smoothing), FP32;
-//   solve   FBiCGStab in FP64 on D with the cycle as the preconditioner.
+//   solve   FP64 defect correction around FP32 FBiCGStab passes on D with the
+//           cycle as the preconditioner (the paper's outer FBiCGStab with a
+//           single-precision preconditioner, with the outer iteration itself
+//           in FP32 between FP64 true residuals).
 // The scalars of the coarse BiCGStab and of the outer solver live on the
 // host: each of their iterations costs one preconditioner cycle or one coarse
 // operator application, far more than the reads of the scalars.
@@ -58,6 +61,11 @@ __global__ void k_mg_scatter_column(const float2* tmp, float2* Dc, int nblocks, 
   Dc[(((long)X * 9 + mode) * n2 + col) * n2 + row] = tmp[t];
 }
 
+__global__ void k_mg_to_half(const float2* in, __half2* out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = __float22half2_rn(in[i]);
+}
+
 unsigned grid_for(long n, int threads = 256) {
   return (unsigned)std::max<long>(1, std::min<long>((n + threads - 1) / threads, (long)sm_count() * 16));
 }
@@ -76,8 +84,13 @@ struct bridge_mg_s {
   long nc = 0;  // complex numbers in a coarse vector
   std::shared_ptr<CloverSet> clov;
   Field V;  // nv FP32 full fields
-  std::unique_ptr<DevBuf> Dc, cvec, partial;
+  std::unique_ptr<DevBuf> Dc, Dch, cvec, partial;  // Dch: FP16 copy of Dc for the coarse solver
+  std::unique_ptr<DevBuf> cnbr;                     // [nblocks][9] coarse neighbours
   std::unique_ptr<PinnedBuf> hpart;
+  // coarse BiCGStab: scalars, reduction partials and ticket counter
+  std::unique_ptr<DevBuf> csc, cpart, ccount;
+  std::unique_ptr<PinnedBuf> hcsc;
+  long coarse_iters = 0, coarse_solves = 0;
   Field r32, x32, res32;  // fine FP32 work fields of the cycle
   float2* cv(int k) const { return reinterpret_cast<float2*>(cvec->ptr) + (long)k * nc; }
 };
@@ -124,24 +137,6 @@ std::vector<cx<double>> vdot_collect(bridge_mg_s* g, int slots) {
 
 // ---- fine FP64 full fields as two flat segments
 long fine_n(const Field& f) { return 12L * f.vh; }
-void faxpy(bridge_mg_s* g, cx<double> a, const Field& x, cx<double> b, const Field& y, cx<double> c, const Field* z) {
-  for (int p = 0; p < 2; ++p)
-    vaxpy<double2>(g, fine_n(x), a, reinterpret_cast<const double2*>(x.ptr(p)), b, reinterpret_cast<double2*>(y.ptr(p)),
-                   c, z ? reinterpret_cast<const double2*>(z->ptr(p)) : nullptr);
-}
-// <x, y> for the listed pairs, computed together (one host wait)
-std::vector<cx<double>> fdots(bridge_mg_s* g, std::initializer_list<std::pair<const Field*, const Field*>> pairs) {
-  int slot = 0;
-  for (const auto& pr : pairs)
-    for (int p = 0; p < 2; ++p)
-      vdot_launch<double2>(g, fine_n(*pr.first), reinterpret_cast<const double2*>(pr.first->ptr(p)),
-                           reinterpret_cast<const double2*>(pr.second->ptr(p)), slot++);
-  auto parts = vdot_collect(g, slot);
-  std::vector<cx<double>> out;
-  for (size_t k = 0; k < parts.size(); k += 2) out.push_back(parts[k] + parts[k + 1]);
-  return out;
-}
-
 // ---- transfer and coarse operator
 MgTransferArgs transfer_args(bridge_mg_s* g) {
   MgTransferArgs a;
@@ -176,67 +171,112 @@ void prolong_to(bridge_mg_s* g, const float2* c, const Field& fine, bool add) {
   note_launch(g->L, K_MG_TRANSFER, bytes, 0, stream_of(g), false);
   BR_CUDA(cudaGetLastError());
 }
-void coarse_apply(bridge_mg_s* g, const float2* x, float2* y, const float2* b = nullptr) {
+template <int RED>
+void launch_coarse_red(int n2, const MgCoarseArgs& a, unsigned grid, cudaStream_t st) {
+  switch (n2) {  // row lengths of 4, 8, 12, 16 and 24 null vectors unroll at compile time
+    case 8: mg_coarse_kernel<RED, 8><<<grid, 256, 0, st>>>(a); break;
+    case 16: mg_coarse_kernel<RED, 16><<<grid, 256, 0, st>>>(a); break;
+    case 24: mg_coarse_kernel<RED, 24><<<grid, 256, 0, st>>>(a); break;
+    case 32: mg_coarse_kernel<RED, 32><<<grid, 256, 0, st>>>(a); break;
+    case 48: mg_coarse_kernel<RED, 48><<<grid, 256, 0, st>>>(a); break;
+    default: mg_coarse_kernel<RED, 0><<<grid, 256, 0, st>>>(a); break;
+  }
+}
+void launch_coarse(int red, int n2, const MgCoarseArgs& a, unsigned grid, cudaStream_t st) {
+  if (red == MG_CR_ALPHA) launch_coarse_red<MG_CR_ALPHA>(n2, a, grid, st);
+  else if (red == MG_CR_OMEGA) launch_coarse_red<MG_CR_OMEGA>(n2, a, grid, st);
+  else launch_coarse_red<MG_CR_NONE>(n2, a, grid, st);
+}
+
+void coarse_apply(bridge_mg_s* g, const float2* x, float2* y, const float2* b = nullptr, int red = MG_CR_NONE,
+                  const float2* rhat = nullptr, bool half = false) {
   MgCoarseArgs a;
+  std::memset(static_cast<void*>(&a), 0, sizeof(a));
   a.m = g->m;
   a.n2 = g->n2;
   a.Dc = reinterpret_cast<const float2*>(g->Dc->ptr);
+  a.Dch = (half && g->Dch) ? reinterpret_cast<const __half2*>(g->Dch->ptr) : nullptr;
+  a.nbr = reinterpret_cast<const int*>(g->cnbr->ptr);
   a.x = x;
   a.b = b;
   a.y = y;
+  a.rhat = rhat;
+  if (red != MG_CR_NONE) {
+    a.red.partials = reinterpret_cast<double*>(g->cpart->ptr);
+    a.red.counter = reinterpret_cast<unsigned*>(g->ccount->ptr);
+    a.red.sc = reinterpret_cast<BiCGScalars*>(g->csc->ptr);
+    a.red.fin = red == MG_CR_ALPHA ? FIN_ALPHA : FIN_OMEGA;
+    a.red.check_done = 1;
+  }
   const long n = g->nc;
-  const double bytes = (double)g->m.nblocks * 9 * g->n2 * g->n2 * 8 + n * 8.0 * (b ? 3 : 2);
+  const double bytes = (double)g->m.nblocks * 9 * g->n2 * g->n2 * (a.Dch ? 4 : 8) + n * 8.0 * (b ? 3 : 2);
   note_launch(g->L, K_MG_COARSE, bytes, (double)g->m.nblocks * 9 * g->n2 * g->n2 * 8, stream_of(g), true);
-  mg_coarse_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream_of(g)>>>(a);
+  launch_coarse(red, g->n2, a, (unsigned)((n + 255) / 256), stream_of(g));
   note_launch(g->L, K_MG_COARSE, bytes, 0, stream_of(g), false);
   BR_CUDA(cudaGetLastError());
 }
 
-// ---- coarse BiCGStab (host scalars): D_c e = r to a relative tolerance
-int coarse_solve(bridge_mg_s* g, const float2* rhs, float2* x) {
-  const long n = g->nc;
-  float2 *r = g->cv(2), *rh = g->cv(3), *p = g->cv(4), *v = g->cv(5), *s = g->cv(6), *t = g->cv(7);
-  const cx<double> one{1, 0}, zero{0, 0};
-  BR_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * n, stream_of(g)));
-  BR_CUDA(cudaMemcpyAsync(r, rhs, sizeof(float2) * n, cudaMemcpyDeviceToDevice, stream_of(g)));
-  BR_CUDA(cudaMemcpyAsync(rh, rhs, sizeof(float2) * n, cudaMemcpyDeviceToDevice, stream_of(g)));
-  BR_CUDA(cudaMemsetAsync(p, 0, sizeof(float2) * n, stream_of(g)));
-  BR_CUDA(cudaMemsetAsync(v, 0, sizeof(float2) * n, stream_of(g)));
-  vdot_launch<float2>(g, n, rhs, rhs, 0);
-  const double b2 = vdot_collect(g, 1)[0].r;
-  if (!(b2 > 0.0)) return 0;
-  const double tol2 = g->prm.coarse_tol * g->prm.coarse_tol * b2;
-  cx<double> rho{1, 0}, alpha{1, 0}, omega{1, 0};
-  double r2 = b2;
-  int it = 0;
-  for (; it < g->prm.coarse_maxiter && r2 > tol2; ++it) {
-    vdot_launch<float2>(g, n, rh, r, 0);
-    const cx<double> rho_new = vdot_collect(g, 1)[0];
-    if (std::hypot(rho_new.r, rho_new.i) == 0.0) break;
-    const cx<double> beta = (rho_new * cx<double>{1.0 / (rho.r * rho.r + rho.i * rho.i), 0} * conj(rho)) *
-                            (alpha * cx<double>{1.0 / (omega.r * omega.r + omega.i * omega.i), 0} * conj(omega));
-    // p = r + beta (p - omega v)
-    vaxpy<float2>(g, n, one, r, beta, p, cx<double>{0, 0} - beta * omega, v);
-    coarse_apply(g, p, v);
-    vdot_launch<float2>(g, n, rh, v, 0);
-    const cx<double> rv = vdot_collect(g, 1)[0];
-    const double rv2 = rv.r * rv.r + rv.i * rv.i;
-    if (!(rv2 > 0.0)) break;
-    alpha = rho_new * cx<double>{1.0 / rv2, 0} * conj(rv);
-    vaxpy<float2>(g, n, one, r, zero, s, cx<double>{0, 0} - alpha, v);  // s = r - alpha v
-    coarse_apply(g, s, t);
-    vdot_launch<float2>(g, n, t, s, 0);
-    vdot_launch<float2>(g, n, t, t, 1);
-    auto d = vdot_collect(g, 2);
-    omega = d[1].r > 0 ? d[0] * cx<double>{1.0 / d[1].r, 0} : zero;
-    vaxpy<float2>(g, n, alpha, p, one, x, omega, s);                       // x += alpha p + omega s
-    vaxpy<float2>(g, n, one, s, zero, r, cx<double>{0, 0} - omega, t);     // r = s - omega t
-    vdot_launch<float2>(g, n, r, r, 0);
-    r2 = vdot_collect(g, 1)[0].r;
-    rho = rho_new;
-    if (omega.r == 0.0 && omega.i == 0.0) break;
+void cbicg_step(bridge_mg_s* g, int op, const float2* b = nullptr) {
+  MgCBicgArgs a;
+  std::memset(static_cast<void*>(&a), 0, sizeof(a));
+  a.n = g->nc;
+  a.x = g->cv(1);
+  a.r = g->cv(2);
+  a.rhat = g->cv(3);
+  a.p = g->cv(4);
+  a.v = g->cv(5);
+  a.s = g->cv(6);
+  a.t = g->cv(7);
+  a.b = b;
+  a.red.partials = reinterpret_cast<double*>(g->cpart->ptr);
+  a.red.counter = reinterpret_cast<unsigned*>(g->ccount->ptr);
+  a.red.sc = reinterpret_cast<BiCGScalars*>(g->csc->ptr);
+  a.red.fin = op == MG_CB_INIT ? FIN_INIT : op == MG_CB_XR ? FIN_RHO : FIN_NONE;
+  a.red.check_done = op == MG_CB_INIT ? 0 : 1;
+  const unsigned grid = (unsigned)((g->nc + 255) / 256);
+  const double bytes = (double)g->nc * 8 * (op == MG_CB_INIT ? 6 : op == MG_CB_S ? 3 : op == MG_CB_XR ? 8 : 4);
+  note_launch(g->L, K_MG_VEC, bytes, 0, stream_of(g), true);
+  switch (op) {
+    case MG_CB_INIT: mg_cbicg_kernel<MG_CB_INIT><<<grid, 256, 0, stream_of(g)>>>(a); break;
+    case MG_CB_S: mg_cbicg_kernel<MG_CB_S><<<grid, 256, 0, stream_of(g)>>>(a); break;
+    case MG_CB_XR: mg_cbicg_kernel<MG_CB_XR><<<grid, 256, 0, stream_of(g)>>>(a); break;
+    default: mg_cbicg_kernel<MG_CB_P><<<grid, 256, 0, stream_of(g)>>>(a); break;
   }
-  return it;
+  note_launch(g->L, K_MG_VEC, bytes, 0, stream_of(g), false);
+  BR_CUDA(cudaGetLastError());
+}
+
+// ---- coarse BiCGStab: D_c e = r to a relative tolerance, the scalars on the
+// device (the van der Vorst recurrences of reduce.cuh); the host polls the
+// done flag every `batch` iterations.  Solution in cv(1).
+int coarse_solve(bridge_mg_s* g, const float2* rhs) {
+  cudaStream_t st = stream_of(g);
+  BiCGScalars init;
+  std::memset(&init, 0, sizeof(init));
+  init.tol2 = g->prm.coarse_tol * g->prm.coarse_tol;
+  init.max_iter = std::max(1, g->prm.coarse_maxiter);
+  init.rho_r = init.alpha_r = init.omega_r = 1.0;
+  BR_CUDA(cudaMemcpyAsync(g->csc->ptr, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  cbicg_step(g, MG_CB_INIT, rhs);
+  const int batch = 8;
+  int launched = 0;
+  for (;;) {
+    for (int k = 0; k < batch && launched < g->prm.coarse_maxiter; ++k, ++launched) {
+      coarse_apply(g, g->cv(4), g->cv(5), nullptr, MG_CR_ALPHA, g->cv(3), true);  // v = D_c p, alpha
+      cbicg_step(g, MG_CB_S);                                                    // s = r - alpha v
+      coarse_apply(g, g->cv(6), g->cv(7), nullptr, MG_CR_OMEGA, nullptr, true);  // t = D_c s, omega
+      cbicg_step(g, MG_CB_XR);                                             // x, r; rho, beta
+      cbicg_step(g, MG_CB_P);                                              // p
+    }
+    BR_CUDA(cudaMemcpyAsync(g->hcsc->ptr, g->csc->ptr, sizeof(BiCGScalars), cudaMemcpyDeviceToHost, st));
+    BR_CUDA(cudaStreamSynchronize(st));
+    const BiCGScalars* q = static_cast<const BiCGScalars*>(g->hcsc->ptr);
+    if (q->done != RUNNING || launched >= g->prm.coarse_maxiter) {
+      g->coarse_iters += q->iter;
+      g->coarse_solves += 1;
+      return q->iter;
+    }
+  }
 }
 
 // ---- fine FP32 pieces of the cycle
@@ -305,7 +345,7 @@ void sap(bridge_mg_s* g, const Field& r, const Field& x, int cycles, bool x_zero
 // z = M r: coarse correction then SAP post-smoothing (FP32 fields).
 void cycle(bridge_mg_s* g, const Field& r, const Field& z) {
   restrict_to(g, r, g->cv(0));
-  coarse_solve(g, g->cv(0), g->cv(1));
+  coarse_solve(g, g->cv(0));
   prolong_to(g, g->cv(1), z, false);
   sap(g, r, z, g->prm.sap_cycles, false);
 }
@@ -319,7 +359,8 @@ void check_block(const bridge_lattice_s* L, const bridge_mg_params& p) {
   }
   BR_CHECK(bs <= 256 && bs >= 2, BRIDGE_EINVAL, "mg blocks hold 2 .. 256 sites");
   BR_CHECK(p.nvec >= 1 && p.nvec <= 32, BRIDGE_EINVAL, "mg nvec must be in 1..32");
-  BR_CHECK(p.sap_cycles >= 0 && p.mr_steps >= 0 && p.coarse_maxiter >= 0, BRIDGE_EINVAL, "mg iteration counts");
+  BR_CHECK(p.sap_cycles >= 0 && p.mr_steps >= 0 && p.coarse_maxiter >= 0 && p.setup_steps >= 0, BRIDGE_EINVAL,
+           "mg iteration counts");
 }
 
 }  // namespace
@@ -359,9 +400,22 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
   g->x32 = make_field(P_F32, BRIDGE_FULL, 1, L->vh);
   g->res32 = make_field(P_F32, BRIDGE_FULL, 1, L->vh);
   g->Dc.reset(new DevBuf((size_t)g->m.nblocks * 9 * g->n2 * g->n2 * sizeof(float2)));
+  {
+    std::vector<int> nb((size_t)g->m.nblocks * 9);
+    for (int X = 0; X < g->m.nblocks; ++X)
+      for (int d = 0; d < 9; ++d)
+        nb[(size_t)X * 9 + d] = d == 0 ? X : mg_block_nbr(g->m, X, (d - 1) >> 1, ((d - 1) & 1) ? -1 : 1);
+    g->cnbr.reset(new DevBuf(nb.size() * sizeof(int)));
+    BR_CUDA(cudaMemcpy(g->cnbr->ptr, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   g->cvec.reset(new DevBuf((size_t)8 * g->nc * sizeof(float2)));
   g->partial.reset(new DevBuf(sizeof(double2) * 1024 * 8));
   g->hpart.reset(new PinnedBuf(sizeof(double2) * 1024 * 8));
+  g->csc.reset(new DevBuf(256));
+  g->hcsc.reset(new PinnedBuf(256));
+  g->cpart.reset(new DevBuf(sizeof(double) * 4 * ((g->nc + 255) / 256)));
+  g->ccount.reset(new DevBuf(256));
+  BR_CUDA(cudaMemsetAsync(g->ccount->ptr, 0, 256, st));
   const size_t canon = (size_t)L->V * 24;
   // ---- null vectors
   {
@@ -380,9 +434,14 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
         k_mg_random<<<grid_for((long)canon), 256, 0, st>>>(reinterpret_cast<double*>(eta.ptr), (long)canon, 1000u + i);
         note_launch(L, K_MG_SETUP, 0, 0, st, false);
         double* xi = reinterpret_cast<double*>(can.ptr) + canon * i;
-        BR_CUDA(cudaMemsetAsync(xi, 0, canon * sizeof(double), st));
-        SolveState S(L, op, s, 1, st, reinterpret_cast<double*>(eta.ptr), xi);
-        while (!S.advance()) BR_CUDA(cudaEventSynchronize(S.wait_event()));
+        for (int step = 0; step < std::max(1, prm.setup_steps); ++step) {
+          if (step > 0) {  // the next source is the last iterate (the scale does not matter)
+            BR_CUDA(cudaMemcpyAsync(eta.ptr, xi, canon * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          }
+          BR_CUDA(cudaMemsetAsync(xi, 0, canon * sizeof(double), st));
+          SolveState S(L, op, s, 1, st, reinterpret_cast<double*>(eta.ptr), xi);
+          while (!S.advance()) BR_CUDA(cudaEventSynchronize(S.wait_event()));
+        }
       }
     }
     canon_to_field(L, reinterpret_cast<const double*>(can.ptr), g->V, st);
@@ -434,6 +493,15 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
         }
       }
     BR_CUDA(cudaGetLastError());
+    if (prm.coarse_half) {
+      const long n = (long)g->m.nblocks * 9 * g->n2 * g->n2;
+      g->Dch.reset(new DevBuf(sizeof(__half2) * n));
+      note_launch(L, K_MG_SETUP, 0, 0, st, true);
+      k_mg_to_half<<<grid_for(n), 256, 0, st>>>(reinterpret_cast<const float2*>(g->Dc->ptr),
+                                                   reinterpret_cast<__half2*>(g->Dch->ptr), n);
+      note_launch(L, K_MG_SETUP, 0, 0, st, false);
+      BR_CUDA(cudaGetLastError());
+    }
     BR_CUDA(cudaStreamSynchronize(st));
   }
   *out = g.release();
@@ -442,27 +510,105 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
 
 namespace bridge {
 
-// FBiCGStab (FP64) on D x = b, preconditioned by the FP32 cycle; b, x
+// Flat vector operations on full fields of one precision (T = float2 for
+// FP32, double2 for FP64): each parity block holds 12 vh complex numbers.
+template <class T>
+void gaxpy(bridge_mg_s* g, cx<double> a, const Field& x, cx<double> b, const Field& y, cx<double> c, const Field* z) {
+  for (int p = 0; p < 2; ++p)
+    vaxpy<T>(g, fine_n(x), a, reinterpret_cast<const T*>(x.ptr(p)), b, reinterpret_cast<T*>(y.ptr(p)), c,
+             z ? reinterpret_cast<const T*>(z->ptr(p)) : nullptr);
+}
+template <class T>
+std::vector<cx<double>> gdots(bridge_mg_s* g, std::initializer_list<std::pair<const Field*, const Field*>> pairs) {
+  int slot = 0;
+  for (const auto& pr : pairs)
+    for (int p = 0; p < 2; ++p)
+      vdot_launch<T>(g, fine_n(*pr.first), reinterpret_cast<const T*>(pr.first->ptr(p)),
+                     reinterpret_cast<const T*>(pr.second->ptr(p)), slot++);
+  auto parts = vdot_collect(g, slot);
+  std::vector<cx<double>> out;
+  for (size_t k = 0; k < parts.size(); k += 2) out.push_back(parts[k] + parts[k + 1]);
+  return out;
+}
+
+// FBiCGStab in FP32 on D e = r (e = 0 on entry), preconditioned by the cycle,
+// to ||r - D e|| <= tol ||r|| by the recursive residual; returns iterations.
+int fbicgstab32(bridge_mg_s* g, const Field& rhs, const Field& x, double tol, int max_iter, int& restarts) {
+  bridge_lattice_s* L = g->L;
+  cudaStream_t st = L->stream;
+  auto F = [&](const char* name) -> Field& { return workspace(L, std::string("mg_") + name, P_F32, BRIDGE_FULL, 1); };
+  Field &r = F("r"), &rh = F("rh"), &p = F("p"), &v = F("v"), &sv = F("s"), &t = F("t"), &ph = F("ph"), &sh = F("sh");
+  auto Dop = [&](const Field& in, const Field& out) { apply_d(L, g->op, out, in, st); };
+  const cx<double> one{1, 0}, zero{0, 0};
+  BR_CUDA(cudaMemsetAsync(x.buf->ptr, 0, x.buf->bytes, st));
+  BR_CUDA(cudaMemcpyAsync(r.buf->ptr, rhs.buf->ptr, r.buf->bytes, cudaMemcpyDeviceToDevice, st));
+  const double b2 = gdots<float2>(g, {{&r, &r}})[0].r;
+  if (!(b2 > 0.0)) return 0;
+  const double tol2 = tol * tol * b2;
+  double r2 = b2;
+  int it = 0;
+  while (it < max_iter && r2 > tol2) {
+    BR_CUDA(cudaMemcpyAsync(rh.buf->ptr, r.buf->ptr, r.buf->bytes, cudaMemcpyDeviceToDevice, st));
+    BR_CUDA(cudaMemsetAsync(p.buf->ptr, 0, p.buf->bytes, st));
+    BR_CUDA(cudaMemsetAsync(v.buf->ptr, 0, v.buf->bytes, st));
+    cx<double> rho{1, 0}, alpha{1, 0}, omega{1, 0};
+    bool breakdown = false;
+    while (it < max_iter && r2 > tol2) {
+      const cx<double> rho_new = gdots<float2>(g, {{&rh, &r}})[0];
+      if (std::hypot(rho_new.r, rho_new.i) < 1e-30 * std::sqrt(r2 * b2)) {
+        breakdown = true;
+        break;
+      }
+      const cx<double> beta = (rho_new * cx<double>{1.0 / (rho.r * rho.r + rho.i * rho.i), 0} * conj(rho)) *
+                              (alpha * cx<double>{1.0 / (omega.r * omega.r + omega.i * omega.i), 0} * conj(omega));
+      gaxpy<float2>(g, one, r, beta, p, cx<double>{0, 0} - beta * omega, &v);  // p = r + beta (p - omega v)
+      cycle(g, p, ph);
+      Dop(ph, v);
+      const cx<double> rv = gdots<float2>(g, {{&rh, &v}})[0];
+      const double rv2 = rv.r * rv.r + rv.i * rv.i;
+      if (!(rv2 > 0.0)) {
+        breakdown = true;
+        break;
+      }
+      alpha = rho_new * cx<double>{1.0 / rv2, 0} * conj(rv);
+      gaxpy<float2>(g, one, r, zero, sv, cx<double>{0, 0} - alpha, &v);  // s = r - alpha v
+      cycle(g, sv, sh);
+      Dop(sh, t);
+      auto d = gdots<float2>(g, {{&t, &sv}, {&t, &t}});
+      omega = d[1].r > 0 ? d[0] * cx<double>{1.0 / d[1].r, 0} : zero;
+      gaxpy<float2>(g, alpha, ph, one, x, omega, &sh);                   // x += alpha p^ + omega s^
+      gaxpy<float2>(g, one, sv, zero, r, cx<double>{0, 0} - omega, &t);  // r = s - omega t
+      r2 = gdots<float2>(g, {{&r, &r}})[0].r;
+      rho = rho_new;
+      ++it;
+      if (omega.r == 0.0 && omega.i == 0.0) {
+        breakdown = true;
+        break;
+      }
+    }
+    if (!breakdown) break;
+    restarts += 1;  // restart from the recursive residual with a fresh shadow vector
+  }
+  return it;
+}
+
+// D x = b in FP64 by defect correction: r = b - D x (FP64), an FP32
+// FBiCGStab pass with the multigrid cycle on D e = r, x += e; b, x
 // canonical FP64 on the device (x: guess in, solution out).
 void mg_solve_one(bridge_mg_s* g, const double* b_dev, double* x_dev, const bridge_solver& s, bridge_info& info) {
   bridge_lattice_s* L = g->L;
   cudaStream_t st = L->stream;
   const auto t0 = std::chrono::steady_clock::now();
-  auto F = [&] { return make_field(P_F64, BRIDGE_FULL, 1, L->vh); };
-  Field b = F(), x = F(), r = F(), rh = F(), p = F(), v = F(), sv = F(), t = F(), ph = F(), sh = F();
+  Field& b = workspace(L, "mg_b64", P_F64, BRIDGE_FULL, 1);
+  Field& x = workspace(L, "mg_x64", P_F64, BRIDGE_FULL, 1);
+  Field& r = workspace(L, "mg_r64", P_F64, BRIDGE_FULL, 1);
+  Field& r32 = workspace(L, "mg_rin", P_F32, BRIDGE_FULL, 1);
+  Field& e32 = workspace(L, "mg_e", P_F32, BRIDGE_FULL, 1);
   canon_to_field(L, b_dev, b, st);
   canon_to_field(L, x_dev, x, st);
   std::memset(&info, 0, sizeof(info));
-  auto Dop = [&](const Field& in, const Field& out) { apply_d(L, g->op, out, in, st); };
-  auto prec = [&](const Field& in, const Field& out) {
-    convert_field(L, in, g->r32, 0, st, nullptr);
-    convert_field(L, in, g->r32, 1, st, nullptr);
-    cycle(g, g->r32, g->x32);
-    convert_field(L, g->x32, out, 0, st, nullptr);
-    convert_field(L, g->x32, out, 1, st, nullptr);
-  };
   const cx<double> one{1, 0}, zero{0, 0};
-  const double b2 = fdots(g, {{&b, &b}})[0].r;
+  const double b2 = gdots<double2>(g, {{&b, &b}})[0].r;
   if (!(b2 > 0.0)) {
     BR_CUDA(cudaMemsetAsync(x.buf->ptr, 0, x.buf->bytes, st));
     field_to_canon(L, x, x_dev, st);
@@ -470,66 +616,33 @@ void mg_solve_one(bridge_mg_s* g, const double* b_dev, double* x_dev, const brid
     info.status = BRIDGE_OK;
     return;
   }
-  const double tol2 = s.tol * s.tol * b2;
+  const double floor_tol = s.inner_tol > 0 ? s.inner_tol : 1e-6;
   const int max_iter = s.max_iter > 0 ? s.max_iter : 1000;
+  const int max_outer = s.max_outer > 0 ? s.max_outer : 50;
   int status = BRIDGE_ENOCONV;
-  for (int restart = 0; restart < 10 && info.inner_iters < max_iter; ++restart) {
-    // r = b - D x (true residual)
-    Dop(x, t);
-    faxpy(g, one, b, zero, r, cx<double>{-1, 0}, &t);
-    double r2 = fdots(g, {{&r, &r}})[0].r;
+  double r2_prev = 0.0, tau = floor_tol;
+  for (int pass = 0;; ++pass) {
+    apply_d(L, g->op, r, x, st);
+    gaxpy<double2>(g, one, b, cx<double>{-1, 0}, r, zero, nullptr);  // r = b - D x
+    const double r2 = gdots<double2>(g, {{&r, &r}})[0].r;
     info.true_rel_residual = std::sqrt(r2 / b2);
-    if (r2 <= tol2) {
+    info.outer_iters = pass;
+    if (r2 <= s.tol * s.tol * b2) {
       status = BRIDGE_OK;
       break;
     }
-    info.outer_iters = restart;
-    BR_CUDA(cudaMemcpyAsync(rh.buf->ptr, r.buf->ptr, r.buf->bytes, cudaMemcpyDeviceToDevice, st));
-    BR_CUDA(cudaMemsetAsync(p.buf->ptr, 0, p.buf->bytes, st));
-    BR_CUDA(cudaMemsetAsync(v.buf->ptr, 0, v.buf->bytes, st));
-    cx<double> rho{1, 0}, alpha{1, 0}, omega{1, 0};
-    bool breakdown = false;
-    while (r2 > tol2 && info.inner_iters < max_iter) {
-      const cx<double> rho_new = fdots(g, {{&rh, &r}})[0];
-      if (std::hypot(rho_new.r, rho_new.i) < 1e-30 * std::sqrt(r2 * b2)) {
-        breakdown = true;
-        break;
-      }
-      const cx<double> beta = (rho_new * cx<double>{1.0 / (rho.r * rho.r + rho.i * rho.i), 0} * conj(rho)) *
-                              (alpha * cx<double>{1.0 / (omega.r * omega.r + omega.i * omega.i), 0} * conj(omega));
-      faxpy(g, one, r, beta, p, cx<double>{0, 0} - beta * omega, &v);  // p = r + beta (p - omega v)
-      prec(p, ph);
-      Dop(ph, v);
-      const cx<double> rv = fdots(g, {{&rh, &v}})[0];
-      const double rv2 = rv.r * rv.r + rv.i * rv.i;
-      if (!(rv2 > 0.0)) {
-        breakdown = true;
-        break;
-      }
-      alpha = rho_new * cx<double>{1.0 / rv2, 0} * conj(rv);
-      faxpy(g, one, r, zero, sv, cx<double>{0, 0} - alpha, &v);  // s = r - alpha v
-      prec(sv, sh);
-      Dop(sh, t);
-      auto d = fdots(g, {{&t, &sv}, {&t, &t}});
-      omega = d[1].r > 0 ? d[0] * cx<double>{1.0 / d[1].r, 0} : zero;
-      faxpy(g, alpha, ph, one, x, omega, &sh);                    // x += alpha p^ + omega s^
-      faxpy(g, one, sv, zero, r, cx<double>{0, 0} - omega, &t);   // r = s - omega t
-      r2 = fdots(g, {{&r, &r}})[0].r;
-      rho = rho_new;
-      info.inner_iters += 1;
-      if (omega.r == 0.0 && omega.i == 0.0) {
-        breakdown = true;
-        break;
-      }
+    if (!std::isfinite(r2)) {
+      status = BRIDGE_EBREAKDOWN;
+      break;
     }
-    if (breakdown) info.restarts += 1;
-  }
-  if (status != BRIDGE_OK) {
-    Dop(x, t);
-    faxpy(g, one, b, zero, r, cx<double>{-1, 0}, &t);
-    const double r2 = fdots(g, {{&r, &r}})[0].r;
-    info.true_rel_residual = std::sqrt(r2 / b2);
-    if (r2 <= tol2) status = BRIDGE_OK;
+    if (pass >= max_outer || info.inner_iters >= max_iter) break;
+    tau = next_inner_tol(floor_tol, s.tol, b2, r2, r2_prev, tau, pass == 0);
+    r2_prev = r2;
+    convert_field(L, r, r32, 0, st, nullptr);
+    convert_field(L, r, r32, 1, st, nullptr);
+    info.inner_iters += fbicgstab32(g, r32, e32, tau, max_iter - info.inner_iters, info.restarts);
+    accumulate64(L, e32, 0, x, 0, st, nullptr);
+    accumulate64(L, e32, 1, x, 1, st, nullptr);
   }
   field_to_canon(L, x, x_dev, st);
   BR_CUDA(cudaStreamSynchronize(st));
@@ -617,10 +730,12 @@ void bridge_mg_defaults(bridge_mg_params* p) {
   for (int k = 0; k < 4; ++k) p->block[k] = 4;
   p->nvec = 16;
   p->setup_tol = 5e-2;
+  p->setup_steps = 1;
   p->sap_cycles = 2;
   p->mr_steps = 4;
   p->coarse_tol = 5e-2;
   p->coarse_maxiter = 200;
+  p->coarse_half = 1;
 }
 
 int bridge_mg_setup(bridge_lattice L, const bridge_op* op, const bridge_mg_params* prm, const double* null_vectors,
@@ -699,6 +814,13 @@ int bridge_mg_coarse_matrix(bridge_mg g, double* out) {
     out[2 * k + 1] = h[k].y;
   }
   BR_MG_END
+}
+
+int bridge_mg_counters(bridge_mg g, long* coarse_solves, long* coarse_iters) {
+  if (!g) return BRIDGE_EINVAL;
+  if (coarse_solves) *coarse_solves = g->coarse_solves;
+  if (coarse_iters) *coarse_iters = g->coarse_iters;
+  return BRIDGE_OK;
 }
 
 int bridge_mg_info(bridge_mg g, int* nblocks, int* nvec) {

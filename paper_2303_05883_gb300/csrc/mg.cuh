@@ -13,6 +13,7 @@
 #pragma once
 
 #include "dslash.cuh"
+#include "reduce.cuh"
 
 namespace bridge {
 
@@ -287,32 +288,132 @@ __global__ void __launch_bounds__(1024) mg_probe_kernel(const MgProbeArgs a) {
 struct MgCoarseArgs {
   MgGeom m;
   int n2;  // 2 nv
-  const float2* Dc;
+  const float2* Dc;     // FP32 coarse operator
+  const __half2* Dch;   // the same in FP16 (used when non-null)
+  const int* nbr;       // [nblocks][9] coarse site of each coupling
   const float2* x;
   const float2* b;
   float2* y;
+  const float2* rhat;  // MG_CR_ALPHA: <rhat, y> -> FIN_ALPHA
+  RedArgs red;
 };
 
-__global__ void __launch_bounds__(256) mg_coarse_kernel(const MgCoarseArgs a) {
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int n2 = a.n2;
-  if (t >= (long)a.m.nblocks * n2) return;
-  const int X = (int)(t / n2), row = (int)(t % n2);
-  cx<float> s = czero<float>();
+enum MgCoarseRed { MG_CR_NONE = 0, MG_CR_ALPHA = 1, MG_CR_OMEGA = 2 };
+
+// y = D_c x (or b - D_c x); with a fused reduction for the coarse BiCGStab:
+// MG_CR_ALPHA <rhat, y>, MG_CR_OMEGA (<y, x>, |y|^2).  Coarse sites of a
+// converged solve (red.sc->done) are skipped.
+// Row `row` of coarse site X: N2 > 0 fixes the row length at compile time
+// (the column loop unrolls into independent loads); N2 = 0 reads it from a.
+BR_D float2 coarse_entry(const float2* p) { return __ldg(p); }
+BR_D float2 coarse_entry(const __half2* p) { return __half22float2(__ldg(p)); }
+
+template <int N2, class E>
+BR_D cx<float> coarse_row(const MgCoarseArgs& a, const E* Dc, int X, int row) {
+  const int n2 = N2 > 0 ? N2 : a.n2;
+  cx<float> s0 = czero<float>(), s1 = czero<float>();
   for (int d = 0; d < 9; ++d) {
-    const int Y = d == 0 ? X : mg_block_nbr(a.m, X, (d - 1) >> 1, ((d - 1) & 1) ? -1 : 1);
-    const float2* M = a.Dc + ((long)X * 9 + d) * n2 * n2 + row;
+    const int Y = __ldg(a.nbr + X * 9 + d);
+    const E* M = Dc + ((long)X * 9 + d) * n2 * n2 + row;
     const float2* xv = a.x + (long)Y * n2;
-    for (int col = 0; col < n2; ++col) {
-      const float2 m = M[(long)col * n2], v = xv[col];
-      s = s + cx<float>{m.x, m.y} * cx<float>{v.x, v.y};
+    if constexpr (N2 > 0) {
+#pragma unroll
+      for (int col = 0; col < N2; col += 2) {
+        const float2 m0 = coarse_entry(M + (long)col * N2), v0 = __ldg(xv + col);
+        const float2 m1 = coarse_entry(M + (long)(col + 1) * N2), v1 = __ldg(xv + col + 1);
+        s0 = s0 + cx<float>{m0.x, m0.y} * cx<float>{v0.x, v0.y};
+        s1 = s1 + cx<float>{m1.x, m1.y} * cx<float>{v1.x, v1.y};
+      }
+    } else {
+      for (int col = 0; col < n2; ++col) {
+        const float2 m = coarse_entry(M + (long)col * n2), v = __ldg(xv + col);
+        s0 = s0 + cx<float>{m.x, m.y} * cx<float>{v.x, v.y};
+      }
     }
   }
-  if (a.b) {
-    const float2 bb = a.b[t];
-    s = cx<float>{bb.x, bb.y} - s;
+  return s0 + s1;
+}
+
+template <int RED, int N2>
+__global__ void __launch_bounds__(256) mg_coarse_kernel(const MgCoarseArgs a) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n2 = N2 > 0 ? N2 : a.n2;
+  const bool skip = RED != MG_CR_NONE && a.red.sc != nullptr && a.red.sc[0].done != RUNNING;
+  double rv[3] = {0.0, 0.0, 0.0};
+  if (!skip && t < (long)a.m.nblocks * n2) {
+    const int X = (int)(t / n2), row = (int)(t % n2);
+    cx<float> s = a.Dch ? coarse_row<N2>(a, a.Dch, X, row) : coarse_row<N2>(a, a.Dc, X, row);
+    if (a.b) {
+      const float2 bb = a.b[t];
+      s = cx<float>{bb.x, bb.y} - s;
+    }
+    a.y[t] = make_float2(s.r, s.i);
+    if (RED == MG_CR_ALPHA) {
+      const float2 h = a.rhat[t];
+      const cx<float> d = cmul_conj(cx<float>{h.x, h.y}, s);
+      rv[0] = d.r;
+      rv[1] = d.i;
+    } else if (RED == MG_CR_OMEGA) {
+      const float2 xv = a.x[t];
+      const cx<float> d = cmul_conj(s, cx<float>{xv.x, xv.y});
+      rv[0] = d.r;
+      rv[1] = d.i;
+      rv[2] = (double)s.r * s.r + (double)s.i * s.i;
+    }
   }
-  a.y[t] = make_float2(s.r, s.i);
+  if (RED == MG_CR_ALPHA) reduce_finalize<2>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
+  if (RED == MG_CR_OMEGA) reduce_finalize<3>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
+}
+
+// Coarse BiCGStab vector steps with the scalars on the device (BiCGScalars,
+// the finalizers of reduce.cuh): INIT x = 0, r = rhat = p = b, v = 0, |b|^2;
+// S s = r - alpha v; XR x += alpha p + omega s, r = s - omega t, (<rhat, r>,
+// |r|^2); P p = r + beta (p - omega v).
+enum MgCBicgOp { MG_CB_INIT = 0, MG_CB_S = 1, MG_CB_XR = 2, MG_CB_P = 3 };
+struct MgCBicgArgs {
+  long n;
+  float2 *x, *r, *rhat, *p, *v, *s, *t;
+  const float2* b;
+  RedArgs red;
+};
+
+template <int OP>
+__global__ void __launch_bounds__(256) mg_cbicg_kernel(const MgCBicgArgs a) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const BiCGScalars* q = a.red.sc;
+  const bool skip = OP != MG_CB_INIT && q->done != RUNNING;
+  double rv[3] = {0.0, 0.0, 0.0};
+  if (!skip && i < a.n) {
+    auto c = [](float2 f) { return cx<float>{f.x, f.y}; };
+    auto f2 = [](cx<float> v) { return make_float2(v.r, v.i); };
+    if (OP == MG_CB_INIT) {
+      const float2 bb = a.b[i];
+      a.x[i] = make_float2(0.f, 0.f);
+      a.r[i] = bb;
+      a.rhat[i] = bb;
+      a.p[i] = bb;
+      a.v[i] = make_float2(0.f, 0.f);
+      rv[0] = (double)bb.x * bb.x + (double)bb.y * bb.y;
+    } else if (OP == MG_CB_S) {
+      const cx<float> al{(float)q->alpha_r, (float)q->alpha_i};
+      a.s[i] = f2(c(a.r[i]) - al * c(a.v[i]));
+    } else if (OP == MG_CB_XR) {
+      const cx<float> al{(float)q->alpha_r, (float)q->alpha_i}, om{(float)q->omega_r, (float)q->omega_i};
+      const cx<float> sv = c(a.s[i]);
+      a.x[i] = f2(c(a.x[i]) + al * c(a.p[i]) + om * sv);
+      const cx<float> rn = sv - om * c(a.t[i]);
+      a.r[i] = f2(rn);
+      const cx<float> d = cmul_conj(c(a.rhat[i]), rn);
+      rv[0] = d.r;
+      rv[1] = d.i;
+      rv[2] = (double)rn.r * rn.r + (double)rn.i * rn.i;
+    } else {
+      const cx<float> be{(float)q->beta_r, (float)q->beta_i}, om{(float)q->omega_r, (float)q->omega_i};
+      a.p[i] = f2(c(a.r[i]) + be * (c(a.p[i]) - om * c(a.v[i])));
+    }
+  }
+  if (OP == MG_CB_INIT) reduce_finalize<1>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
+  if (OP == MG_CB_XR) reduce_finalize<3>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
 }
 
 // SAP block solve: `steps` minimal-residual steps on D_B e = r_B for every

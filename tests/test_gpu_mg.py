@@ -44,8 +44,10 @@ def case(api):
     op = api.make_op("clover", kappa, csw)
     L = api.Lattice(dims)
     L.upload(U, op)
+    # FP32 coarse operator in the coarse solver, so that the cycle can be
+    # compared with the oracle's at a tight coarse tolerance
     mg = api.Multigrid(L, op, api.make_mg_params(block=block, nvec=nv, sap_cycles=2, mr_steps=4, coarse_tol=1e-6,
-                                                 coarse_maxiter=1000), null_vectors=vs)
+                                                 coarse_maxiter=1000, coarse_half=0), null_vectors=vs)
     yield dict(lat=lat, U=U, orc=orc, op=op, L=L, mg=mg, gen=gen)
     mg.close()
     L.close()
