@@ -29,7 +29,10 @@ Moebius domain-wall operator (Ls = 16, M5 = 1.8, b = 1.5, c = 0.5,
 m_f = 0.01): a step is one mixed-precision CG solve on the normal equations
 of the even-odd system (FP32 inner, FP64 defect correction, 1e-10), beside
 D_eo alone and a plain FP64 CG solve.  ``--workload staggered_64x64x64x64``
-does the same for the staggered operator (m = 0.05, CG on the even system).
+does the same for the staggered operator (m = 0.05, CG on the even system);
+``--workload mg_clover_32x32x32x64`` times the two-level multigrid solver
+(setup reported separately) against the mixed BiCGStab on the same
+near-critical clover system, for one and for twelve equations.
 """
 
 from __future__ import annotations
@@ -1036,6 +1039,180 @@ def run_staggered(args):
         dist.destroy_process_group()
 
 
+MG_PARAMS = dict(nvec=12, setup_steps=3, sap_cycles=3, mr_steps=4, coarse_tol=5e-2)
+
+
+def run_mg(args):
+    """Two-level multigrid (FBiCGStab + SAP + coarse BiCGStab) on the 32^3x64
+    clover field near its critical kappa: setup, solve steps, the mixed
+    BiCGStab on the same system, 1 and 12 equations including setup."""
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__ as g
+
+    if rank == 0:
+        g.build()
+    if world > 1:
+        dist.barrier()
+    from ctypes import byref, c_void_p
+
+    import synth
+    from paper_2303_05883_gb300 import _abi, api
+
+    w = synth.WORKLOADS[args.workload]
+    U = w.gauge()
+    b_host = w.sources()[0]
+    b_dev = torch.from_numpy(b_host).to(f"cuda:{local}")
+    x_dev = torch.zeros_like(b_dev)
+    op = api.make_op("clover", w.kappa, w.csw, w.bc)
+    L = api.Lattice(w.dims)
+    L.upload(U, op)
+    h = L.handle
+    stream = L.stream
+    lib = _abi.load()
+    peak, peak_kind = peaks()
+    solver = api.make_solver(tol=w.tol, max_iter=1000)
+    t0 = time.perf_counter()
+    mg = api.Multigrid(L, op, api.make_mg_params(**MG_PARAMS))
+    setup_s = time.perf_counter() - t0
+
+    def mg_solve():
+        x_dev.zero_()
+        torch.cuda.current_stream().synchronize()
+        info = (_abi.bridge_info * 1)()
+        _abi.check(lib.bridge_mg_solve_dev(mg.handle, byref(solver), c_void_p(b_dev.data_ptr()),
+                                           c_void_p(x_dev.data_ptr()), 1, info), "bridge_mg_solve_dev")
+        return info[0]
+
+    for _ in range(args.warmup):
+        mg_solve()
+    torch.cuda.synchronize()
+    api.bridge_stats_reset(h)
+    l0 = api.bridge_launch_count()
+    c0 = mg.counters()
+    infos, host_s = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            t1 = time.perf_counter()
+            infos.append(mg_solve())
+            host_s.append(time.perf_counter() - t1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = api.bridge_launch_count() - l0
+    c1 = mg.counters()
+    st = api.bridge_stats(h)
+    total_bytes = sum(v["bytes"] for v in st.values())
+    ms, total_bytes = aggregate_ranks(ms, total_bytes, device=f"cuda:{local}")
+    value = total_bytes / (ms * 1e-3) / 1e9
+    res = max(i.true_rel_residual for i in infos)
+
+    # ---- one event-profiled solve
+    api.bridge_stats_reset(h)
+    api.bridge_profile(h, True)
+    mg_solve()
+    torch.cuda.synchronize()
+    api.bridge_profile(h, False)
+    pst = api.bridge_stats(h)
+    step_ms_prof = sum(v["ms"] for v in pst.values())
+    dom = max(pst, key=lambda k: pst[k]["ms"])
+    d = pst[dom]
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    roofline = {
+        "bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+        "frac": achieved / peak, "traffic": traffic_for(dom, args.workload),
+        "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]), "launches": d["launches"],
+        "avg_launch_us": 1e3 * d["ms"] / max(1, d["launches"]),
+        "share_of_step": d["ms"] / step_ms_prof if step_ms_prof else None,
+    }
+    shares = {k: round(v["ms"] / step_ms_prof, 4) for k, v in pst.items() if v["ms"] > 0}
+    per_kernel = {k: {"launches": v["launches"], "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9}
+                  for k, v in pst.items() if v["ms"] > 0}
+
+    # ---- the mixed BiCGStab on the same system (the paper's comparison)
+    mixed = api.make_solver(tol=w.tol, inner_prec="f32", max_iter=20000)
+    for _ in range(2):
+        x_dev.zero_()
+        torch.cuda.synchronize()
+        info = (_abi.bridge_info * 1)()
+        t1 = time.perf_counter()
+        _abi.check(lib.bridge_solve_dev(h, byref(op), byref(mixed), c_void_p(b_dev.data_ptr()),
+                                        c_void_p(x_dev.data_ptr()), 1, info), "bridge_solve_dev")
+        bicg_s = time.perf_counter() - t1
+    mg_s = statistics.median(host_s)
+    solve = {
+        "mg_setup_s": setup_s, "mg_solve_ms": ms / args.steps, "mg_outer_passes": statistics.median(i.outer_iters for i in infos),
+        "mg_fbicgstab_iters": statistics.median(i.inner_iters for i in infos),
+        "coarse_iters_per_solve": (c1[1] - c0[1]) / max(1, c1[0] - c0[0]),
+        "mg_true_rel_residual": res, "bicgstab_ms": bicg_s * 1e3, "bicgstab_iters": info[0].inner_iters,
+        "speedup_1_solve_excl_setup": bicg_s / mg_s,
+        "one_equation_s": {"mg_incl_setup": setup_s + mg_s, "bicgstab": bicg_s},
+        "twelve_equations_s": {"mg_incl_setup": setup_s + 12 * mg_s, "bicgstab": 12 * bicg_s},
+        "params": MG_PARAMS,
+    }
+
+    # ---- end to end through bridge_mg_solve with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        b_pin = torch.from_numpy(b_host).pin_memory()
+        x_pin = torch.zeros_like(b_pin).pin_memory()
+        import ctypes
+
+        dp = ctypes.POINTER(ctypes.c_double)
+        bp, xp = ctypes.cast(b_pin.data_ptr(), dp), ctypes.cast(x_pin.data_ptr(), dp)
+        ts = []
+        for _ in range(args.steps):
+            x_pin.zero_()
+            info = (_abi.bridge_info * 1)()
+            t1 = time.perf_counter()
+            _abi.check(lib.bridge_mg_solve(mg.handle, byref(solver), bp, xp, 1, info), "bridge_mg_solve")
+            ts.append(time.perf_counter() - t1)
+        e2e = {"value": (total_bytes / args.steps) / statistics.median(ts) / 1e9 if world == 1 else None,
+               "unit": UNIT, "h2d_bytes_per_step": 2 * b_host.nbytes, "d2h_bytes_per_step": b_host.nbytes,
+               "ms_per_step": 1e3 * statistics.median(ts)}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        v, secs, cores = oracle_sample(w, U, b_host, 4 * args.oracle_sites, seed=0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"FP64 numpy oracle: clover D at {4 * args.oracle_sites} random sites of the {args.workload} "
+                         f"lattice ({secs:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f16 coarse+f64", "data": "synthetic",
+            "config": {
+                "workload": args.workload, "lattice": "x".join(map(str, w.dims)),
+                "operator": f"clover, kappa={w.kappa}, c_sw={w.csw}, bc={list(w.bc)}",
+                "links": f"exp({w.eps} i A), seed {w.seed}", "source": "gaussian", "nrhs": 1,
+                "solver": "two-level multigrid: FBiCGStab (f32 passes, f64 defect correction), SAP smoother, "
+                          "coarse BiCGStab; blocks 4^4",
+                "tol": w.tol, "l2": "inputs larger than L2",
+                "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            },
+            "roofline": roofline, "kernel_shares": shares, "per_kernel": per_kernel, "solve": solve, "e2e": e2e,
+            "gpu_launches": launches, "true_rel_residual": res, "clocks": clk.summary(), "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    mg.close()
+    L.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_serving(args):
     """The request stream alone: lattices {8^4, 16^4, 24^3x48, 32^3x64},
     kappa in [0.11, 0.13], 1-12 right-hand sides, Wilson or clover."""
@@ -1085,6 +1262,8 @@ def main():
         run_mobius(args)
     elif args.workload.startswith("staggered"):
         run_staggered(args)
+    elif args.workload.startswith("mg_"):
+        run_mg(args)
     else:
         run_ours(args)
 

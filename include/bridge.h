@@ -335,6 +335,9 @@ int bridge_mg_destroy(bridge_mg mg);
  * FBiCGStab iterations in inner_iters, restarts, true residual, seconds.
  * Synchronous. */
 int bridge_mg_solve(bridge_mg mg, const bridge_solver* s, const double* b, double* x, int nrhs, bridge_info* info);
+/* The same on device buffers (queued on the lattice stream; returns when done). */
+int bridge_mg_solve_dev(bridge_mg mg, const bridge_solver* s, const double* b_dev, double* x_dev, int nrhs,
+                        bridge_info* info);
 
 /* Pieces of the cycle, on host canonical buffers, for tests.  Coarse
  * vectors are [block][chirality][vector] complex ([re, im] doubles), blocks

@@ -126,6 +126,7 @@ SIGNATURES = {
     "bridge_mg_setup": (c_int, [_h, POINTER(bridge_op), POINTER(bridge_mg_params), _dp, POINTER(_h)]),
     "bridge_mg_destroy": (c_int, [_h]),
     "bridge_mg_solve": (c_int, [_h, POINTER(bridge_solver), _dp, _dp, c_int, POINTER(bridge_info)]),
+    "bridge_mg_solve_dev": (c_int, [_h, POINTER(bridge_solver), c_void_p, c_void_p, c_int, POINTER(bridge_info)]),
     "bridge_mg_apply": (c_int, [_h, c_int, _dp, _dp]),
     "bridge_mg_coarse_matrix": (c_int, [_h, _dp]),
     "bridge_mg_info": (c_int, [_h, POINTER(c_int), POINTER(c_int)]),

@@ -786,6 +786,26 @@ int bridge_mg_solve(bridge_mg g, const bridge_solver* s, const double* b, double
   BR_MG_END
 }
 
+int bridge_mg_solve_dev(bridge_mg g, const bridge_solver* s, const double* b, double* x, int nrhs, bridge_info* info) {
+  BR_MG_BEGIN
+  BR_CHECK(g && s && b && x, BRIDGE_EINVAL, "NULL argument");
+  BR_CHECK(s->tol > 0 && std::isfinite(s->tol), BRIDGE_EINVAL, "tol must be > 0");
+  BR_CHECK(nrhs >= 0, BRIDGE_EINVAL, "nrhs < 0");
+  bridge_lattice_s* L = g->L;
+  std::lock_guard<std::mutex> lk(L->api_mu);
+  const size_t n = (size_t)L->V * 24;
+  int status = BRIDGE_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    bridge_info inf;
+    mg_solve_one(g, b + n * r, x + n * r, *s, inf);
+    if (info) info[r] = inf;
+    if (inf.status != BRIDGE_OK) status = inf.status;
+  }
+  if (status != BRIDGE_OK) set_error(status, "multigrid solve did not reach tolerance");
+  return status;
+  BR_MG_END
+}
+
 int bridge_mg_apply(bridge_mg g, int which, const double* in, double* out) {
   BR_MG_BEGIN
   BR_CHECK(g && in && out, BRIDGE_EINVAL, "NULL argument");

@@ -235,6 +235,9 @@ WORKLOADS = {
     "clover_24x24x24x48_12rhs": Workload(
         "clover_24x24x24x48_12rhs", (24, 24, 24, 48), "clover", 0.125, 1.0, 0.2, 4, 12, "point", 1e-10, inner="f16"
     ),
+    # The 32^3x64 clover field near its critical kappa (BiCGStab needs ~500
+    # iterations): the multigrid solver's workload.
+    "mg_clover_32x32x32x64": Workload("mg_clover_32x32x32x64", (32, 32, 32, 64), "clover", 0.1275, 1.0, 0.2, 2, 1, "gaussian", 1e-10),
     # Twelve point sources on 48^3x96 clover with half-precision storage.
     "clover_48x48x48x96_12rhs": Workload(
         "clover_48x48x48x96_12rhs", (48, 48, 48, 96), "clover", 0.125, 1.0, 0.2, 3, 12, "point", 1e-10, inner="f16"
