@@ -756,11 +756,13 @@ def run_mobius(args):
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")
         e0.record(stream)
         for _ in range(args.steps):
             infos.append(solve_dev(solver))
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     launches = api.bridge_launch_count() - l0
     st = api.bridge_stats(h)
@@ -954,11 +956,13 @@ def run_staggered(args):
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")
         e0.record(stream)
         for _ in range(args.steps):
             infos.append(solve_dev(solver))
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     launches = api.bridge_launch_count() - l0
     st = api.bridge_stats(h)
@@ -1102,6 +1106,7 @@ def run_mg(args):
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")
         e0.record(stream)
         for _ in range(args.steps):
             t1 = time.perf_counter()
@@ -1109,6 +1114,7 @@ def run_mg(args):
             host_s.append(time.perf_counter() - t1)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     launches = api.bridge_launch_count() - l0
     c1 = mg.counters()
