@@ -347,7 +347,9 @@ enum bridge_mg_apply_op {
   BRIDGE_MG_PROLONG = 1,  /* coarse in -> fine out: P in */
   BRIDGE_MG_COARSE = 2,   /* coarse -> coarse: D_c in (the FP32 coarse operator) */
   BRIDGE_MG_SAP = 3,      /* fine -> fine: sap_cycles SAP cycles on D x = in from x = 0 */
-  BRIDGE_MG_CYCLE = 4     /* fine -> fine: the preconditioner */
+  BRIDGE_MG_CYCLE = 4,    /* fine -> fine: the preconditioner */
+  BRIDGE_MG_COARSE_HALF = 5 /* coarse -> coarse: D_c in with the FP16 copy the coarse solver uses
+                               (EINVAL when the setup ran with coarse_half = 0) */
 };
 int bridge_mg_apply(bridge_mg mg, int which, const double* in, double* out);
 /* The coarse operator: [block][coupling 9][column][row] complex doubles;

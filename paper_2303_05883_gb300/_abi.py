@@ -84,6 +84,7 @@ class bridge_mg_params(ctypes.Structure):
 
 
 BRIDGE_MG_RESTRICT, BRIDGE_MG_PROLONG, BRIDGE_MG_COARSE, BRIDGE_MG_SAP, BRIDGE_MG_CYCLE = 0, 1, 2, 3, 4
+BRIDGE_MG_COARSE_HALF = 5
 
 
 class bridge_kstat(ctypes.Structure):

@@ -58,6 +58,41 @@ BR_HD cx<R> cmul_conj(cx<R> a, cx<R> b) {  // conj(a) * b
 template <class R>
 BR_HD cx<R> czero() { return {R(0), R(0)}; }
 
+// Fused multiply-add chains: acc + a b, acc + conj(a) b and acc + s a (s
+// real) with every product term fused into the running sum, so a complex
+// multiply-accumulate is four FMAs instead of two products, two FMAs and two
+// adds.
+template <class R>
+BR_HD R fmar(R a, R b, R c) {
+  if constexpr (sizeof(R) == sizeof(double)) {
+    return fma(a, b, c);
+  } else {
+    return fmaf(a, b, c);
+  }
+}
+template <class R>
+BR_HD cx<R> cfma(cx<R> a, cx<R> b, cx<R> acc) {
+  return {fmar(a.r, b.r, fmar(-a.i, b.i, acc.r)), fmar(a.r, b.i, fmar(a.i, b.r, acc.i))};
+}
+template <class R>
+BR_HD cx<R> cfma_conj(cx<R> a, cx<R> b, cx<R> acc) {
+  return {fmar(a.r, b.r, fmar(a.i, b.i, acc.r)), fmar(a.r, b.i, fmar(-a.i, b.r, acc.i))};
+}
+template <class R>
+BR_HD cx<R> caxpy(R s, cx<R> a, cx<R> acc) {
+  return {fmar(s, a.r, acc.r), fmar(s, a.i, acc.i)};
+}
+// One row of an SU(3) product: a0 b0 + a1 b1 + a2 b2, and the row of the
+// adjoint, conj(a0) b0 + conj(a1) b1 + conj(a2) b2.
+template <class R>
+BR_HD cx<R> crow3(cx<R> a0, cx<R> a1, cx<R> a2, const cx<R> b[3]) {
+  return cfma(a2, b[2], cfma(a1, b[1], a0 * b[0]));
+}
+template <class R>
+BR_HD cx<R> crow3_conj(cx<R> a0, cx<R> a1, cx<R> a2, const cx<R> b[3]) {
+  return cfma_conj(a2, b[2], cfma_conj(a1, b[1], cmul_conj(a0, b[0])));
+}
+
 // ------------------------------------------------------------ precision
 template <int P>
 struct Tr;
@@ -390,8 +425,8 @@ BR_D void hermitian6_apply(const R a[36], const cx<R> x[6], cx<R> y[6]) {
 #pragma unroll
     for (int c = 0; c < r; ++c) {
       cx<R> arc = {o[2 * k], o[2 * k + 1]};
-      y[r] = y[r] + arc * x[c];
-      y[c] = y[c] + cmul_conj(arc, x[r]);
+      y[r] = cfma(arc, x[c], y[r]);
+      y[c] = cfma_conj(arc, x[r], y[c]);
       ++k;
     }
   }

@@ -137,9 +137,9 @@ BR_D void hop_one(const char* in, const char* lb, long vh, uint32_t nb, uint32_t
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       if (FWD)
-        u[k][r] = U.m[r][0] * h[k][0] + U.m[r][1] * h[k][1] + U.m[r][2] * h[k][2];
+        u[k][r] = crow3(U.m[r][0], U.m[r][1], U.m[r][2], h[k]);
       else
-        u[k][r] = cmul_conj(U.m[0][r], h[k][0]) + cmul_conj(U.m[1][r], h[k][1]) + cmul_conj(U.m[2][r], h[k][2]);
+        u[k][r] = crow3_conj(U.m[0][r], U.m[1][r], U.m[2][r], h[k]);
     }
   reconstruct<R, MU, FWD>(u, acc);
 }
@@ -308,9 +308,9 @@ BR_D void hop_one_mr(const char* in, long in_rs, const bool live[NR], const char
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         if (FWD)
-          u[k][q] = U.m[q][0] * h[k][0] + U.m[q][1] * h[k][1] + U.m[q][2] * h[k][2];
+          u[k][q] = crow3(U.m[q][0], U.m[q][1], U.m[q][2], h[k]);
         else
-          u[k][q] = cmul_conj(U.m[0][q], h[k][0]) + cmul_conj(U.m[1][q], h[k][1]) + cmul_conj(U.m[2][q], h[k][2]);
+          u[k][q] = crow3_conj(U.m[0][q], U.m[1][q], U.m[2][q], h[k]);
       }
     reconstruct<T, MU, FWD>(u, acc[r]);
   }

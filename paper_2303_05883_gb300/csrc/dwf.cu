@@ -208,8 +208,15 @@ long site_bytes(int prec) { return prec == P_F64 ? 192 : 96; }
 long link_bytes(int prec) { return prec == P_F64 ? 144 : 48; }
 
 // Threads per block are ns * Ls rounded up to whole warps, ns four-dimensional
-// sites per block; the tuner picks 128 or 256 (FP64: 128).
-int sites_per_block(int threads, int Ls) { return std::max(1, threads / Ls); }
+// sites per block; the tuner picks 128 or 256 (FP64: 128).  ns is capped so
+// that the largest hop kernel (two staged operands and two dense s-matrices)
+// fits in the 227 KB of shared memory a block may use.
+int sites_per_block(int threads, int Ls, int prec) {
+  const long R = prec == P_F64 ? 8 : 4;
+  const long per_site = dwf_hop_smem(prec, Ls, 1, true, true, false) - 2L * 2 * Ls * Ls * R;
+  const long cap = std::max(1L, (232448 - 2L * 2 * Ls * Ls * R) / per_site);
+  return (int)std::max(1L, std::min<long>(threads / Ls, cap));
+}
 constexpr int kMinThreads = 128;
 
 std::string dims_tag(const bridge_lattice_s* L) {
@@ -260,7 +267,7 @@ void run_dwf_hop(bridge_lattice_s* L, const DwfSet& set, const bridge_op& op, co
   a.out_parity = c.out_parity;
   a.Ls = c.Ls;
   a.nrhs = c.nrhs;
-  a.ns = sites_per_block(sh.block, c.Ls);
+  a.ns = sites_per_block(sh.block, c.Ls, c.prec);
   a.nsb = (int)((L->vh + a.ns - 1) / a.ns);
   a.scale = c.scale;
   a.scalef = (float)c.scale;
@@ -337,7 +344,7 @@ void run_dwf_mix(bridge_lattice_s* L, const DwfSet& set, const DwfMix& c, cudaSt
   a.vh = (uint32_t)L->vh;
   a.Ls = c.Ls;
   a.nrhs = c.nrhs;
-  a.ns = sites_per_block(sh.block, c.Ls);
+  a.ns = sites_per_block(sh.block, c.Ls, c.prec);
   a.nsb = (int)((L->vh + a.ns - 1) / a.ns);
   a.in_bs = c.in_bs;
   a.out_bs = c.out_bs;
@@ -566,7 +573,7 @@ int dwf_solve(bridge_lattice_s* L, const bridge_op& op, const bridge_solver& prm
 
   // CG scalars and reduction scratch of this solve (sized for the smallest
   // blocks any launch shape uses)
-  const int ns = sites_per_block(kMinThreads, Ls);
+  const int ns = sites_per_block(kMinThreads, Ls, P_F64);  // the fewest sites per block of any launch
   const long nsb = (L->vh + ns - 1) / ns;
   DevBuf sc(sizeof(CGScalars) * nrhs), partials(sizeof(double) * 4 * nsb * nrhs), counter(256);
   DevBuf mask((size_t)nq * sizeof(int)), resbuf(sizeof(double) * 4 * nrhs * 2);
@@ -868,7 +875,7 @@ void tune_dwf_kernels(bridge_lattice_s* L, const bridge_op& op, int prec, int nr
   Field ff = make_field(P_F32, BRIDGE_FULL, nq, L->vh), ff2 = make_field(P_F32, BRIDGE_FULL, nq, L->vh);
   uint32_t seed = 11;
   for (const Field* f : {&fe, &fe2, &fe3, &fe4, &fx, &fo, &ff, &ff2}) fill_scratch(*f, seed++, st);
-  const long nsb = (L->vh + sites_per_block(kMinThreads, Ls) - 1) / sites_per_block(kMinThreads, Ls);
+  const long nsb = (L->vh + sites_per_block(kMinThreads, Ls, P_F64) - 1) / sites_per_block(kMinThreads, Ls, P_F64);
   DevBuf sc(sizeof(CGScalars) * nrhs), partials(sizeof(double) * 4 * nsb * nrhs), counter(256);
   BR_CUDA(cudaMemsetAsync(counter.ptr, 0, 256, st));
   std::vector<CGScalars> hs(nrhs);

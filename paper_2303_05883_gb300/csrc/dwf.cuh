@@ -197,9 +197,9 @@ BR_D void smix_row(const R* mat, const cx<R>* sh, int Ls, int ns, int s, int sl,
     const R a = rp[t], b = rm[t];
     const cx<R>* v = sh + (long)t * 12 * ns + sl;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) res[k] = res[k] + a * v[k * ns];
+    for (int k = 0; k < 6; ++k) res[k] = caxpy(a, v[k * ns], res[k]);
 #pragma unroll
-    for (int k = 6; k < 12; ++k) res[k] = res[k] + b * v[k * ns];
+    for (int k = 6; k < 12; ++k) res[k] = caxpy(b, v[k * ns], res[k]);
   }
 }
 
@@ -237,9 +237,9 @@ BR_D void hop_shared(const char* in, long vh, uint32_t nbw, const cx<typename Tr
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       if (FWD)
-        u[k][r] = U[3 * r] * h[k][0] + U[3 * r + 1] * h[k][1] + U[3 * r + 2] * h[k][2];
+        u[k][r] = crow3(U[3 * r], U[3 * r + 1], U[3 * r + 2], h[k]);
       else
-        u[k][r] = cmul_conj(U[r], h[k][0]) + cmul_conj(U[3 + r], h[k][1]) + cmul_conj(U[6 + r], h[k][2]);
+        u[k][r] = crow3_conj(U[r], U[3 + r], U[6 + r], h[k]);
     }
   reconstruct<R, MU, FWD>(u, acc);
 }

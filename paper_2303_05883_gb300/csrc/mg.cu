@@ -22,7 +22,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "mg.cuh"
@@ -61,9 +64,23 @@ __global__ void k_mg_scatter_column(const float2* tmp, float2* Dc, int nblocks, 
   Dc[(((long)X * 9 + mode) * n2 + col) * n2 + row] = tmp[t];
 }
 
-__global__ void k_mg_to_half(const float2* in, __half2* out, long n) {
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    out[i] = __float22half2_rn(in[i]);
+// FP16 copy of Dc[m][col][row] (m = X * 9 + d); with tiled != 0 in the
+// layout coarse_row_h4 reads, out[((m * (n2 / 4) + col / 4) * n2 + row) * 4 + col % 4].
+__global__ void k_mg_to_half(const float2* in, __half2* out, long nmat, int n2, int tiled) {
+  const long n = nmat * n2 * n2;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    long src = i;
+    if (tiled) {
+      const int j = (int)(i % 4);
+      long t = i / 4;
+      const int row = (int)(t % n2);
+      t /= n2;
+      const int g = (int)(t % (n2 / 4));
+      const long m = t / (n2 / 4);
+      src = (m * n2 + 4 * g + j) * n2 + row;
+    }
+    out[i] = __float22half2_rn(in[src]);
+  }
 }
 
 unsigned grid_for(long n, int threads = 256) {
@@ -92,6 +109,7 @@ struct bridge_mg_s {
   std::unique_ptr<PinnedBuf> hcsc;
   long coarse_iters = 0, coarse_solves = 0;
   Field r32, x32, res32;  // fine FP32 work fields of the cycle
+  int sap_clover_smem = 1;  // SAP kernel variant (picked by timing at setup)
   float2* cv(int k) const { return reinterpret_cast<float2*>(cvec->ptr) + (long)k * nc; }
 };
 
@@ -173,7 +191,8 @@ void prolong_to(bridge_mg_s* g, const float2* c, const Field& fine, bool add) {
 }
 template <int RED>
 void launch_coarse_red(int n2, const MgCoarseArgs& a, unsigned grid, cudaStream_t st) {
-  switch (n2) {  // row lengths of 4, 8, 12, 16 and 24 null vectors unroll at compile time
+  // row lengths of 4, 8, 12, 16 and 24 null vectors (mg_coarse_unrolled) unroll at compile time
+  switch (n2) {
     case 8: mg_coarse_kernel<RED, 8><<<grid, 256, 0, st>>>(a); break;
     case 16: mg_coarse_kernel<RED, 16><<<grid, 256, 0, st>>>(a); break;
     case 24: mg_coarse_kernel<RED, 24><<<grid, 256, 0, st>>>(a); break;
@@ -196,6 +215,8 @@ void coarse_apply(bridge_mg_s* g, const float2* x, float2* y, const float2* b = 
   a.n2 = g->n2;
   a.Dc = reinterpret_cast<const float2*>(g->Dc->ptr);
   a.Dch = (half && g->Dch) ? reinterpret_cast<const __half2*>(g->Dch->ptr) : nullptr;
+  // the tiled FP16 rows read x four entries (32 bytes) at a time
+  if (a.Dch && mg_coarse_unrolled(g->n2) && (reinterpret_cast<uintptr_t>(x) & 15) != 0) a.Dch = nullptr;
   a.nbr = reinterpret_cast<const int*>(g->cnbr->ptr);
   a.x = x;
   a.b = b;
@@ -308,6 +329,20 @@ void fine_residual32(bridge_mg_s* g, const Field& b, const Field& x, const Field
   }
 }
 
+// Raise the dynamic shared memory limit of a SAP kernel variant (once per
+// device and size; at most 256 sites x 672 bytes = 168 KB).
+template <bool CS>
+void allow_sap_smem(long smem) {
+  static std::mutex mu;
+  static std::map<int, long> done;
+  int dev = 0;
+  BR_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev] >= smem) return;
+  BR_CUDA(cudaFuncSetAttribute(mg_sap_kernel<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  done[dev] = smem;
+}
+
 void sap_half_sweep(bridge_mg_s* g, const Field& r, const Field& x, int colour) {
   MgSapArgs a;
   std::memset(static_cast<void*>(&a), 0, sizeof(a));
@@ -320,13 +355,61 @@ void sap_half_sweep(bridge_mg_s* g, const Field& r, const Field& x, int colour) 
   a.field_block = r.block;
   a.gauge = gauge_ptr(g->L, P_F32);
   a.clov = clover_ptr(g->L, *g->clov, P_F32, false);
-  const long smem = 12L * g->m.bsites * 8;
+  const bool cs = g->sap_clover_smem != 0;
+  const long smem = mg_sap_smem(g->m.bsites, cs);
+  if (cs)
+    allow_sap_smem<true>(smem);
+  else
+    allow_sap_smem<false>(smem);
   const double sites = (double)g->L->V / 2;
-  const double bytes = sites * (96 + 2 * 96 + 8 * 48 + 288);
+  // r, x in and out, the clover term, and the forward links of the hops that stay in the block
+  double inner = 0;
+  for (int k = 0; k < 4; ++k) inner += (double)(g->m.b[k] - 1) / g->m.b[k];
+  const double bytes = sites * (96 + 2 * 96 + 288 + 48 * inner);
   note_launch(g->L, K_MG_SAP, bytes, sites * g->prm.mr_steps * 1900.0, stream_of(g), true);
-  mg_sap_kernel<<<g->m.nblocks, block_threads(g), (size_t)smem, stream_of(g)>>>(a);
+  if (cs)
+    mg_sap_kernel<true><<<g->m.nblocks / 2, block_threads(g), (size_t)smem, stream_of(g)>>>(a);
+  else
+    mg_sap_kernel<false><<<g->m.nblocks / 2, block_threads(g), (size_t)smem, stream_of(g)>>>(a);
   note_launch(g->L, K_MG_SAP, bytes, 0, stream_of(g), false);
   BR_CUDA(cudaGetLastError());
+}
+
+// Time both SAP kernel variants on a scratch residual (three half sweeps
+// each, after one untimed) and keep the faster.  BRIDGE_MG_SAP=0 or 1 in the
+// environment fixes the variant instead (1: clover term staged).
+void pick_sap_variant(bridge_mg_s* g) {
+  if (const char* e = std::getenv("BRIDGE_MG_SAP")) {
+    if (e[0] == '0' || e[0] == '1') {
+      g->sap_clover_smem = e[0] - '0';
+      return;
+    }
+  }
+  cudaStream_t st = stream_of(g);
+  fill_scratch(g->r32, 7, st);
+  BR_CUDA(cudaMemsetAsync(g->x32.buf->ptr, 0, g->x32.buf->bytes, st));
+  cudaEvent_t e0, e1;
+  BR_CUDA(cudaEventCreate(&e0));
+  BR_CUDA(cudaEventCreate(&e1));
+  float best = 0.f;
+  int pick = 1;
+  for (int v = 1; v >= 0; --v) {
+    g->sap_clover_smem = v;
+    sap_half_sweep(g, g->r32, g->x32, 0);
+    BR_CUDA(cudaEventRecord(e0, st));
+    for (int k = 0; k < 3; ++k) sap_half_sweep(g, g->r32, g->x32, k & 1);
+    BR_CUDA(cudaEventRecord(e1, st));
+    BR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    BR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (v == 1 || ms < best) {
+      best = ms;
+      pick = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g->sap_clover_smem = pick;
 }
 
 // x = approximate D^-1 r by `cycles` SAP cycles added to x (x holds a start).
@@ -498,12 +581,14 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
       g->Dch.reset(new DevBuf(sizeof(__half2) * n));
       note_launch(L, K_MG_SETUP, 0, 0, st, true);
       k_mg_to_half<<<grid_for(n), 256, 0, st>>>(reinterpret_cast<const float2*>(g->Dc->ptr),
-                                                   reinterpret_cast<__half2*>(g->Dch->ptr), n);
+                                                   reinterpret_cast<__half2*>(g->Dch->ptr), (long)g->m.nblocks * 9,
+                                                   g->n2, mg_coarse_unrolled(g->n2) ? 1 : 0);
       note_launch(L, K_MG_SETUP, 0, 0, st, false);
       BR_CUDA(cudaGetLastError());
     }
     BR_CUDA(cudaStreamSynchronize(st));
   }
+  pick_sap_variant(g.get());
   *out = g.release();
   return BRIDGE_OK;
 }
@@ -688,6 +773,13 @@ void mg_apply(bridge_mg_s* g, int which, const double* in, double* out) {
     case BRIDGE_MG_COARSE:
       c64_to_32(in, reinterpret_cast<float2*>(cin.ptr));
       coarse_apply(g, reinterpret_cast<float2*>(cin.ptr), reinterpret_cast<float2*>(cout.ptr));
+      c32_to_64(reinterpret_cast<float2*>(cout.ptr), out);
+      break;
+    case BRIDGE_MG_COARSE_HALF:
+      if (!g->Dch) throw Error{BRIDGE_EINVAL, "no FP16 coarse operator (coarse_half = 0)"};
+      c64_to_32(in, reinterpret_cast<float2*>(cin.ptr));
+      coarse_apply(g, reinterpret_cast<float2*>(cin.ptr), reinterpret_cast<float2*>(cout.ptr), nullptr, MG_CR_NONE,
+                   nullptr, true);
       c32_to_64(reinterpret_cast<float2*>(cout.ptr), out);
       break;
     case BRIDGE_MG_SAP:

@@ -308,6 +308,40 @@ enum MgCoarseRed { MG_CR_NONE = 0, MG_CR_ALPHA = 1, MG_CR_OMEGA = 2 };
 BR_D float2 coarse_entry(const float2* p) { return __ldg(p); }
 BR_D float2 coarse_entry(const __half2* p) { return __half22float2(__ldg(p)); }
 
+// Row lengths with a compile-time kernel; the FP16 copy of the coarse
+// operator is stored in 16-byte tiles for them (below).
+BR_HD bool mg_coarse_unrolled(int n2) { return n2 == 8 || n2 == 16 || n2 == 24 || n2 == 32 || n2 == 48; }
+
+// Row `row` of coarse site X from the tiled FP16 copy: for coupling d the
+// entries (row, 4 g .. 4 g + 3) are one 16-byte word at
+// ((X * 9 + d) * (N2 / 4) + g) * N2 + row, so each thread reads its row four
+// entries per load while the threads of one site read consecutive words.
+template <int N2>
+BR_D cx<float> coarse_row_h4(const MgCoarseArgs& a, int X, int row) {
+  static_assert(N2 % 4 == 0, "tiled rows need a multiple of four entries");
+  const uint4* Dt = reinterpret_cast<const uint4*>(a.Dch);
+  cx<float> s0 = czero<float>(), s1 = czero<float>();
+  for (int d = 0; d < 9; ++d) {
+    const int Y = __ldg(a.nbr + X * 9 + d);
+    const uint4* M = Dt + ((long)X * 9 + d) * (N2 / 4) * N2 + row;
+    const float4* xv = reinterpret_cast<const float4*>(a.x + (long)Y * N2);
+#pragma unroll
+    for (int g = 0; g < N2 / 4; ++g) {
+      const uint4 w = __ldg(M + (long)g * N2);
+      const float4 x01 = __ldg(xv + 2 * g), x23 = __ldg(xv + 2 * g + 1);
+      const float2 m0 = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+      const float2 m1 = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+      const float2 m2 = __half22float2(*reinterpret_cast<const __half2*>(&w.z));
+      const float2 m3 = __half22float2(*reinterpret_cast<const __half2*>(&w.w));
+      s0 = cfma(cx<float>{m0.x, m0.y}, cx<float>{x01.x, x01.y}, s0);
+      s1 = cfma(cx<float>{m1.x, m1.y}, cx<float>{x01.z, x01.w}, s1);
+      s0 = cfma(cx<float>{m2.x, m2.y}, cx<float>{x23.x, x23.y}, s0);
+      s1 = cfma(cx<float>{m3.x, m3.y}, cx<float>{x23.z, x23.w}, s1);
+    }
+  }
+  return s0 + s1;
+}
+
 template <int N2, class E>
 BR_D cx<float> coarse_row(const MgCoarseArgs& a, const E* Dc, int X, int row) {
   const int n2 = N2 > 0 ? N2 : a.n2;
@@ -321,13 +355,13 @@ BR_D cx<float> coarse_row(const MgCoarseArgs& a, const E* Dc, int X, int row) {
       for (int col = 0; col < N2; col += 2) {
         const float2 m0 = coarse_entry(M + (long)col * N2), v0 = __ldg(xv + col);
         const float2 m1 = coarse_entry(M + (long)(col + 1) * N2), v1 = __ldg(xv + col + 1);
-        s0 = s0 + cx<float>{m0.x, m0.y} * cx<float>{v0.x, v0.y};
-        s1 = s1 + cx<float>{m1.x, m1.y} * cx<float>{v1.x, v1.y};
+        s0 = cfma(cx<float>{m0.x, m0.y}, cx<float>{v0.x, v0.y}, s0);
+        s1 = cfma(cx<float>{m1.x, m1.y}, cx<float>{v1.x, v1.y}, s1);
       }
     } else {
       for (int col = 0; col < n2; ++col) {
         const float2 m = coarse_entry(M + (long)col * n2), v = __ldg(xv + col);
-        s0 = s0 + cx<float>{m.x, m.y} * cx<float>{v.x, v.y};
+        s0 = cfma(cx<float>{m.x, m.y}, cx<float>{v.x, v.y}, s0);
       }
     }
   }
@@ -342,7 +376,11 @@ __global__ void __launch_bounds__(256) mg_coarse_kernel(const MgCoarseArgs a) {
   double rv[3] = {0.0, 0.0, 0.0};
   if (!skip && t < (long)a.m.nblocks * n2) {
     const int X = (int)(t / n2), row = (int)(t % n2);
-    cx<float> s = a.Dch ? coarse_row<N2>(a, a.Dch, X, row) : coarse_row<N2>(a, a.Dc, X, row);
+    cx<float> s;
+    if constexpr (N2 > 0)
+      s = a.Dch ? coarse_row_h4<N2>(a, X, row) : coarse_row<N2>(a, a.Dc, X, row);
+    else
+      s = a.Dch ? coarse_row<N2>(a, a.Dch, X, row) : coarse_row<N2>(a, a.Dc, X, row);
     if (a.b) {
       const float2 bb = a.b[t];
       s = cx<float>{bb.x, bb.y} - s;
@@ -430,59 +468,92 @@ struct MgSapArgs {
   const char* clov;
 };
 
-__global__ void __launch_bounds__(256) mg_sap_kernel(const MgSapArgs a) {
+// The k-th block of one colour (the grid covers that colour only): with an
+// even number of blocks along x, every row of blocks (fixed y, z, t block
+// coordinates) holds cd[0] / 2 of each colour.
+BR_D int mg_colour_block(const MgGeom& m, int colour, int k) {
+  const int half = m.cd[0] / 2;
+  const int R = k / half, bx2 = k % half;
+  const int s = R % m.cd[1] + (R / m.cd[1]) % m.cd[2] + R / (m.cd[1] * m.cd[2]);
+  return 2 * bx2 + ((s + colour) & 1) + m.cd[0] * R;
+}
+
+// Dynamic shared memory of mg_sap_kernel: rho, the 4 forward links (all 18
+// reals) and, with CS, the clover term (72 reals) of every site of the block.
+BR_HD long mg_sap_smem(int bsites, bool cs) { return (long)bsites * (12 * 8 + 4 * 18 * 4 + (cs ? 72 * 4 : 0)); }
+
+// One SAP half sweep: every block of one colour solves D_B e = r_B by
+// `steps` MR steps from e = 0 and adds e to x.  One CTA per block, one
+// thread per site.  The links of the block are staged in shared memory once,
+// so the MR steps read them there: a hop inside the block in -mu uses
+// U_mu(x - mu), the forward link of the neighbour site.  CS: the clover term
+// is staged as well (up to 168 KB, one CTA per SM); otherwise each step
+// reads it from L2 (up to 96 KB, two CTAs per SM).  The faster variant is
+// picked by timing at setup.
+template <bool CS>
+__global__ void __launch_bounds__(256, CS ? 1 : 2) mg_sap_kernel(const MgSapArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ float2 sh[32];
-  const int blk = blockIdx.x;
-  if (mg_block_colour(a.m, blk) != a.colour) return;  // uniform per CTA
+  const int blk = mg_colour_block(a.m, a.colour, blockIdx.x);
   const int j = threadIdx.x, nsite = a.m.bsites;
   const bool on = j < nsite;
-  cx<float>* rho = reinterpret_cast<cx<float>*>(dsm);  // [12][nsite]
+  cx<float>* rho = reinterpret_cast<cx<float>*>(dsm);            // [12][nsite]
+  float* lk = reinterpret_cast<float*>(rho + 12L * nsite);        // [4 mu][18][nsite]
+  float* cl = lk + 72L * nsite;                                   // [72][nsite]
   const long vh = a.m.g.vh;
+  const long lbb = link_block_bytes(P_F32, vh);
   int c[4], p = 0;
   uint32_t ih = 0;
-  int lc[4] = {0, 0, 0, 0};
   int nbf[4], nbb[4];  // block-local neighbours (-1 outside)
-  uint32_t gf[4], gb[4];
-  cx<float> e[12], rr[12];
+  cx<float> e[12];
   if (on) {
     mg_site(a.m, blk, j, c, p, ih);
     int q = j, stride = 1;
-    int st[4];
     for (int k = 0; k < 4; ++k) {
-      lc[k] = q % a.m.b[k];
+      const int lc = q % a.m.b[k];
       q /= a.m.b[k];
-      st[k] = stride;
+      nbf[k] = lc + 1 < a.m.b[k] ? j + stride : -1;
+      nbb[k] = lc > 0 ? j - stride : -1;
       stride *= a.m.b[k];
     }
-    for (int k = 0; k < 4; ++k) {
-      nbf[k] = lc[k] + 1 < a.m.b[k] ? j + st[k] : -1;
-      nbb[k] = lc[k] > 0 ? j - st[k] : -1;
-    }
-    uint32_t xh = (uint32_t)(c[0] >> 1);
-    bool w1, w2;
-    neighbours<0>(a.m.g, ih, c, xh, gf[0], gb[0], w1, w2);
-    neighbours<1>(a.m.g, ih, c, xh, gf[1], gb[1], w1, w2);
-    neighbours<2>(a.m.g, ih, c, xh, gf[2], gb[2], w1, w2);
-    neighbours<3>(a.m.g, ih, c, xh, gf[3], gb[3], w1, w2);
+    cx<float> rr[12];
     load_spinor<P_F32>(a.r + p * a.field_block, vh, ih, rr);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       rho[k * nsite + j] = rr[k];
       e[k] = czero<float>();
     }
+    const char* g_out = a.gauge + (long)p * 4 * lbb;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      if (nbf[mu] < 0) continue;  // no hop of the block uses it
+      Link<float> U;
+      load_link<P_F32, true>(g_out + mu * lbb, vh, ih, U);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        lk[(mu * 18 + 2 * k) * nsite + j] = U.m[k / 3][k % 3].r;
+        lk[(mu * 18 + 2 * k + 1) * nsite + j] = U.m[k / 3][k % 3].i;
+      }
+    }
+    if (CS) {
+      const char* clov = a.clov + p * clover_block_bytes(P_F32, vh);
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        float t[36];
+        load_clover_block<P_F32, true>(clov, vh, ih, b, t);
+#pragma unroll
+        for (int k = 0; k < 36; ++k) cl[(36 * b + k) * nsite + j] = t[k];
+      }
+    }
   }
   __syncthreads();
-  const long lbb = link_block_bytes(P_F32, vh);
-  const char* g_out = a.gauge + (long)p * 4 * lbb;
-  const char* g_in = a.gauge + (long)(1 - p) * 4 * lbb;
   const char* clov = a.clov + p * clover_block_bytes(P_F32, vh);
   for (int step = 0; step < a.steps; ++step) {
     cx<float> qv[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) qv[k] = czero<float>();
     if (on) {
-      // H_B rho: hops to neighbours inside the block, rho read from shared memory
+      // H_B rho: hops to neighbours inside the block, all operands in shared memory
       cx<float> acc[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = czero<float>();
@@ -495,11 +566,10 @@ __global__ void __launch_bounds__(256) mg_sap_kernel(const MgSapArgs a) {
           cx<float> psi[12], h[2][3], u[2][3];
 #pragma unroll
           for (int k = 0; k < 12; ++k) psi[k] = rho[k * nsite + nb];
+          const float* lu = lk + (long)mu * 18 * nsite + (fb == 0 ? j : nb);
           Link<float> U;
-          if (fb == 0)
-            load_link<P_F32>(g_out + mu * lbb, vh, ih, U);
-          else
-            load_link<P_F32>(g_in + mu * lbb, vh, gb[mu], U);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) U.m[k / 3][k % 3] = cx<float>{lu[(2 * k) * nsite], lu[(2 * k + 1) * nsite]};
           switch (mu * 2 + fb) {
             case 0: project<float, 0, true>(psi, h); break;
             case 1: project<float, 0, false>(psi, h); break;
@@ -515,9 +585,9 @@ __global__ void __launch_bounds__(256) mg_sap_kernel(const MgSapArgs a) {
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
               if (fb == 0)
-                u[s][r] = U.m[r][0] * h[s][0] + U.m[r][1] * h[s][1] + U.m[r][2] * h[s][2];
+                u[s][r] = crow3(U.m[r][0], U.m[r][1], U.m[r][2], h[s]);
               else
-                u[s][r] = cmul_conj(U.m[0][r], h[s][0]) + cmul_conj(U.m[1][r], h[s][1]) + cmul_conj(U.m[2][r], h[s][2]);
+                u[s][r] = crow3_conj(U.m[0][r], U.m[1][r], U.m[2][r], h[s]);
             }
           switch (mu * 2 + fb) {
             case 0: reconstruct<float, 0, true>(u, acc); break;
@@ -534,9 +604,19 @@ __global__ void __launch_bounds__(256) mg_sap_kernel(const MgSapArgs a) {
       cx<float> mine[12], tr[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) mine[k] = rho[k * nsite + j];
-      clover_apply<P_F32>(clov, vh, ih, mine, tr);
+      if (CS) {
 #pragma unroll
-      for (int k = 0; k < 12; ++k) qv[k] = tr[k] - a.kappa * acc[k];
+        for (int b = 0; b < 2; ++b) {
+          float t[36];
+#pragma unroll
+          for (int k = 0; k < 36; ++k) t[k] = cl[(36 * b + k) * nsite + j];
+          hermitian6_apply<float>(t, mine + 6 * b, tr + 6 * b);
+        }
+      } else {
+        clover_apply<P_F32>(clov, vh, ih, mine, tr);
+      }
+#pragma unroll
+      for (int k = 0; k < 12; ++k) qv[k] = caxpy(-a.kappa, acc[k], tr[k]);
     }
     // alpha = <q, rho> / <q, q> over the block
     cx<float> dqr = czero<float>();
@@ -545,8 +625,8 @@ __global__ void __launch_bounds__(256) mg_sap_kernel(const MgSapArgs a) {
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         const cx<float> rk = rho[k * nsite + j];
-        dqr = dqr + cmul_conj(qv[k], rk);
-        dqq += qv[k].r * qv[k].r + qv[k].i * qv[k].i;
+        dqr = cfma_conj(qv[k], rk, dqr);
+        dqq = fmaf(qv[k].r, qv[k].r, fmaf(qv[k].i, qv[k].i, dqq));
       }
     }
     const cx<float> sqr = mg_block_allsum(dqr, sh);
@@ -556,8 +636,8 @@ __global__ void __launch_bounds__(256) mg_sap_kernel(const MgSapArgs a) {
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         const cx<float> rk = rho[k * nsite + j];
-        e[k] = e[k] + alpha * rk;
-        rho[k * nsite + j] = rk - alpha * qv[k];
+        e[k] = cfma(alpha, rk, e[k]);
+        rho[k * nsite + j] = cfma(cx<float>{-alpha.r, -alpha.i}, qv[k], rk);
       }
     }
     __syncthreads();
@@ -598,12 +678,14 @@ __global__ void __launch_bounds__(256) mg_axpbypcz_kernel(long n, cx<S> ca, cons
 template <class T>
 __global__ void __launch_bounds__(256) mg_dot_kernel(long n, const T* x, const T* y, double2* partial) {
   __shared__ double sr[8], si[8];
-  double ar = 0, ai = 0;
+  using R = decltype(T{}.x);
+  PartialSum<R> pr, pi;  // compensated FP32 sums for FP32 data: no FP64 instruction in the loop
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const T a = x[i], b = y[i];
-    ar += (double)a.x * b.x + (double)a.y * b.y;
-    ai += (double)a.x * b.y - (double)a.y * b.x;
+    pr.add(fmar<R>(a.x, b.x, a.y * b.y));
+    pi.add(fmar<R>(a.x, b.y, -a.y * b.x));
   }
+  double ar = pr.value(), ai = pi.value();
   for (int off = 16; off > 0; off >>= 1) {
     ar += __shfl_xor_sync(0xffffffffu, ar, off);
     ai += __shfl_xor_sync(0xffffffffu, ai, off);

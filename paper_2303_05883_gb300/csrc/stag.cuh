@@ -112,10 +112,10 @@ BR_D void stag_hop_one(const char* in, const char* lb, long vh, uint32_t nb, uin
   for (int r = 0; r < 3; ++r) {
     cx<R> w;
     if (FWD)
-      w = U.m[r][0] * v[0] + U.m[r][1] * v[1] + U.m[r][2] * v[2];
+      w = crow3(U.m[r][0], U.m[r][1], U.m[r][2], v);
     else
-      w = cmul_conj(U.m[0][r], v[0]) + cmul_conj(U.m[1][r], v[1]) + cmul_conj(U.m[2][r], v[2]);
-    acc[r] = acc[r] + f * w;
+      w = crow3_conj(U.m[0][r], U.m[1][r], U.m[2][r], v);
+    acc[r] = caxpy(f, w, acc[r]);
   }
 }
 

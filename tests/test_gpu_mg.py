@@ -94,6 +94,28 @@ def test_coarse_operator_columns(api, case):
     assert rel(mg.apply(_abi.BRIDGE_MG_COARSE, x), orc.restrict(orc.D(orc.prolong(x)))) < TOL32
 
 
+@pytest.mark.parametrize("nv", [3, 4, 12])
+def test_coarse_operator_fp16_copy(api, case, nv):
+    """The FP16 copy of D_c the coarse solver applies (tiled 16-byte rows for
+    2 nv in 8, 16, 24, 32, 48; plain rows otherwise) against the oracle's
+    P^dag D P x, within the FP16 rounding of the entries."""
+    from paper_2303_05883_gb300 import _abi
+
+    lat, U, op, L = case["lat"], case["U"], case["op"], case["L"]
+    gen = np.random.default_rng(100 + nv)
+    vs = gen.standard_normal((nv, lat.V, 4, 3)) + 1j * gen.standard_normal((nv, lat.V, 4, 3))
+    orc = multigrid.Multigrid(U, lat, 0.12, 1.0, (2, 2, 2, 2), vs)
+    mg = api.Multigrid(L, op, api.make_mg_params(block=(2, 2, 2, 2), nvec=nv, coarse_half=1), null_vectors=vs)
+    x = gen.standard_normal((mg.nblocks, 2, nv)) + 1j * gen.standard_normal((mg.nblocks, 2, nv))
+    want = orc.restrict(orc.D(orc.prolong(x)))
+    assert rel(mg.apply(_abi.BRIDGE_MG_COARSE, x), want) < TOL32
+    assert rel(mg.apply(_abi.BRIDGE_MG_COARSE_HALF, x), want) < 2e-3
+    mg.close()
+    # without the FP16 copy the half application is refused
+    with pytest.raises(_abi.BridgeError):
+        case["mg"].apply(_abi.BRIDGE_MG_COARSE_HALF, x[:, :, :3] if nv >= 3 else x)
+
+
 def test_sap_smoother(api, case):
     from paper_2303_05883_gb300 import _abi
 
