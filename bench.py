@@ -1043,7 +1043,7 @@ def run_staggered(args):
         dist.destroy_process_group()
 
 
-MG_PARAMS = dict(nvec=12, setup_steps=3, sap_cycles=3, mr_steps=4, coarse_tol=5e-2)
+MG_PARAMS = dict(nvec=12, setup_steps=3, sap_cycles=2, mr_steps=6, coarse_tol=1e-1)
 
 
 def run_mg(args):

@@ -108,8 +108,11 @@ struct bridge_mg_s {
   std::unique_ptr<DevBuf> csc, cpart, ccount;
   std::unique_ptr<PinnedBuf> hcsc;
   long coarse_iters = 0, coarse_solves = 0;
+  int last_coarse_iters = 0;  // iterations of the previous coarse solve (sizes the first batch)
   Field r32, x32, res32;  // fine FP32 work fields of the cycle
   int sap_clover_smem = 1;  // SAP kernel variant (picked by timing at setup)
+  // error word of the streamed coarse kernel, in the scalar buffer after the BiCGScalars
+  int* cerr() const { return reinterpret_cast<int*>(static_cast<char*>(csc->ptr) + 192); }
   float2* cv(int k) const { return reinterpret_cast<float2*>(cvec->ptr) + (long)k * nc; }
 };
 
@@ -201,6 +204,43 @@ void launch_coarse_red(int n2, const MgCoarseArgs& a, unsigned grid, cudaStream_
     default: mg_coarse_kernel<RED, 0><<<grid, 256, 0, st>>>(a); break;
   }
 }
+// The streamed FP16 kernel: `stages` tile buffers (2 .. 4, up to ~70 KB
+// unless two tiles are larger), a persistent grid of up to 4 CTAs per SM as
+// shared memory allows.
+template <int RED, int N2>
+void launch_coarse_tma_n(MgCoarseArgs a, int nblocks, cudaStream_t st) {
+  constexpr long tile = mg_coarse_tile_bytes<N2>();
+  a.stages = (int)std::max(2L, std::min(4L, 70L * 1024 / tile));
+  const long smem = a.stages * tile;
+  static std::mutex mu;
+  static std::map<int, long> done;
+  int dev = 0;
+  BR_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev] < smem) {
+      BR_CUDA(cudaFuncSetAttribute(mg_coarse_tma_kernel<RED, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+      done[dev] = smem;
+    }
+  }
+  const long per_sm = std::max(1L, std::min(4L, (220L * 1024) / (smem + 4 * 1024)));
+  const long grid = std::min<long>(nblocks, per_sm * sm_count());
+  mg_coarse_tma_kernel<RED, N2><<<(unsigned)grid, 256, (size_t)smem, st>>>(a);
+}
+template <int RED>
+void launch_coarse_tma(int n2, const MgCoarseArgs& a, int nblocks, cudaStream_t st) {
+  switch (n2) {
+    case 8: launch_coarse_tma_n<RED, 8>(a, nblocks, st); break;
+    case 16: launch_coarse_tma_n<RED, 16>(a, nblocks, st); break;
+    case 24: launch_coarse_tma_n<RED, 24>(a, nblocks, st); break;
+    case 32: launch_coarse_tma_n<RED, 32>(a, nblocks, st); break;
+    default: launch_coarse_tma_n<RED, 48>(a, nblocks, st); break;
+  }
+}
+// Blocks of the streamed kernel at most (sizes the reduction partials).
+long coarse_tma_max_grid() { return 4L * sm_count(); }
+
 void launch_coarse(int red, int n2, const MgCoarseArgs& a, unsigned grid, cudaStream_t st) {
   if (red == MG_CR_ALPHA) launch_coarse_red<MG_CR_ALPHA>(n2, a, grid, st);
   else if (red == MG_CR_OMEGA) launch_coarse_red<MG_CR_OMEGA>(n2, a, grid, st);
@@ -215,9 +255,8 @@ void coarse_apply(bridge_mg_s* g, const float2* x, float2* y, const float2* b = 
   a.n2 = g->n2;
   a.Dc = reinterpret_cast<const float2*>(g->Dc->ptr);
   a.Dch = (half && g->Dch) ? reinterpret_cast<const __half2*>(g->Dch->ptr) : nullptr;
-  // the tiled FP16 rows read x four entries (32 bytes) at a time
-  if (a.Dch && mg_coarse_unrolled(g->n2) && (reinterpret_cast<uintptr_t>(x) & 15) != 0) a.Dch = nullptr;
   a.nbr = reinterpret_cast<const int*>(g->cnbr->ptr);
+  a.err = g->cerr();
   a.x = x;
   a.b = b;
   a.y = y;
@@ -232,9 +271,27 @@ void coarse_apply(bridge_mg_s* g, const float2* x, float2* y, const float2* b = 
   const long n = g->nc;
   const double bytes = (double)g->m.nblocks * 9 * g->n2 * g->n2 * (a.Dch ? 4 : 8) + n * 8.0 * (b ? 3 : 2);
   note_launch(g->L, K_MG_COARSE, bytes, (double)g->m.nblocks * 9 * g->n2 * g->n2 * 8, stream_of(g), true);
-  launch_coarse(red, g->n2, a, (unsigned)((n + 255) / 256), stream_of(g));
+  if (a.Dch && mg_coarse_unrolled(g->n2)) {  // the tiled FP16 copy: streamed by bulk copies
+    if (red == MG_CR_ALPHA)
+      launch_coarse_tma<MG_CR_ALPHA>(g->n2, a, g->m.nblocks, stream_of(g));
+    else if (red == MG_CR_OMEGA)
+      launch_coarse_tma<MG_CR_OMEGA>(g->n2, a, g->m.nblocks, stream_of(g));
+    else
+      launch_coarse_tma<MG_CR_NONE>(g->n2, a, g->m.nblocks, stream_of(g));
+  } else {
+    launch_coarse(red, g->n2, a, (unsigned)((n + 255) / 256), stream_of(g));
+  }
   note_launch(g->L, K_MG_COARSE, bytes, 0, stream_of(g), false);
   BR_CUDA(cudaGetLastError());
+}
+
+static_assert(sizeof(BiCGScalars) <= 192, "the coarse error word follows the scalars");
+
+// The host copy of the scalar buffer (hcsc) holds the streamed coarse
+// kernel's error word at byte 192.
+void check_coarse_err(bridge_mg_s* g) {
+  const int e = *reinterpret_cast<const int*>(static_cast<const char*>(g->hcsc->ptr) + 192);
+  if (e != 0) throw Error{BRIDGE_ECUDA, "coarse operator: a tile copy did not complete within 1 s"};
 }
 
 void cbicg_step(bridge_mg_s* g, int op, const float2* b = nullptr) {
@@ -279,9 +336,12 @@ int coarse_solve(bridge_mg_s* g, const float2* rhs) {
   init.rho_r = init.alpha_r = init.omega_r = 1.0;
   BR_CUDA(cudaMemcpyAsync(g->csc->ptr, &init, sizeof(init), cudaMemcpyHostToDevice, st));
   cbicg_step(g, MG_CB_INIT, rhs);
-  const int batch = 8;
+  // The first batch runs to just short of the previous solve's count without
+  // a host poll; later batches are short.  Iterations queued past
+  // convergence exit at once (their kernels check the done flag).
+  int batch = std::max(4, g->last_coarse_iters - 2);
   int launched = 0;
-  for (;;) {
+  for (;; batch = 4) {
     for (int k = 0; k < batch && launched < g->prm.coarse_maxiter; ++k, ++launched) {
       coarse_apply(g, g->cv(4), g->cv(5), nullptr, MG_CR_ALPHA, g->cv(3), true);  // v = D_c p, alpha
       cbicg_step(g, MG_CB_S);                                                    // s = r - alpha v
@@ -289,12 +349,14 @@ int coarse_solve(bridge_mg_s* g, const float2* rhs) {
       cbicg_step(g, MG_CB_XR);                                             // x, r; rho, beta
       cbicg_step(g, MG_CB_P);                                              // p
     }
-    BR_CUDA(cudaMemcpyAsync(g->hcsc->ptr, g->csc->ptr, sizeof(BiCGScalars), cudaMemcpyDeviceToHost, st));
+    BR_CUDA(cudaMemcpyAsync(g->hcsc->ptr, g->csc->ptr, 256, cudaMemcpyDeviceToHost, st));
     BR_CUDA(cudaStreamSynchronize(st));
+    check_coarse_err(g);
     const BiCGScalars* q = static_cast<const BiCGScalars*>(g->hcsc->ptr);
     if (q->done != RUNNING || launched >= g->prm.coarse_maxiter) {
       g->coarse_iters += q->iter;
       g->coarse_solves += 1;
+      g->last_coarse_iters = q->iter;
       return q->iter;
     }
   }
@@ -496,7 +558,8 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
   g->hpart.reset(new PinnedBuf(sizeof(double2) * 1024 * 8));
   g->csc.reset(new DevBuf(256));
   g->hcsc.reset(new PinnedBuf(256));
-  g->cpart.reset(new DevBuf(sizeof(double) * 4 * ((g->nc + 255) / 256)));
+  BR_CUDA(cudaMemsetAsync(g->csc->ptr, 0, 256, st));
+  g->cpart.reset(new DevBuf(sizeof(double) * 4 * std::max((g->nc + 255) / 256, coarse_tma_max_grid())));
   g->ccount.reset(new DevBuf(256));
   BR_CUDA(cudaMemsetAsync(g->ccount->ptr, 0, 256, st));
   const size_t canon = (size_t)L->V * 24;
@@ -781,6 +844,8 @@ void mg_apply(bridge_mg_s* g, int which, const double* in, double* out) {
       coarse_apply(g, reinterpret_cast<float2*>(cin.ptr), reinterpret_cast<float2*>(cout.ptr), nullptr, MG_CR_NONE,
                    nullptr, true);
       c32_to_64(reinterpret_cast<float2*>(cout.ptr), out);
+      BR_CUDA(cudaMemcpy(g->hcsc->ptr, g->csc->ptr, 256, cudaMemcpyDeviceToHost));
+      check_coarse_err(g);
       break;
     case BRIDGE_MG_SAP:
       canon_to_field(L, in, g->r32, st);

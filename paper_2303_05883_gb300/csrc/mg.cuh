@@ -296,9 +296,54 @@ struct MgCoarseArgs {
   float2* y;
   const float2* rhat;  // MG_CR_ALPHA: <rhat, y> -> FIN_ALPHA
   RedArgs red;
+  int* err;     // mg_coarse_tma_kernel: set to 1 if a tile copy did not arrive in time
+  int stages;   // mg_coarse_tma_kernel: tile buffers in shared memory (2 .. 4)
 };
 
 enum MgCoarseRed { MG_CR_NONE = 0, MG_CR_ALPHA = 1, MG_CR_OMEGA = 2 };
+
+// ---- bulk async copies (TMA) into shared memory, completed on an mbarrier
+BR_D uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+BR_D void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+BR_D void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+BR_D void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// One thread: announce `bytes` on the barrier and start the copy of `bytes`
+// (a multiple of 16, both addresses 16-byte aligned) from global memory.
+BR_D void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+               : "=l"(state)
+               : "r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  (void)state;
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// Wait for the phase of the given parity to complete, giving up after about
+// a second (returns false then).
+BR_D bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 255) == 255) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > 1000000000ull) return false;
+    }
+  }
+  return false;
+}
 
 // y = D_c x (or b - D_c x); with a fused reduction for the coarse BiCGStab:
 // MG_CR_ALPHA <rhat, y>, MG_CR_OMEGA (<y, x>, |y|^2).  Coarse sites of a
@@ -308,39 +353,11 @@ enum MgCoarseRed { MG_CR_NONE = 0, MG_CR_ALPHA = 1, MG_CR_OMEGA = 2 };
 BR_D float2 coarse_entry(const float2* p) { return __ldg(p); }
 BR_D float2 coarse_entry(const __half2* p) { return __half22float2(__ldg(p)); }
 
-// Row lengths with a compile-time kernel; the FP16 copy of the coarse
-// operator is stored in 16-byte tiles for them (below).
+// Row lengths with compile-time kernels.  For them the FP16 copy of the
+// coarse operator is stored in 16-byte tiles, entries (row, 4 g .. 4 g + 3)
+// of coupling d of site X in word ((X * 9 + d) * (N2 / 4) + g) * N2 + row,
+// and applied by mg_coarse_tma_kernel.
 BR_HD bool mg_coarse_unrolled(int n2) { return n2 == 8 || n2 == 16 || n2 == 24 || n2 == 32 || n2 == 48; }
-
-// Row `row` of coarse site X from the tiled FP16 copy: for coupling d the
-// entries (row, 4 g .. 4 g + 3) are one 16-byte word at
-// ((X * 9 + d) * (N2 / 4) + g) * N2 + row, so each thread reads its row four
-// entries per load while the threads of one site read consecutive words.
-template <int N2>
-BR_D cx<float> coarse_row_h4(const MgCoarseArgs& a, int X, int row) {
-  static_assert(N2 % 4 == 0, "tiled rows need a multiple of four entries");
-  const uint4* Dt = reinterpret_cast<const uint4*>(a.Dch);
-  cx<float> s0 = czero<float>(), s1 = czero<float>();
-  for (int d = 0; d < 9; ++d) {
-    const int Y = __ldg(a.nbr + X * 9 + d);
-    const uint4* M = Dt + ((long)X * 9 + d) * (N2 / 4) * N2 + row;
-    const float4* xv = reinterpret_cast<const float4*>(a.x + (long)Y * N2);
-#pragma unroll
-    for (int g = 0; g < N2 / 4; ++g) {
-      const uint4 w = __ldg(M + (long)g * N2);
-      const float4 x01 = __ldg(xv + 2 * g), x23 = __ldg(xv + 2 * g + 1);
-      const float2 m0 = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
-      const float2 m1 = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
-      const float2 m2 = __half22float2(*reinterpret_cast<const __half2*>(&w.z));
-      const float2 m3 = __half22float2(*reinterpret_cast<const __half2*>(&w.w));
-      s0 = cfma(cx<float>{m0.x, m0.y}, cx<float>{x01.x, x01.y}, s0);
-      s1 = cfma(cx<float>{m1.x, m1.y}, cx<float>{x01.z, x01.w}, s1);
-      s0 = cfma(cx<float>{m2.x, m2.y}, cx<float>{x23.x, x23.y}, s0);
-      s1 = cfma(cx<float>{m3.x, m3.y}, cx<float>{x23.z, x23.w}, s1);
-    }
-  }
-  return s0 + s1;
-}
 
 template <int N2, class E>
 BR_D cx<float> coarse_row(const MgCoarseArgs& a, const E* Dc, int X, int row) {
@@ -376,9 +393,10 @@ __global__ void __launch_bounds__(256) mg_coarse_kernel(const MgCoarseArgs a) {
   double rv[3] = {0.0, 0.0, 0.0};
   if (!skip && t < (long)a.m.nblocks * n2) {
     const int X = (int)(t / n2), row = (int)(t % n2);
+    // the tiled FP16 copy of the unrolled row lengths goes to mg_coarse_tma_kernel
     cx<float> s;
     if constexpr (N2 > 0)
-      s = a.Dch ? coarse_row_h4<N2>(a, X, row) : coarse_row<N2>(a, a.Dc, X, row);
+      s = coarse_row<N2>(a, a.Dc, X, row);
     else
       s = a.Dch ? coarse_row<N2>(a, a.Dch, X, row) : coarse_row<N2>(a, a.Dc, X, row);
     if (a.b) {
@@ -398,6 +416,132 @@ __global__ void __launch_bounds__(256) mg_coarse_kernel(const MgCoarseArgs a) {
       rv[1] = d.i;
       rv[2] = (double)s.r * s.r + (double)s.i * s.i;
     }
+  }
+  if (RED == MG_CR_ALPHA) reduce_finalize<2>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
+  if (RED == MG_CR_OMEGA) reduce_finalize<3>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
+}
+
+// The same operator from the tiled FP16 copy, streamed by the bulk-copy
+// engine: a persistent CTA walks its coarse sites (blockIdx.x, + gridDim.x,
+// ...); the 9 * N2 * N2 FP16 entries of a site are contiguous, so one bulk
+// copy per site moves them into one of `stages` shared-memory buffers while
+// the CTA computes on the previous ones.  Thread (d, row) forms the row sum
+// of coupling d from shared memory against x at the coupled site (staged in
+// shared memory, its loads issued one site ahead), and N2 threads add the
+// nine couplings.  Coarse sites of a converged solve (red.sc->done) are
+// skipped.
+template <int N2>
+__host__ __device__ constexpr long mg_coarse_tile_bytes() { return 9L * (N2 / 4) * N2 * 16; }
+
+template <int RED, int N2>
+__global__ void __launch_bounds__(256) mg_coarse_tma_kernel(const MgCoarseArgs a) {
+  static_assert(N2 % 4 == 0 && 9 * N2 <= 512, "tiled rows of at most 56 entries");
+  constexpr int NG = N2 / 4;
+  constexpr long TILE = mg_coarse_tile_bytes<N2>();
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t bar[4];
+  __shared__ float2 xs[9 * N2];
+  __shared__ float2 part[9 * N2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int stages = a.stages;
+  const bool skip = RED != MG_CR_NONE && a.red.sc != nullptr && a.red.sc[0].done != RUNNING;
+  const int nb = a.m.nblocks, first = blockIdx.x, step = gridDim.x;
+  const int mine = (skip || first >= nb) ? 0 : (nb - first + step - 1) / step;
+  const char* src = reinterpret_cast<const char*>(a.Dch);
+  double rv[3] = {0.0, 0.0, 0.0};
+  if (tid == 0) {
+    for (int k = 0; k < stages; ++k) mbar_init(&bar[k], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int k = 0; k < stages && k < mine; ++k) {
+      const int X = first + k * step;
+      bulk_load(dsm + k * TILE, src + (long)X * TILE, (uint32_t)TILE, &bar[k]);
+    }
+  // x at the coupled sites of the first site (two entries per thread at most)
+  float2 xn[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  auto load_x = [&](int X) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = tid + q * nt;
+      if (i < 9 * N2) {
+        const int Y = __ldg(a.nbr + X * 9 + i / N2);
+        xn[q] = __ldg(a.x + (long)Y * N2 + i % N2);
+      }
+    }
+  };
+  if (mine > 0) load_x(first);
+  bool failed = false;
+  int it = 0;
+  for (; it < mine; ++it) {
+    const int X = first + it * step, buf = it % stages;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (tid + q * nt < 9 * N2) xs[tid + q * nt] = xn[q];
+    if (it + 1 < mine) load_x(X + step);
+    // operands of this site's epilogue, loaded before the wait
+    float2 eb = make_float2(0.f, 0.f), ev = make_float2(0.f, 0.f);
+    if (tid < N2) {
+      const long t = (long)X * N2 + tid;
+      if (a.b) eb = a.b[t];
+      if (RED == MG_CR_ALPHA) ev = a.rhat[t];
+      if (RED == MG_CR_OMEGA) ev = a.x[t];
+    }
+    const bool ok = mbar_wait(&bar[buf], (uint32_t)((it / stages) & 1));
+    if (!__syncthreads_and(ok)) {
+      failed = true;
+      break;
+    }
+    const uint4* tile = reinterpret_cast<const uint4*>(dsm + buf * TILE);
+    for (int p = tid; p < 9 * N2; p += nt) {
+      const int d = p / N2, row = p % N2;
+      const float2* xv = xs + d * N2;
+      cx<float> s0 = czero<float>(), s1 = czero<float>();
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const uint4 w = tile[(d * NG + g) * N2 + row];
+        const float2 m0 = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+        const float2 m1 = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+        const float2 m2 = __half22float2(*reinterpret_cast<const __half2*>(&w.z));
+        const float2 m3 = __half22float2(*reinterpret_cast<const __half2*>(&w.w));
+        const float2 x0 = xv[4 * g], x1 = xv[4 * g + 1], x2 = xv[4 * g + 2], x3 = xv[4 * g + 3];
+        s0 = cfma(cx<float>{m0.x, m0.y}, cx<float>{x0.x, x0.y}, s0);
+        s1 = cfma(cx<float>{m1.x, m1.y}, cx<float>{x1.x, x1.y}, s1);
+        s0 = cfma(cx<float>{m2.x, m2.y}, cx<float>{x2.x, x2.y}, s0);
+        s1 = cfma(cx<float>{m3.x, m3.y}, cx<float>{x3.x, x3.y}, s1);
+      }
+      const cx<float> sum = s0 + s1;
+      part[p] = make_float2(sum.r, sum.i);
+    }
+    __syncthreads();  // buffer `buf` and xs are free again
+    if (tid == 0 && it + stages < mine) {
+      fence_proxy_async_smem();
+      bulk_load(dsm + buf * TILE, src + (long)(X + stages * step) * TILE, (uint32_t)TILE, &bar[buf]);
+    }
+    if (tid < N2) {
+      cx<float> sv = czero<float>();
+#pragma unroll
+      for (int d = 0; d < 9; ++d) sv = sv + cx<float>{part[d * N2 + tid].x, part[d * N2 + tid].y};
+      const long t = (long)X * N2 + tid;
+      if (a.b) sv = cx<float>{eb.x, eb.y} - sv;
+      a.y[t] = make_float2(sv.r, sv.i);
+      if (RED == MG_CR_ALPHA) {
+        const cx<float> d = cmul_conj(cx<float>{ev.x, ev.y}, sv);
+        rv[0] += d.r;
+        rv[1] += d.i;
+      } else if (RED == MG_CR_OMEGA) {
+        const cx<float> d = cmul_conj(sv, cx<float>{ev.x, ev.y});
+        rv[0] += d.r;
+        rv[1] += d.i;
+        rv[2] += (double)sv.r * sv.r + (double)sv.i * sv.i;
+      }
+    }
+  }
+  if (failed) {
+    // let the copies still in flight land (bounded) before the CTA exits
+    for (int k = it; k < mine && k < it + stages; ++k) (void)mbar_wait(&bar[k % stages], (uint32_t)((k / stages) & 1));
+    if (tid == 0) atomicExch(a.err, 1);
   }
   if (RED == MG_CR_ALPHA) reduce_finalize<2>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
   if (RED == MG_CR_OMEGA) reduce_finalize<3>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
