@@ -159,7 +159,7 @@ def traffic_for(kernel: str, workload: str):
 def kernel_source_hash(kernel: str = "") -> str:
     d = hashlib.sha256()
     files = ["common.cuh", "dslash.cuh", "reduce.cuh"] + (["dwf.cuh"] if kernel.startswith("dwf") else []) + (
-        ["stag.cuh"] if kernel.startswith("stag") else [])
+        ["stag.cuh"] if kernel.startswith("stag") else []) + (["mg.cuh"] if kernel.startswith("mg") else [])
     for f in files:
         d.update(open(os.path.join(ROOT, "paper_2303_05883_gb300", "csrc", f), "rb").read())
     return d.hexdigest()[:16]

@@ -54,7 +54,17 @@ struct HopArgs {
   const char* clovE;  // [parity] clover blocks (T^-1)
   const char* clovM;  // [parity] clover blocks (T)
   RedArgs red;
+  // 0: every site; 1 or 2: only the sites in blocks of extents mb whose block
+  // coordinates sum to an even (1) or odd (2) number (one colour of a
+  // Schwarz blocking); the other sites are neither read nor written.
+  int mcol;
+  int mb[4];
 };
+
+BR_D bool hop_site_masked(const HopArgs& a, const int c[4]) {
+  return a.mcol != 0 &&
+         ((c[0] / a.mb[0] + c[1] / a.mb[1] + c[2] / a.mb[2] + c[3] / a.mb[3]) & 1) != a.mcol - 1;
+}
 
 template <class R, int MU, bool FWD>
 BR_D void project(const cx<R> p[12], cx<R> h[2][3]) {
@@ -192,6 +202,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
       int c[4];
       uint32_t xh;
       site_coords(a.g, ih, p, c, xh);
+      if (hop_site_masked(a, c)) continue;
       cx<R> acc[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = czero<R>();
@@ -358,6 +369,7 @@ __global__ void __launch_bounds__(256) hop_kernel_mr(const HopArgs a) {
       int c[4];
       uint32_t xh;
       site_coords(a.g, ih, p, c, xh);
+      if (hop_site_masked(a, c)) continue;
       cx<T> acc[NR][12];
 #pragma unroll
       for (int r = 0; r < NR; ++r)

@@ -311,7 +311,7 @@ void cbicg_step(bridge_mg_s* g, int op, const float2* b = nullptr) {
   a.red.sc = reinterpret_cast<BiCGScalars*>(g->csc->ptr);
   a.red.fin = op == MG_CB_INIT ? FIN_INIT : op == MG_CB_XR ? FIN_RHO : FIN_NONE;
   a.red.check_done = op == MG_CB_INIT ? 0 : 1;
-  const unsigned grid = (unsigned)((g->nc + 255) / 256);
+  const unsigned grid = (unsigned)std::min<long>((g->nc + 255) / 256, 2L * sm_count());
   const double bytes = (double)g->nc * 8 * (op == MG_CB_INIT ? 6 : op == MG_CB_S ? 3 : op == MG_CB_XR ? 8 : 4);
   note_launch(g->L, K_MG_VEC, bytes, 0, stream_of(g), true);
   switch (op) {
@@ -363,7 +363,9 @@ int coarse_solve(bridge_mg_s* g, const float2* rhs) {
 }
 
 // ---- fine FP32 pieces of the cycle
-void fine_residual32(bridge_mg_s* g, const Field& b, const Field& x, const Field& out) {
+// colour >= 0: only at the sites of that colour's blocks (the next SAP half
+// sweep reads nothing else).
+void fine_residual32(bridge_mg_s* g, const Field& b, const Field& x, const Field& out, int colour = -1) {
   // out = b - D x = b - T x + kappa H x
   for (int q = 0; q < 2; ++q) {
     HopCall c;
@@ -387,6 +389,11 @@ void fine_residual32(bridge_mg_s* g, const Field& b, const Field& x, const Field
     c.self_rs = x.rs;
     c.aux = b.ptr(q);
     c.aux_rs = b.rs;
+    if (colour >= 0) {
+      c.mcol = colour + 1;
+      for (int k = 0; k < 4; ++k) c.mb[k] = g->m.b[k];
+      c.work_fraction = 0.5;
+    }
     run_hop(g->L, c, stream_of(g));
   }
 }
@@ -481,7 +488,7 @@ void sap(bridge_mg_s* g, const Field& r, const Field& x, int cycles, bool x_zero
       if (cyc == 0 && colour == 0 && x_zero) {
         sap_half_sweep(g, r, x, colour);  // residual = r while x = 0
       } else {
-        fine_residual32(g, r, x, g->res32);
+        fine_residual32(g, r, x, g->res32, colour);
         sap_half_sweep(g, g->res32, x, colour);
       }
     }

@@ -559,15 +559,19 @@ struct MgCBicgArgs {
   RedArgs red;
 };
 
+// Grid-stride over the coarse vector (the grid is a couple of CTAs per SM,
+// so the fused reductions combine few block partials); per-thread sums in
+// compensated FP32.
 template <int OP>
 __global__ void __launch_bounds__(256) mg_cbicg_kernel(const MgCBicgArgs a) {
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const BiCGScalars* q = a.red.sc;
   const bool skip = OP != MG_CB_INIT && q->done != RUNNING;
-  double rv[3] = {0.0, 0.0, 0.0};
-  if (!skip && i < a.n) {
-    auto c = [](float2 f) { return cx<float>{f.x, f.y}; };
-    auto f2 = [](cx<float> v) { return make_float2(v.r, v.i); };
+  PartialSum<float> p0, p1, p2;
+  auto c = [](float2 f) { return cx<float>{f.x, f.y}; };
+  auto f2 = [](cx<float> v) { return make_float2(v.r, v.i); };
+  const cx<float> al{(float)q->alpha_r, (float)q->alpha_i}, om{(float)q->omega_r, (float)q->omega_i};
+  const cx<float> be{(float)q->beta_r, (float)q->beta_i};
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; !skip && i < a.n; i += (long)gridDim.x * blockDim.x) {
     if (OP == MG_CB_INIT) {
       const float2 bb = a.b[i];
       a.x[i] = make_float2(0.f, 0.f);
@@ -575,25 +579,23 @@ __global__ void __launch_bounds__(256) mg_cbicg_kernel(const MgCBicgArgs a) {
       a.rhat[i] = bb;
       a.p[i] = bb;
       a.v[i] = make_float2(0.f, 0.f);
-      rv[0] = (double)bb.x * bb.x + (double)bb.y * bb.y;
+      p0.add(fmaf(bb.x, bb.x, bb.y * bb.y));
     } else if (OP == MG_CB_S) {
-      const cx<float> al{(float)q->alpha_r, (float)q->alpha_i};
       a.s[i] = f2(c(a.r[i]) - al * c(a.v[i]));
     } else if (OP == MG_CB_XR) {
-      const cx<float> al{(float)q->alpha_r, (float)q->alpha_i}, om{(float)q->omega_r, (float)q->omega_i};
       const cx<float> sv = c(a.s[i]);
       a.x[i] = f2(c(a.x[i]) + al * c(a.p[i]) + om * sv);
       const cx<float> rn = sv - om * c(a.t[i]);
       a.r[i] = f2(rn);
       const cx<float> d = cmul_conj(c(a.rhat[i]), rn);
-      rv[0] = d.r;
-      rv[1] = d.i;
-      rv[2] = (double)rn.r * rn.r + (double)rn.i * rn.i;
+      p0.add(d.r);
+      p1.add(d.i);
+      p2.add(fmaf(rn.r, rn.r, rn.i * rn.i));
     } else {
-      const cx<float> be{(float)q->beta_r, (float)q->beta_i}, om{(float)q->omega_r, (float)q->omega_i};
       a.p[i] = f2(c(a.r[i]) + be * (c(a.p[i]) - om * c(a.v[i])));
     }
   }
+  double rv[3] = {p0.value(), p1.value(), p2.value()};
   if (OP == MG_CB_INIT) reduce_finalize<1>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
   if (OP == MG_CB_XR) reduce_finalize<3>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
 }

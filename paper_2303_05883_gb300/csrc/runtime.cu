@@ -295,8 +295,11 @@ void run_hop(bridge_lattice_s* L, HopCall c, cudaStream_t st) {
     if (a.red.fin == FIN_NONE) a.red.fin = FIN_STORE;
   }
   const HopCost hc = hop_cost(c.prec, c.flags, c.red);
-  const double bytes = c.count_work ? (double)L->vh * (hc.rhs_bytes * c.nrhs + hc.shared_bytes) : 0.0;
-  const double flops = c.count_work ? (double)L->vh * c.nrhs * hc.rhs_flops : 0.0;
+  a.mcol = c.mcol;
+  for (int k = 0; k < 4; ++k) a.mb[k] = std::max(1, c.mb[k]);
+  const double bytes =
+      c.count_work ? c.work_fraction * (double)L->vh * (hc.rhs_bytes * c.nrhs + hc.shared_bytes) : 0.0;
+  const double flops = c.count_work ? c.work_fraction * (double)L->vh * c.nrhs * hc.rhs_flops : 0.0;
   note_launch(L, c.cls, bytes, flops, st, true);
   BR_CHECK(launch_hop_any(c.prec, c.flags, c.red, a, sh.block, st, nullptr, sh.variant), BRIDGE_EINVAL,
            "hop variant not instantiated");
