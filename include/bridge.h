@@ -312,11 +312,15 @@ typedef struct {
   double coarse_tol;  /* relative tolerance of the coarse BiCGStab */
   int coarse_maxiter; /* iteration limit of the coarse BiCGStab */
   int coarse_half;    /* 1: the coarse BiCGStab reads an FP16 copy of the coarse operator (FP32 math) */
+  int coarse_eo;      /* 1: with coarse_half and 2 nvec in {8, 16, 24, 32, 48}, the coarse BiCGStab runs on
+                         the even-odd preconditioned coarse system (coarse sites split by the parity of
+                         their block coordinates; every hopping coupling joins the two), the odd part
+                         reconstructed after; coarse_tol then bounds that system's relative residual */
 } bridge_mg_params;
 
 /* Defaults: blocks 4^4, 16 null vectors, setup_tol 5e-2, 1 setup step,
  * 2 SAP cycles, 4 MR steps, coarse_tol 5e-2, coarse_maxiter 200, FP16
- * coarse operator in the coarse solver. */
+ * coarse operator in the coarse solver, even-odd coarse system. */
 void bridge_mg_defaults(bridge_mg_params* p);
 /* Build the multigrid hierarchy for op on the lattice's gauge field.
  * null_vectors: NULL to generate them (solves of random sources), or nvec
@@ -348,8 +352,9 @@ enum bridge_mg_apply_op {
   BRIDGE_MG_COARSE = 2,   /* coarse -> coarse: D_c in (the FP32 coarse operator) */
   BRIDGE_MG_SAP = 3,      /* fine -> fine: sap_cycles SAP cycles on D x = in from x = 0 */
   BRIDGE_MG_CYCLE = 4,    /* fine -> fine: the preconditioner */
-  BRIDGE_MG_COARSE_HALF = 5 /* coarse -> coarse: D_c in with the FP16 copy the coarse solver uses
-                               (EINVAL when the setup ran with coarse_half = 0) */
+  BRIDGE_MG_COARSE_HALF = 5, /* coarse -> coarse: D_c in with the FP16 copy the coarse solver uses
+                                (EINVAL when the setup ran with coarse_half = 0) */
+  BRIDGE_MG_COARSE_SOLVE = 6 /* coarse -> coarse: the coarse solver's approximation of D_c^-1 in */
 };
 int bridge_mg_apply(bridge_mg mg, int which, const double* in, double* out);
 /* The coarse operator: [block][coupling 9][column][row] complex doubles;

@@ -80,11 +80,12 @@ class bridge_mg_params(ctypes.Structure):
         ("coarse_tol", c_double),
         ("coarse_maxiter", c_int),
         ("coarse_half", c_int),
+        ("coarse_eo", c_int),
     ]
 
 
 BRIDGE_MG_RESTRICT, BRIDGE_MG_PROLONG, BRIDGE_MG_COARSE, BRIDGE_MG_SAP, BRIDGE_MG_CYCLE = 0, 1, 2, 3, 4
-BRIDGE_MG_COARSE_HALF = 5
+BRIDGE_MG_COARSE_HALF, BRIDGE_MG_COARSE_SOLVE = 5, 6
 
 
 class bridge_kstat(ctypes.Structure):

@@ -54,17 +54,12 @@ struct HopArgs {
   const char* clovE;  // [parity] clover blocks (T^-1)
   const char* clovM;  // [parity] clover blocks (T)
   RedArgs red;
-  // 0: every site; 1 or 2: only the sites in blocks of extents mb whose block
-  // coordinates sum to an even (1) or odd (2) number (one colour of a
-  // Schwarz blocking); the other sites are neither read nor written.
-  int mcol;
-  int mb[4];
+  // Non-null: compute only the n_map output sites site_map[0 .. n_map) (half-
+  // lattice indices, ascending; e.g. the sites of one colour of a Schwarz
+  // blocking); the other sites are neither read nor written.
+  const uint32_t* site_map;
+  uint32_t n_map;
 };
-
-BR_D bool hop_site_masked(const HopArgs& a, const int c[4]) {
-  return a.mcol != 0 &&
-         ((c[0] / a.mb[0] + c[1] / a.mb[1] + c[2] / a.mb[2] + c[3] / a.mb[3]) & 1) != a.mcol - 1;
-}
 
 template <class R, int MU, bool FWD>
 BR_D void project(const cx<R> p[12], cx<R> h[2][3]) {
@@ -198,11 +193,12 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
     const char* g_in = a.gauge + (long)(1 - p) * 4 * lbb;
     const char* in = a.in + rhs * a.in_rs;
     const uint32_t stride = (uint32_t)a.nblk * blockDim.x;
-    for (uint32_t ih = sb * blockDim.x + threadIdx.x; ih < (uint32_t)vh; ih += stride) {
+    const uint32_t nsite = a.site_map ? a.n_map : (uint32_t)vh;
+    for (uint32_t k = sb * blockDim.x + threadIdx.x; k < nsite; k += stride) {
+      const uint32_t ih = a.site_map ? __ldg(a.site_map + k) : k;
       int c[4];
       uint32_t xh;
       site_coords(a.g, ih, p, c, xh);
-      if (hop_site_masked(a, c)) continue;
       cx<R> acc[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = czero<R>();
@@ -365,11 +361,12 @@ __global__ void __launch_bounds__(256) hop_kernel_mr(const HopArgs a) {
     const char* g_in = a.gauge + (long)(1 - p) * 4 * lbb;
     const char* in = a.in + r0 * a.in_rs;
     const uint32_t stride = (uint32_t)a.nblk * blockDim.x;
-    for (uint32_t ih = sb * blockDim.x + threadIdx.x; ih < (uint32_t)vh; ih += stride) {
+    const uint32_t nsite = a.site_map ? a.n_map : (uint32_t)vh;
+    for (uint32_t k = sb * blockDim.x + threadIdx.x; k < nsite; k += stride) {
+      const uint32_t ih = a.site_map ? __ldg(a.site_map + k) : k;
       int c[4];
       uint32_t xh;
       site_coords(a.g, ih, p, c, xh);
-      if (hop_site_masked(a, c)) continue;
       cx<T> acc[NR][12];
 #pragma unroll
       for (int r = 0; r < NR; ++r)

@@ -239,8 +239,8 @@ struct HopCall {
   CloverSet* clov = nullptr;  // optional: use this set instead of the cache lookup
   bool count_work = true;     // false: count the launch only (work is credited by the caller)
   RedArgs redargs{};
-  int mcol = 0;               // HopArgs::mcol: 0 all sites, 1 / 2 one colour of the blocking mb
-  int mb[4] = {1, 1, 1, 1};
+  const uint32_t* site_map = nullptr;  // HopArgs::site_map / n_map: a subset of the output sites
+  uint32_t n_map = 0;
   double work_fraction = 1.0;  // share of the sites the launch computes (for the byte and flop counts)
 };
 void run_hop(bridge_lattice_s* L, HopCall c, cudaStream_t st);

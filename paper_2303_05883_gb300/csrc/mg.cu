@@ -102,6 +102,7 @@ struct bridge_mg_s {
   std::shared_ptr<CloverSet> clov;
   Field V;  // nv FP32 full fields
   std::unique_ptr<DevBuf> Dc, Dch, cvec, partial;  // Dch: FP16 copy of Dc for the coarse solver
+  std::unique_ptr<DevBuf> Deo;  // FP16 tiles of the even-odd coarse system (null: solve the full system)
   std::unique_ptr<DevBuf> cnbr;                     // [nblocks][9] coarse neighbours
   std::unique_ptr<PinnedBuf> hpart;
   // coarse BiCGStab: scalars, reduction partials and ticket counter
@@ -111,6 +112,9 @@ struct bridge_mg_s {
   int last_coarse_iters = 0;  // iterations of the previous coarse solve (sizes the first batch)
   Field r32, x32, res32;  // fine FP32 work fields of the cycle
   int sap_clover_smem = 1;  // SAP kernel variant (picked by timing at setup)
+  // half-lattice sites of parity p in blocks of colour c: smap[soff[p][c] .. + sn[p][c])
+  std::unique_ptr<DevBuf> smap;
+  long soff[2][2] = {{0, 0}, {0, 0}}, sn[2][2] = {{0, 0}, {0, 0}};
   // error word of the streamed coarse kernel, in the scalar buffer after the BiCGScalars
   int* cerr() const { return reinterpret_cast<int*>(static_cast<char*>(csc->ptr) + 192); }
   float2* cv(int k) const { return reinterpret_cast<float2*>(cvec->ptr) + (long)k * nc; }
@@ -247,8 +251,55 @@ void launch_coarse(int red, int n2, const MgCoarseArgs& a, unsigned grid, cudaSt
   else launch_coarse_red<MG_CR_NONE>(n2, a, grid, st);
 }
 
+// One streamed application of the FP16 tiles T (Dch: D_c; Deo: the even-odd
+// pieces): y = sum_{d0 <= d < d1} T[X][d] x_Y (or b - sum) at the coarse
+// sites of one colour (parity -1: every site), with an optional fused
+// reduction for the coarse BiCGStab.
+void coarse_stream(bridge_mg_s* g, const DevBuf& tiles, int parity, int d0, int d1, const float2* x, float2* y,
+                   const float2* b, int red, const float2* rhat, const float2* xin) {
+  MgCoarseArgs a;
+  std::memset(static_cast<void*>(&a), 0, sizeof(a));
+  a.m = g->m;
+  a.n2 = g->n2;
+  a.Dch = reinterpret_cast<const __half2*>(tiles.ptr);
+  a.nbr = reinterpret_cast<const int*>(g->cnbr->ptr);
+  a.err = g->cerr();
+  a.x = x;
+  a.b = b;
+  a.y = y;
+  a.rhat = rhat;
+  a.xin = xin;
+  a.parity = parity;
+  a.d0 = d0;
+  a.d1 = d1;
+  if (red != MG_CR_NONE) {
+    a.red.partials = reinterpret_cast<double*>(g->cpart->ptr);
+    a.red.counter = reinterpret_cast<unsigned*>(g->ccount->ptr);
+    a.red.sc = reinterpret_cast<BiCGScalars*>(g->csc->ptr);
+    a.red.fin = red == MG_CR_ALPHA ? FIN_ALPHA : FIN_OMEGA;
+    a.red.check_done = 1;
+  }
+  const int sites = parity < 0 ? g->m.nblocks : g->m.nblocks / 2;
+  const double nsite = (double)sites * g->n2;
+  const double bytes = (double)sites * (d1 - d0) * g->n2 * g->n2 * 4 +
+                       8.0 * nsite * (2 + (b ? 1 : 0) + (red != MG_CR_NONE ? 1 : 0));
+  note_launch(g->L, K_MG_COARSE, bytes, (double)sites * (d1 - d0) * g->n2 * g->n2 * 8, stream_of(g), true);
+  if (red == MG_CR_ALPHA)
+    launch_coarse_tma<MG_CR_ALPHA>(g->n2, a, sites, stream_of(g));
+  else if (red == MG_CR_OMEGA)
+    launch_coarse_tma<MG_CR_OMEGA>(g->n2, a, sites, stream_of(g));
+  else
+    launch_coarse_tma<MG_CR_NONE>(g->n2, a, sites, stream_of(g));
+  note_launch(g->L, K_MG_COARSE, bytes, 0, stream_of(g), false);
+  BR_CUDA(cudaGetLastError());
+}
+
 void coarse_apply(bridge_mg_s* g, const float2* x, float2* y, const float2* b = nullptr, int red = MG_CR_NONE,
                   const float2* rhat = nullptr, bool half = false) {
+  if (half && g->Dch && mg_coarse_unrolled(g->n2)) {  // the tiled FP16 copy: streamed by bulk copies
+    coarse_stream(g, *g->Dch, -1, 0, 9, x, y, b, red, rhat, nullptr);
+    return;
+  }
   MgCoarseArgs a;
   std::memset(static_cast<void*>(&a), 0, sizeof(a));
   a.m = g->m;
@@ -256,7 +307,6 @@ void coarse_apply(bridge_mg_s* g, const float2* x, float2* y, const float2* b = 
   a.Dc = reinterpret_cast<const float2*>(g->Dc->ptr);
   a.Dch = (half && g->Dch) ? reinterpret_cast<const __half2*>(g->Dch->ptr) : nullptr;
   a.nbr = reinterpret_cast<const int*>(g->cnbr->ptr);
-  a.err = g->cerr();
   a.x = x;
   a.b = b;
   a.y = y;
@@ -271,16 +321,7 @@ void coarse_apply(bridge_mg_s* g, const float2* x, float2* y, const float2* b = 
   const long n = g->nc;
   const double bytes = (double)g->m.nblocks * 9 * g->n2 * g->n2 * (a.Dch ? 4 : 8) + n * 8.0 * (b ? 3 : 2);
   note_launch(g->L, K_MG_COARSE, bytes, (double)g->m.nblocks * 9 * g->n2 * g->n2 * 8, stream_of(g), true);
-  if (a.Dch && mg_coarse_unrolled(g->n2)) {  // the tiled FP16 copy: streamed by bulk copies
-    if (red == MG_CR_ALPHA)
-      launch_coarse_tma<MG_CR_ALPHA>(g->n2, a, g->m.nblocks, stream_of(g));
-    else if (red == MG_CR_OMEGA)
-      launch_coarse_tma<MG_CR_OMEGA>(g->n2, a, g->m.nblocks, stream_of(g));
-    else
-      launch_coarse_tma<MG_CR_NONE>(g->n2, a, g->m.nblocks, stream_of(g));
-  } else {
-    launch_coarse(red, g->n2, a, (unsigned)((n + 255) / 256), stream_of(g));
-  }
+  launch_coarse(red, g->n2, a, (unsigned)((n + 255) / 256), stream_of(g));
   note_launch(g->L, K_MG_COARSE, bytes, 0, stream_of(g), false);
   BR_CUDA(cudaGetLastError());
 }
@@ -335,7 +376,18 @@ int coarse_solve(bridge_mg_s* g, const float2* rhs) {
   init.max_iter = std::max(1, g->prm.coarse_maxiter);
   init.rho_r = init.alpha_r = init.omega_r = 1.0;
   BR_CUDA(cudaMemcpyAsync(g->csc->ptr, &init, sizeof(init), cudaMemcpyHostToDevice, st));
-  cbicg_step(g, MG_CB_INIT, rhs);
+  const bool eo = g->Deo != nullptr;
+  if (eo) {
+    // even-odd: cv8 = A_O^-1 r_O; cv10 = A_E^-1 r_E - (A^-1 H)_EO cv8 (zero on O),
+    // the right-hand side of the even system; t (cv7) stays zero on O
+    const DevBuf& T = *g->Deo;
+    BR_CUDA(cudaMemsetAsync(g->cv(10), 0, sizeof(float2) * g->nc, st));
+    BR_CUDA(cudaMemsetAsync(g->cv(7), 0, sizeof(float2) * g->nc, st));
+    coarse_stream(g, T, 1, 0, 1, rhs, g->cv(8), nullptr, MG_CR_NONE, nullptr, nullptr);
+    coarse_stream(g, T, 0, 0, 1, rhs, g->cv(10), nullptr, MG_CR_NONE, nullptr, nullptr);
+    coarse_stream(g, T, 0, 1, 9, g->cv(8), g->cv(10), g->cv(10), MG_CR_NONE, nullptr, nullptr);
+  }
+  cbicg_step(g, MG_CB_INIT, eo ? g->cv(10) : rhs);
   // The first batch runs to just short of the previous solve's count without
   // a host poll; later batches are short.  Iterations queued past
   // convergence exit at once (their kernels check the done flag).
@@ -343,11 +395,20 @@ int coarse_solve(bridge_mg_s* g, const float2* rhs) {
   int launched = 0;
   for (;; batch = 4) {
     for (int k = 0; k < batch && launched < g->prm.coarse_maxiter; ++k, ++launched) {
-      coarse_apply(g, g->cv(4), g->cv(5), nullptr, MG_CR_ALPHA, g->cv(3), true);  // v = D_c p, alpha
-      cbicg_step(g, MG_CB_S);                                                    // s = r - alpha v
-      coarse_apply(g, g->cv(6), g->cv(7), nullptr, MG_CR_OMEGA, nullptr, true);  // t = D_c s, omega
-      cbicg_step(g, MG_CB_XR);                                             // x, r; rho, beta
-      cbicg_step(g, MG_CB_P);                                              // p
+      if (eo) {  // the operator 1 - (A^-1 H)_EO (A^-1 H)_OE on E, in two streamed passes
+        const DevBuf& T = *g->Deo;
+        coarse_stream(g, T, 1, 1, 9, g->cv(4), g->cv(9), nullptr, MG_CR_NONE, nullptr, nullptr);
+        coarse_stream(g, T, 0, 1, 9, g->cv(9), g->cv(5), g->cv(4), MG_CR_ALPHA, g->cv(3), nullptr);  // v, alpha
+        cbicg_step(g, MG_CB_S);                                                                   // s
+        coarse_stream(g, T, 1, 1, 9, g->cv(6), g->cv(9), nullptr, MG_CR_NONE, nullptr, nullptr);
+        coarse_stream(g, T, 0, 1, 9, g->cv(9), g->cv(7), g->cv(6), MG_CR_OMEGA, nullptr, g->cv(6));  // t, omega
+      } else {
+        coarse_apply(g, g->cv(4), g->cv(5), nullptr, MG_CR_ALPHA, g->cv(3), true);  // v = D_c p, alpha
+        cbicg_step(g, MG_CB_S);                                                    // s = r - alpha v
+        coarse_apply(g, g->cv(6), g->cv(7), nullptr, MG_CR_OMEGA, nullptr, true);  // t = D_c s, omega
+      }
+      cbicg_step(g, MG_CB_XR);  // x, r; rho, beta
+      cbicg_step(g, MG_CB_P);   // p
     }
     BR_CUDA(cudaMemcpyAsync(g->hcsc->ptr, g->csc->ptr, 256, cudaMemcpyDeviceToHost, st));
     BR_CUDA(cudaStreamSynchronize(st));
@@ -357,6 +418,8 @@ int coarse_solve(bridge_mg_s* g, const float2* rhs) {
       g->coarse_iters += q->iter;
       g->coarse_solves += 1;
       g->last_coarse_iters = q->iter;
+      if (eo)  // e_O = A_O^-1 r_O - (A^-1 H)_OE e_E, into the odd entries of the solution cv1
+        coarse_stream(g, *g->Deo, 1, 1, 9, g->cv(1), g->cv(1), g->cv(8), MG_CR_NONE, nullptr, nullptr);
       return q->iter;
     }
   }
@@ -390,9 +453,9 @@ void fine_residual32(bridge_mg_s* g, const Field& b, const Field& x, const Field
     c.aux = b.ptr(q);
     c.aux_rs = b.rs;
     if (colour >= 0) {
-      c.mcol = colour + 1;
-      for (int k = 0; k < 4; ++k) c.mb[k] = g->m.b[k];
-      c.work_fraction = 0.5;
+      c.site_map = reinterpret_cast<const uint32_t*>(g->smap->ptr) + g->soff[q][colour];
+      c.n_map = (uint32_t)g->sn[q][colour];
+      c.work_fraction = (double)g->sn[q][colour] / (double)g->L->vh;
     }
     run_hop(g->L, c, stream_of(g));
   }
@@ -560,7 +623,7 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
     g->cnbr.reset(new DevBuf(nb.size() * sizeof(int)));
     BR_CUDA(cudaMemcpy(g->cnbr->ptr, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice));
   }
-  g->cvec.reset(new DevBuf((size_t)8 * g->nc * sizeof(float2)));
+  g->cvec.reset(new DevBuf((size_t)11 * g->nc * sizeof(float2)));
   g->partial.reset(new DevBuf(sizeof(double2) * 1024 * 8));
   g->hpart.reset(new PinnedBuf(sizeof(double2) * 1024 * 8));
   g->csc.reset(new DevBuf(256));
@@ -569,6 +632,31 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
   g->cpart.reset(new DevBuf(sizeof(double) * 4 * std::max((g->nc + 255) / 256, coarse_tma_max_grid())));
   g->ccount.reset(new DevBuf(256));
   BR_CUDA(cudaMemsetAsync(g->ccount->ptr, 0, 256, st));
+  // ---- the sites of each parity and block colour (for the SAP residuals)
+  {
+    std::vector<uint32_t> lists[2][2];
+    const int* Ld = L->dims;
+    const uint32_t lxh = (uint32_t)Ld[0] / 2;
+    for (int p = 0; p < 2; ++p)
+      for (int t = 0; t < Ld[3]; ++t)
+        for (int z = 0; z < Ld[2]; ++z)
+          for (int y = 0; y < Ld[1]; ++y)
+            for (uint32_t xh = 0; xh < lxh; ++xh) {
+              const int x = 2 * (int)xh + ((p + y + z + t) & 1);
+              const int col = (x / g->m.b[0] + y / g->m.b[1] + z / g->m.b[2] + t / g->m.b[3]) & 1;
+              const uint32_t ih = xh + lxh * (uint32_t)(y + Ld[1] * (z + Ld[2] * t));
+              lists[p][col].push_back(ih);
+            }
+    std::vector<uint32_t> all;
+    for (int p = 0; p < 2; ++p)
+      for (int c = 0; c < 2; ++c) {
+        g->soff[p][c] = (long)all.size();
+        g->sn[p][c] = (long)lists[p][c].size();
+        all.insert(all.end(), lists[p][c].begin(), lists[p][c].end());
+      }
+    g->smap.reset(new DevBuf(sizeof(uint32_t) * all.size()));
+    BR_CUDA(cudaMemcpy(g->smap->ptr, all.data(), sizeof(uint32_t) * all.size(), cudaMemcpyHostToDevice));
+  }
   const size_t canon = (size_t)L->V * 24;
   // ---- null vectors
   {
@@ -655,6 +743,25 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
                                                    g->n2, mg_coarse_unrolled(g->n2) ? 1 : 0);
       note_launch(L, K_MG_SETUP, 0, 0, st, false);
       BR_CUDA(cudaGetLastError());
+      if (prm.coarse_eo && mg_coarse_unrolled(g->n2)) {
+        // the even-odd tiles: A_X^-1 and A_X^-1 times the hopping couplings, then FP16 tiled
+        const int n2 = g->n2;
+        DevBuf ainv(sizeof(float2) * (size_t)g->m.nblocks * n2 * n2), deo(sizeof(float2) * (size_t)n);
+        const size_t inv_smem = sizeof(float2) * (size_t)(2 * n2 * n2 + n2);
+        note_launch(L, K_MG_SETUP, 0, 0, st, true);
+        mg_invert_self_kernel<<<g->m.nblocks, 256, inv_smem, st>>>(reinterpret_cast<const float2*>(g->Dc->ptr),
+                                                                   reinterpret_cast<float2*>(ainv.ptr), n2);
+        mg_premul_kernel<<<g->m.nblocks, 256, sizeof(float2) * (size_t)n2 * n2, st>>>(
+            reinterpret_cast<const float2*>(g->Dc->ptr), reinterpret_cast<const float2*>(ainv.ptr),
+            reinterpret_cast<float2*>(deo.ptr), n2);
+        g->Deo.reset(new DevBuf(sizeof(__half2) * n));
+        k_mg_to_half<<<grid_for(n), 256, 0, st>>>(reinterpret_cast<const float2*>(deo.ptr),
+                                                     reinterpret_cast<__half2*>(g->Deo->ptr), (long)g->m.nblocks * 9,
+                                                     n2, 1);
+        note_launch(L, K_MG_SETUP, 0, 0, st, false);
+        BR_CUDA(cudaGetLastError());
+        BR_CUDA(cudaStreamSynchronize(st));  // the temporaries are freed on return
+      }
     }
     BR_CUDA(cudaStreamSynchronize(st));
   }
@@ -854,6 +961,11 @@ void mg_apply(bridge_mg_s* g, int which, const double* in, double* out) {
       BR_CUDA(cudaMemcpy(g->hcsc->ptr, g->csc->ptr, 256, cudaMemcpyDeviceToHost));
       check_coarse_err(g);
       break;
+    case BRIDGE_MG_COARSE_SOLVE:
+      c64_to_32(in, reinterpret_cast<float2*>(cin.ptr));
+      coarse_solve(g, reinterpret_cast<float2*>(cin.ptr));
+      c32_to_64(g->cv(1), out);
+      break;
     case BRIDGE_MG_SAP:
       canon_to_field(L, in, g->r32, st);
       BR_CUDA(cudaMemsetAsync(g->x32.buf->ptr, 0, g->x32.buf->bytes, st));
@@ -900,6 +1012,7 @@ void bridge_mg_defaults(bridge_mg_params* p) {
   p->coarse_tol = 5e-2;
   p->coarse_maxiter = 200;
   p->coarse_half = 1;
+  p->coarse_eo = 1;
 }
 
 int bridge_mg_setup(bridge_lattice L, const bridge_op* op, const bridge_mg_params* prm, const double* null_vectors,

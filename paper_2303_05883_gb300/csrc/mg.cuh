@@ -53,6 +53,16 @@ BR_HD int mg_block_colour(const MgGeom& m, int blk) {
   return s & 1;
 }
 
+// The k-th block of one colour (the grid covers that colour only): with an
+// even number of blocks along x, every row of blocks (fixed y, z, t block
+// coordinates) holds cd[0] / 2 of each colour.
+BR_HD int mg_colour_block(const MgGeom& m, int colour, int k) {
+  const int half = m.cd[0] / 2;
+  const int R = k / half, bx2 = k % half;
+  const int s = R % m.cd[1] + (R / m.cd[1]) % m.cd[2] + R / (m.cd[1] * m.cd[2]);
+  return 2 * bx2 + ((s + colour) & 1) + m.cd[0] * R;
+}
+
 // Coarse neighbour of block blk at +mu (dir = +1) or -mu (dir = -1), periodic.
 BR_HD int mg_block_nbr(const MgGeom& m, int blk, int mu, int dir) {
   int bc[4], r = blk;
@@ -298,6 +308,11 @@ struct MgCoarseArgs {
   RedArgs red;
   int* err;     // mg_coarse_tma_kernel: set to 1 if a tile copy did not arrive in time
   int stages;   // mg_coarse_tma_kernel: tile buffers in shared memory (2 .. 4)
+  // mg_coarse_tma_kernel only: the coarse sites of one colour (parity 0 / 1,
+  // -1 all sites), the couplings d0 .. d1 - 1 summed, and the vector of the
+  // MG_CR_OMEGA dot <y, xin> (null: x).
+  int parity, d0, d1;
+  const float2* xin;
 };
 
 enum MgCoarseRed { MG_CR_NONE = 0, MG_CR_ALPHA = 1, MG_CR_OMEGA = 2 };
@@ -422,14 +437,18 @@ __global__ void __launch_bounds__(256) mg_coarse_kernel(const MgCoarseArgs a) {
 }
 
 // The same operator from the tiled FP16 copy, streamed by the bulk-copy
-// engine: a persistent CTA walks its coarse sites (blockIdx.x, + gridDim.x,
-// ...); the 9 * N2 * N2 FP16 entries of a site are contiguous, so one bulk
-// copy per site moves them into one of `stages` shared-memory buffers while
-// the CTA computes on the previous ones.  Thread (d, row) forms the row sum
-// of coupling d from shared memory against x at the coupled site (staged in
+// engine: a persistent CTA walks its coarse sites (the k-th site of its
+// share: k = blockIdx.x, + gridDim.x, ...); the 9 * N2 * N2 FP16 entries of
+// a site are contiguous, so one bulk copy per site (of the couplings d0 ..
+// d1 - 1) moves them into one of `stages` shared-memory buffers while the
+// CTA computes on the previous ones.  Thread (d, row) forms the row sum of
+// coupling d from shared memory against x at the coupled site (staged in
 // shared memory, its loads issued one site ahead), and N2 threads add the
-// nine couplings.  Coarse sites of a converged solve (red.sc->done) are
-// skipped.
+// couplings: y = sum, or y = b - sum.  With a colour (parity >= 0) only that
+// colour's sites are visited, which with the even-odd tiles (slot 0 =
+// A^-1, slots 1..8 = A^-1 times the hopping couplings) applies the pieces
+// of the even-odd preconditioned coarse system.  Coarse sites of a
+// converged solve (red.sc->done) are skipped.
 template <int N2>
 __host__ __device__ constexpr long mg_coarse_tile_bytes() { return 9L * (N2 / 4) * N2 * 16; }
 
@@ -442,12 +461,16 @@ __global__ void __launch_bounds__(256) mg_coarse_tma_kernel(const MgCoarseArgs a
   __shared__ __align__(8) uint64_t bar[4];
   __shared__ float2 xs[9 * N2];
   __shared__ float2 part[9 * N2];
+  constexpr long CT = TILE / 9;  // bytes of one coupling
   const int tid = threadIdx.x, nt = blockDim.x;
   const int stages = a.stages;
   const bool skip = RED != MG_CR_NONE && a.red.sc != nullptr && a.red.sc[0].done != RUNNING;
-  const int nb = a.m.nblocks, first = blockIdx.x, step = gridDim.x;
-  const int mine = (skip || first >= nb) ? 0 : (nb - first + step - 1) / step;
-  const char* src = reinterpret_cast<const char*>(a.Dch);
+  const int nsites = a.parity < 0 ? a.m.nblocks : a.m.nblocks / 2, first = blockIdx.x, step = gridDim.x;
+  const int mine = (skip || first >= nsites) ? 0 : (nsites - first + step - 1) / step;
+  const int d0 = a.d0, nd = a.d1 - a.d0;
+  const uint32_t cbytes = (uint32_t)(nd * CT);
+  auto site = [&](int k) { return a.parity < 0 ? k : mg_colour_block(a.m, a.parity, k); };
+  const char* src = reinterpret_cast<const char*>(a.Dch) + d0 * CT;
   double rv[3] = {0.0, 0.0, 0.0};
   if (tid == 0) {
     for (int k = 0; k < stages; ++k) mbar_init(&bar[k], 1);
@@ -456,8 +479,8 @@ __global__ void __launch_bounds__(256) mg_coarse_tma_kernel(const MgCoarseArgs a
   __syncthreads();
   if (tid == 0)
     for (int k = 0; k < stages && k < mine; ++k) {
-      const int X = first + k * step;
-      bulk_load(dsm + k * TILE, src + (long)X * TILE, (uint32_t)TILE, &bar[k]);
+      const int X = site(first + k * step);
+      bulk_load(dsm + k * TILE, src + (long)X * TILE, cbytes, &bar[k]);
     }
   // x at the coupled sites of the first site (two entries per thread at most)
   float2 xn[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
@@ -465,28 +488,28 @@ __global__ void __launch_bounds__(256) mg_coarse_tma_kernel(const MgCoarseArgs a
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int i = tid + q * nt;
-      if (i < 9 * N2) {
-        const int Y = __ldg(a.nbr + X * 9 + i / N2);
+      if (i < nd * N2) {
+        const int Y = __ldg(a.nbr + X * 9 + d0 + i / N2);
         xn[q] = __ldg(a.x + (long)Y * N2 + i % N2);
       }
     }
   };
-  if (mine > 0) load_x(first);
+  if (mine > 0) load_x(site(first));
   bool failed = false;
   int it = 0;
   for (; it < mine; ++it) {
-    const int X = first + it * step, buf = it % stages;
+    const int X = site(first + it * step), buf = it % stages;
 #pragma unroll
     for (int q = 0; q < 2; ++q)
-      if (tid + q * nt < 9 * N2) xs[tid + q * nt] = xn[q];
-    if (it + 1 < mine) load_x(X + step);
+      if (tid + q * nt < nd * N2) xs[tid + q * nt] = xn[q];
+    if (it + 1 < mine) load_x(site(first + (it + 1) * step));
     // operands of this site's epilogue, loaded before the wait
     float2 eb = make_float2(0.f, 0.f), ev = make_float2(0.f, 0.f);
     if (tid < N2) {
       const long t = (long)X * N2 + tid;
       if (a.b) eb = a.b[t];
       if (RED == MG_CR_ALPHA) ev = a.rhat[t];
-      if (RED == MG_CR_OMEGA) ev = a.x[t];
+      if (RED == MG_CR_OMEGA) ev = a.xin ? a.xin[t] : a.x[t];
     }
     const bool ok = mbar_wait(&bar[buf], (uint32_t)((it / stages) & 1));
     if (!__syncthreads_and(ok)) {
@@ -494,7 +517,7 @@ __global__ void __launch_bounds__(256) mg_coarse_tma_kernel(const MgCoarseArgs a
       break;
     }
     const uint4* tile = reinterpret_cast<const uint4*>(dsm + buf * TILE);
-    for (int p = tid; p < 9 * N2; p += nt) {
+    for (int p = tid; p < nd * N2; p += nt) {
       const int d = p / N2, row = p % N2;
       const float2* xv = xs + d * N2;
       cx<float> s0 = czero<float>(), s1 = czero<float>();
@@ -517,12 +540,11 @@ __global__ void __launch_bounds__(256) mg_coarse_tma_kernel(const MgCoarseArgs a
     __syncthreads();  // buffer `buf` and xs are free again
     if (tid == 0 && it + stages < mine) {
       fence_proxy_async_smem();
-      bulk_load(dsm + buf * TILE, src + (long)(X + stages * step) * TILE, (uint32_t)TILE, &bar[buf]);
+      bulk_load(dsm + buf * TILE, src + (long)site(first + (it + stages) * step) * TILE, cbytes, &bar[buf]);
     }
     if (tid < N2) {
       cx<float> sv = czero<float>();
-#pragma unroll
-      for (int d = 0; d < 9; ++d) sv = sv + cx<float>{part[d * N2 + tid].x, part[d * N2 + tid].y};
+      for (int d = 0; d < nd; ++d) sv = sv + cx<float>{part[d * N2 + tid].x, part[d * N2 + tid].y};
       const long t = (long)X * N2 + tid;
       if (a.b) sv = cx<float>{eb.x, eb.y} - sv;
       a.y[t] = make_float2(sv.r, sv.i);
@@ -545,6 +567,102 @@ __global__ void __launch_bounds__(256) mg_coarse_tma_kernel(const MgCoarseArgs a
   }
   if (RED == MG_CR_ALPHA) reduce_finalize<2>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
   if (RED == MG_CR_OMEGA) reduce_finalize<3>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
+}
+
+// ---- even-odd preconditioning of the coarse system (setup)
+// With E / O the coarse sites of the two colours (every hopping coupling
+// joins opposite colours), D_c = [[A_E, H_EO], [H_OE, A_O]] with A the
+// self couplings; the even-odd system is
+//   (1 - A_E^-1 H_EO A_O^-1 H_OE) e_E = A_E^-1 r_E - A_E^-1 H_EO A_O^-1 r_O,
+//   e_O = A_O^-1 r_O - A_O^-1 H_OE e_E.
+// Its tiles hold A_X^-1 in slot 0 and A_X^-1 times each hopping coupling in
+// slots 1..8.
+
+// A_X^-1 for every coarse site by Gauss-Jordan elimination with partial
+// pivoting on [A | 1] in shared memory (row-major, n x 2n), one CTA per site.
+// Dc and Ainv are column-major (entry (row, col) at col * n + row).
+__global__ void __launch_bounds__(256) mg_invert_self_kernel(const float2* Dc, float2* Ainv, int n) {
+  extern __shared__ __align__(16) unsigned char dsm_inv[];
+  float2* M = reinterpret_cast<float2*>(dsm_inv);  // [n][2n]
+  float2* f = M + 2L * n * n;                      // [n] elimination factors
+  __shared__ int piv;
+  const int X = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, w = 2 * n;
+  const float2* A = Dc + (long)X * 9 * n * n;  // coupling 0
+  for (int i = tid; i < n * w; i += nt) {
+    const int r = i / w, c = i % w;
+    M[i] = c < n ? A[(long)c * n + r] : make_float2(c - n == r ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      int best = k;
+      float bv = -1.f;
+      for (int r = k; r < n; ++r) {
+        const float2 v = M[r * w + k];
+        const float m2 = v.x * v.x + v.y * v.y;
+        if (m2 > bv) {
+          bv = m2;
+          best = r;
+        }
+      }
+      piv = best;
+    }
+    __syncthreads();
+    const int pr = piv;
+    if (pr != k)
+      for (int c = tid; c < w; c += nt) {
+        const float2 t = M[k * w + c];
+        M[k * w + c] = M[pr * w + c];
+        M[pr * w + c] = t;
+      }
+    __syncthreads();
+    const float2 pv = M[k * w + k];
+    const float den = pv.x * pv.x + pv.y * pv.y;
+    const cx<float> inv{pv.x / den, -pv.y / den};
+    __syncthreads();  // every thread has the pivot before row k changes
+    for (int c = tid; c < w; c += nt) {
+      const cx<float> v = cx<float>{M[k * w + c].x, M[k * w + c].y} * inv;
+      M[k * w + c] = make_float2(v.r, v.i);
+    }
+    __syncthreads();
+    for (int r = tid; r < n; r += nt) f[r] = M[r * w + k];
+    __syncthreads();
+    for (int i = tid; i < n * w; i += nt) {
+      const int r = i / w, c = i % w;
+      if (r != k) {
+        const cx<float> v = cx<float>{M[i].x, M[i].y} - cx<float>{f[r].x, f[r].y} * cx<float>{M[k * w + c].x, M[k * w + c].y};
+        M[i] = make_float2(v.r, v.i);
+      }
+    }
+    __syncthreads();
+  }
+  float2* out = Ainv + (long)X * n * n;
+  for (int i = tid; i < n * n; i += nt) {
+    const int c = i / n, r = i % n;
+    out[i] = M[r * w + n + c];
+  }
+}
+
+// Deo[X][0] = A_X^-1, Deo[X][d] = A_X^-1 Dc[X][d] for d = 1..8 (column-major
+// n x n each); one CTA per coarse site, A_X^-1 in shared memory.
+__global__ void __launch_bounds__(256) mg_premul_kernel(const float2* Dc, const float2* Ainv, float2* Deo, int n) {
+  extern __shared__ __align__(16) unsigned char dsm_pm[];
+  float2* sa = reinterpret_cast<float2*>(dsm_pm);
+  const int X = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, nn = n * n;
+  for (int i = tid; i < nn; i += nt) sa[i] = Ainv[(long)X * nn + i];
+  __syncthreads();
+  float2* out = Deo + (long)X * 9 * nn;
+  for (int i = tid; i < 9 * nn; i += nt) {
+    const int d = i / nn, rem = i % nn, c = rem / n, r = rem % n;
+    if (d == 0) {
+      out[i] = sa[rem];
+      continue;
+    }
+    const float2* Md = Dc + ((long)X * 9 + d) * nn + (long)c * n;  // column c of coupling d
+    cx<float> acc = czero<float>();
+    for (int k = 0; k < n; ++k) acc = cfma(cx<float>{sa[k * n + r].x, sa[k * n + r].y}, cx<float>{Md[k].x, Md[k].y}, acc);
+    out[i] = make_float2(acc.r, acc.i);
+  }
 }
 
 // Coarse BiCGStab vector steps with the scalars on the device (BiCGScalars,
@@ -613,16 +731,6 @@ struct MgSapArgs {
   const char* gauge;
   const char* clov;
 };
-
-// The k-th block of one colour (the grid covers that colour only): with an
-// even number of blocks along x, every row of blocks (fixed y, z, t block
-// coordinates) holds cd[0] / 2 of each colour.
-BR_D int mg_colour_block(const MgGeom& m, int colour, int k) {
-  const int half = m.cd[0] / 2;
-  const int R = k / half, bx2 = k % half;
-  const int s = R % m.cd[1] + (R / m.cd[1]) % m.cd[2] + R / (m.cd[1] * m.cd[2]);
-  return 2 * bx2 + ((s + colour) & 1) + m.cd[0] * R;
-}
 
 // Dynamic shared memory of mg_sap_kernel: rho, the 4 forward links (all 18
 // reals) and, with CS, the clover term (72 reals) of every site of the block.

@@ -295,8 +295,8 @@ void run_hop(bridge_lattice_s* L, HopCall c, cudaStream_t st) {
     if (a.red.fin == FIN_NONE) a.red.fin = FIN_STORE;
   }
   const HopCost hc = hop_cost(c.prec, c.flags, c.red);
-  a.mcol = c.mcol;
-  for (int k = 0; k < 4; ++k) a.mb[k] = std::max(1, c.mb[k]);
+  a.site_map = c.site_map;
+  a.n_map = c.n_map;
   const double bytes =
       c.count_work ? c.work_fraction * (double)L->vh * (hc.rhs_bytes * c.nrhs + hc.shared_bytes) : 0.0;
   const double flops = c.count_work ? c.work_fraction * (double)L->vh * c.nrhs * hc.rhs_flops : 0.0;
