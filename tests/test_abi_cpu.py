@@ -71,6 +71,12 @@ def test_strerror_and_defaults(built):
     assert "converge" in api.bridge_strerror(-3)
     s = api.make_solver()
     assert s.tol == 1e-10 and s.mixed == 1 and s.check_every == 16
+    m = api.make_mg_params()
+    assert list(m.block) == [4, 4, 4, 4] and m.nvec == 16 and m.setup_steps == 1
+    assert (m.sap_cycles, m.mr_steps, m.coarse_maxiter) == (2, 4, 200)
+    assert m.coarse_tol == 5e-2 and m.coarse_half == 1 and m.coarse_eo == 1
+    m = api.make_mg_params(block=(2, 2, 4, 4), nvec=12, coarse_eo=0, coarse_tol=0.1)
+    assert list(m.block) == [2, 2, 4, 4] and m.nvec == 12 and m.coarse_eo == 0 and m.coarse_tol == 0.1
 
 
 def test_invalid_extents_rejected(built):
