@@ -6,12 +6,15 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_reference_arm_prints_contract_line():
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
-                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+@pytest.mark.parametrize("workload", ["clover_32x32x32x64", "mobius_24x24x24x48x16", "staggered_32x32x32x32"])
+def test_reference_arm_prints_contract_line(workload):
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", workload, "--steps", "1",
+                          "--warmup", "0", "--oracle-sites", "1024"], cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [x for x in out.stdout.splitlines() if x.startswith("{")]
     assert len(lines) == 1
@@ -24,4 +27,4 @@ def test_reference_arm_prints_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"] == "clover_32x32x32x64"
+    assert d["config"]["workload"] == workload
