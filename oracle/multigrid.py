@@ -26,7 +26,13 @@ space vectors.  It prints no algorithmic detail beyond that.  Readings taken
 * the cycle M r: e_c = (approximate) solution of D_c e_c = P^dag r; z = P e_c;
   then z += SAP(r - D z) (post-smoothing only);
 * FBiCGStab: BiCGStab with the preconditioner applied to the search
-  directions (p^ = M p, s^ = M s), so M may change between applications.
+  directions (p^ = M p, s^ = M s), so M may change between applications;
+* the coarse BiCGStab may run on the even-odd preconditioned coarse system
+  (coarse sites split by the parity of their block coordinates, which every
+  hopping coupling of D_c flips): with A the self couplings and H the
+  hopping part, (1 - A_E^-1 H_EO A_O^-1 H_OE) e_E = A_E^-1 (r_E - H_EO
+  A_O^-1 r_O) and e_O = A_O^-1 (r_O - H_OE e_E) (the paper names BiCGStab
+  for the coarse grid and does not say whether it is preconditioned).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 """
@@ -145,6 +151,29 @@ class Multigrid:
             M[:, k] = self.restrict(self.D(self.prolong(e.reshape(-1, 2, self.nv)))).reshape(-1)
         self._Dc = M
         return M
+
+    def coarse_evenodd_solve(self, rc, tol=1e-12, maxiter=5000):
+        """D_c e = rc through the even-odd preconditioned coarse system (see the
+        module docstring), BiCGStab on the even sites; built from the dense D_c."""
+        from . import solvers
+
+        Dc = self.coarse_dense()
+        colour = np.repeat(self.blocks.colour, 2 * self.nv)
+        E, O = colour == 0, colour == 1
+        A_E, H_EO = Dc[np.ix_(E, E)], Dc[np.ix_(E, O)]
+        H_OE, A_O = Dc[np.ix_(O, E)], Dc[np.ix_(O, O)]
+        r = rc.reshape(-1)
+        AOinv_rO = np.linalg.solve(A_O, r[O])
+        rhs = np.linalg.solve(A_E, r[E] - H_EO @ AOinv_rO)
+
+        def schur(v):
+            return v - np.linalg.solve(A_E, H_EO @ np.linalg.solve(A_O, H_OE @ v))
+
+        e_E, info = solvers.bicgstab(schur, rhs, tol=tol, maxiter=maxiter)
+        e = np.zeros_like(r)
+        e[E] = e_E
+        e[O] = np.linalg.solve(A_O, r[O] - H_OE @ e_E)
+        return e.reshape(rc.shape), info
 
     # --- SAP smoother -----------------------------------------------------------------
     def mr(self, rb, colour, steps):

@@ -608,3 +608,23 @@ def mg_solve_error():
     x1, i1 = multigrid.fbicgstab(mg.D, lambda r: r, b, tol=1e-12, maxiter=500)
     x2, i2 = solvers.bicgstab(mg.D, b, tol=1e-12, maxiter=500)
     return max(err, rel(x1, x_lu), float(abs(i1["iters"] - i2["iters"]) > 1))
+
+
+def mg_coarse_evenodd_error():
+    """Every hopping coupling of D_c joins coarse sites of opposite colour (the
+    same-colour blocks of the dense P^dag M P hold only the self couplings), and
+    the even-odd coarse solve reaches the LU solution of the full coarse system."""
+    lat, U, mg = _mg_case(nv=3, kappa=0.12)
+    P = _dense_P(mg)
+    M = solvers.dense_dirac(U, lat, mg.kappa, mg.csw)
+    Dc = P.conj().T @ M @ P
+    n2 = 2 * mg.nv
+    colour = np.repeat(mg.blocks.colour, n2)
+    site = np.repeat(np.arange(mg.blocks.nblocks), n2)
+    same_colour_other_site = (colour[:, None] == colour[None, :]) & (site[:, None] != site[None, :])
+    err = float(np.abs(Dc[same_colour_other_site]).max() / np.abs(Dc).max())
+    gen = np.random.default_rng(23)
+    rc = gen.standard_normal((mg.blocks.nblocks, 2, mg.nv)) + 1j * gen.standard_normal((mg.blocks.nblocks, 2, mg.nv))
+    e, info = mg.coarse_evenodd_solve(rc, tol=1e-13)
+    return max(err, rel(e.reshape(-1), np.linalg.solve(Dc, rc.reshape(-1))))
+

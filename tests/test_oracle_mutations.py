@@ -77,6 +77,10 @@ MUTANTS = [
     ("multigrid", "return z + self.sap(r - self.D(z), cycles, mr_steps)", "return z + self.sap(r, cycles, mr_steps)",
      pins.mg_cycle_error, 1e-10),
     ("multigrid", "x = x + alpha * ph + omega * sh", "x = x + alpha * p + omega * s", pins.mg_solve_error, 1e-10),
+    ("multigrid", "e[O] = np.linalg.solve(A_O, r[O] - H_OE @ e_E)", "e[O] = np.linalg.solve(A_O, r[O] + H_OE @ e_E)",
+     pins.mg_coarse_evenodd_error, 1e-10),
+    ("multigrid", "rhs = np.linalg.solve(A_E, r[E] - H_EO @ AOinv_rO)", "rhs = np.linalg.solve(A_E, r[E])",
+     pins.mg_coarse_evenodd_error, 1e-10),
     # staggered
     ("staggered", "for nu in range(mu):", "for nu in range(mu + 1):", pins.staggered_free_field_error, 1e-10),
     ("staggered", "out -= 0.5 * e * np.einsum", "out += 0.5 * e * np.einsum", pins.staggered_free_field_error, 1e-10),

@@ -240,3 +240,8 @@ def test_mg_cycle_composition():
 
 def test_mg_fbicgstab_solve():
     assert pins.mg_solve_error() < 1e-10
+
+
+def test_mg_coarse_evenodd_solve():
+    assert pins.mg_coarse_evenodd_error() < 1e-10
+
