@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 import synth  # noqa: E402
-from oracle import dirac, domainwall, evenodd, solvers, staggered  # noqa: E402
+from oracle import dirac, domainwall, evenodd, multigrid, solvers, staggered  # noqa: E402
 from oracle.lattice import Lattice  # noqa: E402
 
 DIMS = (2, 2, 2, 4)
@@ -37,6 +37,11 @@ def cases():
     psi5 = synth.gaussian_spinor(DIMS, SEED, nrhs=4)
     stg = staggered.Staggered(U, lat, 0.1)
     chi = psi[:, 0, :]
+    # two-level multigrid: blocks 1x1x1x2 (2^4 coarse sites), the two null
+    # vectors a seeded Gaussian pair; the cycle (exact coarse solve, 2 SAP
+    # cycles of 4 MR steps) and the even-odd coarse solve of the restricted source
+    mg = multigrid.Multigrid(U, lat, KAPPA, CSW, (1, 1, 1, 2), synth.gaussian_spinor(DIMS, SEED + 1, nrhs=2))
+    mg_eo, _ = mg.coarse_evenodd_solve(mg.restrict(psi), tol=1e-14)
     return {
         "wilson_D": dirac.wilson(U, psi, lat, KAPPA),
         "clover_D": dirac.dirac(U, psi, lat, KAPPA, CSW),
@@ -46,6 +51,8 @@ def cases():
         "mobius_Dhat_dag": mob.schur_dag(psi5[:, lat.even]),
         "staggered_D": stg.full(chi),
         "staggered_Dhat": stg.schur(chi[lat.even]),
+        "mg_cycle": mg.cycle(psi, 2, 4),
+        "mg_coarse_eo_solve": mg_eo,
     }
 
 
@@ -55,6 +62,7 @@ def write():
         with open(os.path.join(HERE, f"{name}_2x2x2x4.txt"), "w") as f:
             f.write(f"# oracle {name}: lattice {DIMS}, kappa {KAPPA}, c_sw {CSW}, links exp({EPS} i A) seed {SEED},\n")
             f.write("# Moebius Ls 4, M5 1.8, b 1.5, c 0.5, m_f 0.1; staggered m 0.1 (spin-0 components of the source);\n")
+            f.write("# multigrid blocks 1x1x1x2, null vectors Gaussian seed 2025 (2 of them), 2 SAP cycles x 4 MR steps;\n")
             f.write("# Gaussian source seed 2024 (synth); written by tests/golden/make_golden.py from oracle/ only.\n")
             f.write("# one complex number per line: real imag (canonical order [site][spin][colour])\n")
             for z in flat:

@@ -21,7 +21,7 @@ def load(name):
 
 
 @pytest.mark.parametrize("name", ["wilson_D", "clover_D", "schur_Dhat", "solution", "mobius_D", "mobius_Dhat_dag",
-                                  "staggered_D", "staggered_Dhat"])
+                                  "staggered_D", "staggered_Dhat", "mg_cycle", "mg_coarse_eo_solve"])
 def test_oracle_matches_golden(name):
     got = np.asarray(make_golden.cases()[name]).reshape(-1)
     want = load(name)
