@@ -458,9 +458,12 @@ __global__ void __launch_bounds__(256) hop_kernel_mr(const HopArgs a) {
 // nothing is launched: *occ receives the resident blocks per SM instead.
 // variant v in [0, 6): register budget {none, 80, 64}[v % 3] and, for v >= 3,
 // read-once operands loaded around L1; v in {6, 7, 8}: 2, 3 or 4 right-hand
-// sides per thread (hop_kernel_mr; grid = nblk x ceil(nrhs / NR)).  Only the
-// kernels of the Schur passes, D_eo and the FP64 residual have variants
-// other than 0, and only FP32/FP16/BF16 have the multi-RHS ones.
+// sides per thread (hop_kernel_mr; grid = nblk x ceil(nrhs / NR)); v in
+// {9, 10}: the shared-link tile kernel (hop_kernel_tile, 32-site tiles for
+// up to 12 right-hand sides per block, one / two tiles staged per barrier;
+// grid = nblk x ceil(nrhs / 12), the block size is its own).
+// Only the kernels of the Schur passes, D_eo and the FP64 residual have
+// variants other than 0, and only FP32/FP16/BF16 have the multi-RHS ones.
 template <int P>
 bool launch_hop(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ = nullptr, int variant = 0);
 template <>
@@ -472,7 +475,11 @@ bool launch_hop<P_F16>(int flags, int red, const HopArgs& a, int block, cudaStre
 template <>
 bool launch_hop<P_BF16>(int flags, int red, const HopArgs& a, int block, cudaStream_t st, int* occ, int variant);
 bool hop_has_variants(int flags, int red);
-// right-hand sides per thread of a variant (1 for v < 6)
-inline int hop_variant_rpt(int variant) { return variant >= 6 ? variant - 4 : 1; }
+// Right-hand sides covered by one block group of a variant: 1 for v < 6, NR
+// for the NR-per-thread kernels (v = 6, 7, 8) and up to 12 for the
+// shared-link tile kernels (v = 9, 10; dslash_tile.cuh).
+inline int hop_variant_rpt(int variant) { return variant >= 9 ? 12 : variant >= 6 ? variant - 4 : 1; }
+constexpr int HOP_NVARIANT = 11;
+inline bool hop_variant_is_tile(int variant) { return variant >= 9; }
 
 }  // namespace bridge

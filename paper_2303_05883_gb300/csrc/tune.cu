@@ -108,7 +108,9 @@ static std::vector<Candidate> candidates(long vh, int nrhs, const std::vector<in
   std::vector<Candidate> out;
   for (int v : variants) {
     const int groups = (nrhs + hop_variant_rpt(v) - 1) / hop_variant_rpt(v);
-    for (int block : {64, 128, 256}) {
+    // the tile kernels choose their own block size: one set of grids
+    const std::vector<int> blocks = hop_variant_is_tile(v) ? std::vector<int>{64} : std::vector<int>{64, 128, 256};
+    for (int block : blocks) {
       const long cover = (vh + block - 1) / block;
       const int per_sm = std::max(1, occ(block, v));
       for (int m : {1, 2}) {
@@ -126,9 +128,12 @@ static std::vector<int> hop_variants(int prec, int flags, int red, int nrhs) {
   if (!hop_has_variants(flags, red)) return v;
   for (int k = 1; k < 6; ++k) v.push_back(k);
   const bool residual = (flags & F_SELF_CLOV) != 0;
-  if (prec != P_F64 && !residual)
+  if (prec != P_F64 && !residual) {
     for (int k = 6; k < 9; ++k)
       if (hop_variant_rpt(k) <= nrhs) v.push_back(k);
+    if (nrhs >= 2)
+      for (int k = 9; k < HOP_NVARIANT; ++k) v.push_back(k);
+  }
   return v;
 }
 
@@ -313,7 +318,7 @@ extern "C" int bridge_tune(bridge_lattice L, const bridge_op* op, int prec, int 
 
 extern "C" int bridge_tune_set(bridge_lattice L, const char* key, int block, int nblk, int variant) {
   // block >= 64: the solver sizes its reduction partials for at most vh / 64 site blocks
-  if (!L || !key || block < 64 || block > 256 || block % 32 || nblk < 1 || variant < 0 || variant > 8)
+  if (!L || !key || block < 64 || block > 256 || block % 32 || nblk < 1 || variant < 0 || variant >= HOP_NVARIANT)
     return BRIDGE_EINVAL;
   std::lock_guard<std::mutex> lk(L->tune_mu);
   L->tuned[key] = LaunchShape{block, nblk, variant};

@@ -24,6 +24,13 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def site_max(a, b):
+    """Largest per-site error over the RMS per-site norm of b ((sites, 4, 3))."""
+    e = np.linalg.norm((a - b).reshape(a.shape[0], -1), axis=1)
+    n = np.linalg.norm(b.reshape(b.shape[0], -1), axis=1)
+    return float(e.max() / np.sqrt(np.mean(n ** 2)))
+
+
 def sample_sites(lat, n, seed, parity=None):
     gen = np.random.default_rng(seed)
     L = lat.dims
@@ -59,39 +66,55 @@ def c2(api):
     L.close()
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
 def test_full_operator_sampled_32x32x32x64(c2, prec):
     w, lat, U, b = c2["w"], c2["lat"], c2["U"], c2["b"]
     got = c2["L"].D(c2["op"], b, prec)
     s = sample_sites(lat, 1500, 1)
     want = dirac.dirac(U, b, lat, w.kappa, w.csw, w.bc, sites=s)
     assert rel(got[s], want) < TOL[prec]
+    assert site_max(got[s], want) < 10 * TOL[prec]
 
 
-def test_deo_sampled_32x32x32x64(c2):
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_deo_sampled_32x32x32x64(c2, prec):
     w, lat, U, b = c2["w"], c2["lat"], c2["U"], c2["b"]
-    got = c2["L"].Deo(c2["op"], np.ascontiguousarray(b[lat.odd]), 0, "f32")  # D_eo psi_o
+    got = c2["L"].Deo(c2["op"], np.ascontiguousarray(b[lat.odd]), 0, prec)  # D_eo psi_o
     s = sample_sites(lat, 1500, 2, parity=0)
     full = lat.embed(b[lat.odd], 1)
     want = -w.kappa * dirac.hop(U, full, lat, w.bc, sites=s)
-    assert rel(got[s // 2], want) < TOL["f32"]
+    assert rel(got[s // 2], want) < TOL[prec]
+    assert site_max(got[s // 2], want) < 10 * TOL[prec]
 
 
-def test_schur_sampled_32x32x32x64(c2):
-    """D^(eo) x_e at sampled even sites, built by the oracle from its neighbour set."""
-    w, lat, U, b = c2["w"], c2["lat"], c2["U"], c2["b"]
-    xe = np.ascontiguousarray(b[lat.even])
-    got = c2["L"].Dhat(c2["op"], xe, "f32")
-    s = sample_sites(lat, 400, 3, parity=0)
+def schur_at(lat, U, w, full_e, s):
+    """The oracle's D^(eo) x_e at even sites s, from x_e at their next-nearest
+    neighbourhood (full_e: a full-lattice array holding x_e there)."""
     ys = np.unique(np.concatenate([lat.neighbor(s, mu, st)[0] for mu in range(4) for st in (1, -1)]))
-    full_e = lat.embed(xe, 0)
     Tinv_y = np.linalg.inv(dirac.clover_term(U, lat, w.kappa, w.csw, ys))
     tmp = dirac.apply_site(Tinv_y, -w.kappa * dirac.hop(U, full_e, lat, w.bc, sites=ys))
     tmp_full = np.zeros_like(full_e)
     tmp_full[ys] = tmp
     Tinv_s = np.linalg.inv(dirac.clover_term(U, lat, w.kappa, w.csw, s))
-    want = full_e[s] - dirac.apply_site(Tinv_s, -w.kappa * dirac.hop(U, tmp_full, lat, w.bc, sites=s))
-    assert rel(got[s // 2], want) < TOL["f32"]
+    return full_e[s] - dirac.apply_site(Tinv_s, -w.kappa * dirac.hop(U, tmp_full, lat, w.bc, sites=s))
+
+
+def neighbourhood(lat, s):
+    """s, its eight neighbours and theirs."""
+    ys = np.unique(np.concatenate([lat.neighbor(s, mu, st)[0] for mu in range(4) for st in (1, -1)]))
+    return np.unique(np.concatenate([lat.neighbor(ys, mu, st)[0] for mu in range(4) for st in (1, -1)] + [s]))
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_schur_sampled_32x32x32x64(c2, prec):
+    """D^(eo) x_e at sampled even sites, built by the oracle from its neighbour set."""
+    w, lat, U, b = c2["w"], c2["lat"], c2["U"], c2["b"]
+    xe = np.ascontiguousarray(b[lat.even])
+    got = c2["L"].Dhat(c2["op"], xe, prec)
+    s = sample_sites(lat, 400, 3, parity=0)
+    want = schur_at(lat, U, w, lat.embed(xe, 0), s)
+    assert rel(got[s // 2], want) < TOL[prec]
+    assert site_max(got[s // 2], want) < 10 * TOL[prec]
 
 
 def test_mixed_solve_32x32x32x64(c2, api):
@@ -108,16 +131,47 @@ def test_mixed_solve_32x32x32x64(c2, api):
     assert rel(Dx[s], b[s] - r) < 1e-13
 
 
-def test_twelve_rhs_f16_48x48x48x96(api):
-    """48^3 x 96, 12 point sources, FP16 storage inner solver, FP64 outer to 1e-10."""
-    import torch
-
+@pytest.fixture(scope="module")
+def c3(api):
     w = synth.WORKLOADS["clover_48x48x48x96_12rhs"]
     lat = Lattice(w.dims)
     U = w.gauge()
     op = api.make_op("clover", w.kappa, w.csw)
     L = api.Lattice(w.dims)
     L.upload(U, op)
+    yield dict(w=w, lat=lat, U=U, op=op, L=L)
+    L.close()
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_schur_twelve_rhs_sampled_48x48x48x96(api, c3, prec):
+    """D^(eo) on 12 Gaussian right-hand sides at 48^3 x 96 in 16-bit storage,
+    with the launch shapes the autotuner picks for the 12-RHS solve, checked
+    at sampled even sites (and the corners) of three right-hand sides."""
+    import torch
+
+    w, lat, U, L, op = c3["w"], c3["lat"], c3["U"], c3["L"], c3["op"]
+    api.bridge_tune(L.handle, op, prec, 12)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    xe = torch.randn((12, lat.V // 2, 4, 3), dtype=torch.complex128, device="cuda", generator=gen)
+    got = L.Dhat(op, xe, prec)
+    s = sample_sites(lat, 150, 9, parity=0)
+    z = neighbourhood(lat, s)
+    for k in (0, 5, 11):
+        full_e = np.zeros((lat.V, 4, 3), dtype=np.complex128)
+        full_e[z] = xe[k, torch.from_numpy(z // 2).cuda()].cpu().numpy()
+        want = schur_at(lat, U, w, full_e, s)
+        g = got[k, torch.from_numpy(s // 2).cuda()].cpu().numpy()
+        assert rel(g, want) < TOL[prec], (k, rel(g, want))
+        assert site_max(g, want) < 10 * TOL[prec], (k, site_max(g, want))
+    del xe, got
+
+
+def test_twelve_rhs_f16_48x48x48x96(api, c3):
+    """48^3 x 96, 12 point sources, FP16 storage inner solver, FP64 outer to 1e-10."""
+    import torch
+
+    w, lat, U, L, op = c3["w"], c3["lat"], c3["U"], c3["L"], c3["op"]
     B = torch.zeros((12, w.volume, 4, 3), dtype=torch.complex128, device="cuda")
     for k in range(12):
         B[k, 0, k // 3, k % 3] = 1.0
@@ -138,4 +192,3 @@ def test_twelve_rhs_f16_48x48x48x96(api):
         r = bk - dirac.dirac(U, x, lat, w.kappa, w.csw, w.bc, sites=s)
         # |b| = 1 (one unit entry); the sampled residual is bounded by the global one
         assert np.linalg.norm(r) <= 2 * w.tol, (k, np.linalg.norm(r))
-    L.close()
