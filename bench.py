@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--rate-factors", type=float, nargs="+", default=[0.5, 0.9],
                     help="serving workload: arrival rates as fractions of the saturated rate")
     ap.add_argument("--oracle-sites", type=int, default=16384, help="sites per oracle sample")
+    ap.add_argument("--multi-rhs", default="clover_48x48x48x96_12rhs",
+                    help="clover workload: the multi-RHS workload measured beside it ('' to skip)")
+    ap.add_argument("--multi-rhs-steps", type=int, default=2, help="timed solves of the multi-RHS workload")
     ap.add_argument("--deo-only", action="store_true",
                     help="Moebius workload: only the operator legs (one Schur operator, then D_eo), for profiler captures")
     return ap.parse_args()
@@ -428,6 +431,114 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def alu_peaks(api):
+    """Measured scalar FMA throughput (TFLOP/s) of the FP32 and FP64 pipes."""
+    return {"f32_tflops": api.bridge_alu_peak("f32") / 1e12, "f64_tflops": api.bridge_alu_peak("f64") / 1e12,
+            "how": "bridge_alu_peak: every SM filled with independent scalar FMA chains, 2 flops per FMA, best of 5"}
+
+
+def multi_rhs_leg(args, api, local, peak, alu):
+    """The multi-RHS workload beside the plain FP64 solve.
+
+    48^3 x 96 clover (c_sw = 1, kappa = 0.125, links exp(0.2 i A), seed 3),
+    the 12 spin-colour point sources at the origin, FP16 storage with
+    per-site scales, FP32 inner BiCGStab, FP64 defect correction to a true
+    relative residual of 1e-10 for every right-hand side.  Timed: K solves of
+    all 12 right-hand sides with resident inputs (CUDA events on the library
+    stream), then one event-profiled solve for the per-kernel rooflines, then
+    one plain FP64 BiCGStab solve of the first right-hand side (the
+    comparison is 12 x that time).
+    """
+    import ctypes
+
+    import torch
+
+    import synth
+    from paper_2303_05883_gb300 import _abi
+
+    w = synth.WORKLOADS[args.multi_rhs]
+    nrhs = w.nrhs
+    t_setup = time.perf_counter()
+    U = w.gauge()
+    op = api.make_op(w.kind, w.kappa, w.csw, w.bc)
+    L = api.Lattice(w.dims)
+    L.upload(U, op)
+    del U
+    h = L.handle
+    b = torch.zeros((nrhs, w.volume, 4, 3), dtype=torch.complex128, device=f"cuda:{local}")
+    for k in range(nrhs):
+        b[k, 0, k // 3, k % 3] = 1.0
+    x = torch.zeros_like(b)
+    lib = _abi.load()
+
+    def solve(prm, n):
+        x.zero_()
+        torch.cuda.current_stream().synchronize()
+        info = (_abi.bridge_info * n)()
+        _abi.check(lib.bridge_solve_dev(h, ctypes.byref(op), ctypes.byref(prm), ctypes.c_void_p(b.data_ptr()),
+                                        ctypes.c_void_p(x.data_ptr()), n, info), "bridge_solve_dev")
+        return [info[k] for k in range(n)]
+
+    api.bridge_tune(h, op, w.inner, nrhs)
+    mixed = api.make_solver(tol=w.tol, inner_prec=w.inner, mixed=1)
+    solve(mixed, nrhs)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    api.bridge_stats_reset(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K = max(1, args.multi_rhs_steps)
+    with Clocks(local) as clk:
+        e0.record(L.stream)
+        for _ in range(K):
+            infos = solve(mixed, nrhs)
+        e1.record(L.stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    st = api.bridge_stats(h)
+    gbs = sum(v["bytes"] for v in st.values()) / K / (ms * 1e-3) / 1e9
+    # one event-profiled solve: per-kernel times of exactly the iterations run
+    api.bridge_stats_reset(h)
+    api.bridge_profile(h, True)
+    solve(mixed, nrhs)
+    torch.cuda.synchronize()
+    api.bridge_profile(h, False)
+    pst = api.bridge_stats(h)
+    step_ms = sum(v["ms"] for v in pst.values())
+    site_rhs = nrhs * w.volume // 2
+    flops_site = {"schur_pass1": 1848, "schur_pass2_alpha": 1944, "schur_pass2_omega": 1944}
+    kernels = {}
+    for k, fl in flops_site.items():
+        d = pst.get(k)
+        if not d or d["launches"] == 0:
+            continue
+        us = 1e3 * d["ms"] / d["launches"]
+        ach = d["bytes"] / d["launches"] / (us * 1e-6) / 1e9
+        tf = site_rhs * fl / (us * 1e-6) / 1e12
+        kernels[k] = {"avg_launch_us": us, "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                      "gbs": ach, "hbm_frac": ach / peak, "tflops": tf,
+                      "fp32_frac": tf / alu["f32_tflops"] if alu else None,
+                      "share_of_step": d["ms"] / step_ms if step_ms else None}
+    shares = {k: round(v["ms"] / step_ms, 4) for k, v in pst.items() if v["ms"] > 0}
+    res = max(i.true_rel_residual for i in infos)
+    out = {"workload": w.name, "lattice": "x".join(map(str, w.dims)), "nrhs": nrhs, "inner_prec": w.inner,
+           "mixed_ms": ms, "mixed_steps": K, "gbs": gbs, "inner_iters": max(i.inner_iters for i in infos),
+           "outer_iters": max(i.outer_iters for i in infos), "true_rel_residual": res,
+           "status": sorted({i.status for i in infos}), "kernels": kernels, "kernel_shares": shares,
+           "clocks": clk.summary(), "setup_s": setup_s}
+    if not args.no_fp64:
+        api.bridge_tune(h, op, "f64", 1)
+        s64 = api.make_solver(tol=w.tol, mixed=0)
+        t0 = time.perf_counter()
+        i64 = solve(s64, 1)[0]
+        t64 = time.perf_counter() - t0
+        out.update({"fp64_ms_one_rhs": 1e3 * t64, "fp64_ms": nrhs * 1e3 * t64, "fp64_inner_iters": i64.inner_iters,
+                    "fp64_true_rel_residual": i64.true_rel_residual, "speedup": nrhs * 1e3 * t64 / ms})
+    L.close()
+    del b, x
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -604,6 +715,12 @@ def run_ours(args):
                "sample": f"FP64 numpy oracle: clover D at {4 * args.oracle_sites} random sites of the "
                          f"{args.workload} lattice ({secs:.1f} s)"}
 
+    # ---- measured FMA peaks and the multi-RHS workload (default workload only)
+    alu = alu_peaks(api) if rank == 0 else None
+    multi = None
+    if args.multi_rhs and args.workload == "clover_32x32x32x64" and args.multi_rhs != args.workload:
+        multi = multi_rhs_leg(args, api, local, peaks()[0], alu)
+
     if rank == 0:
         sb = {"f32": 96, "f16": 52, "bf16": 52, "f64": 192}[inner]
         working_set = (4 * w.volume * sb / 2 + w.volume * sb * 1.5 + nrhs * (12 * w.volume / 2 * sb + 3 * w.volume * 192)) / 1e9
@@ -611,6 +728,9 @@ def run_ours(args):
             "metric": METRIC,
             "value": value,
             "unit": UNIT,
+            "value_is": ("algorithmic HBM GB/s of one whole mixed-precision solve (every kernel of the step: "
+                         "Schur hops, BiCGStab vectors, FP64 residual), inputs resident; the D_eo kernel alone is "
+                         "deo.gbs, the dominant kernel's is roofline.achieved"),
             "n_gpus": world,
             "steps": args.steps,
             "warmup": args.warmup,
@@ -638,6 +758,8 @@ def run_ours(args):
                               for k, v in api.bridge_tune_table(h).items() if k.startswith("hop/")},
             "deo": deo,
             "solve": solve,
+            "multi_rhs": multi,
+            "alu_peaks": alu,
             "serving": serving,
             "e2e": e2e,
             "gpu_launches": launches,

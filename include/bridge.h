@@ -216,8 +216,7 @@ int bridge_mult_Dhat_dag_dev(bridge_lattice lat, const bridge_op* op, int prec, 
  * cudaMalloc while they apply the operator (for example an application that
  * reserves all device memory for its own pool at start-up, or a
  * latency-critical loop where an allocation, which may synchronize the
- * device, is not allowed).  The paper has no counterpart: this is a
- * deployment variant of the Eq. 1 operator.
+ * device, is not allowed).  The paper has no counterpart.
  *
  * in_dev / out_dev: nrhs canonical FP64 even half-lattice vectors on the
  * device (nrhs*V/2*24 doubles each), owned by the caller.  Its scratch (the
@@ -405,6 +404,20 @@ int bridge_profile(bridge_lattice lat, int enable);
 /* Number of kernels this library launched in this process (graph nodes
  * count once per replay). */
 long bridge_launch_count(void);
+/* Number of device allocations (cudaMalloc and stream-ordered cudaMallocAsync)
+ * this library made in this process; a diagnostic for tests of the
+ * no-allocation entry point. */
+long bridge_device_alloc_count(void);
+/* Measured arithmetic throughput of the current device's scalar fused
+ * multiply-add pipe (the instruction the stencils use), for the rooflines
+ * of kernels bound by arithmetic rather than memory; the paper has no
+ * counterpart (it quotes A64FX's nominal peak).  prec: BRIDGE_F32 or
+ * BRIDGE_F64.  *flops_per_s = 2 x FMAs per second of a grid that fills every
+ * SM with independent FMA chains, best of five timed launches.  Runs a few
+ * milliseconds of GPU work on a private stream and synchronizes it.
+ * Returns BRIDGE_EINVAL for another precision or a NULL pointer,
+ * BRIDGE_ECUDA without a device. */
+int bridge_alu_peak(int prec, double* flops_per_s);
 /* Neighbour map of the GPU layout, computed on the host with the same code
  * the kernels use: out[2*mu + 0/1] = half-lattice index of x + mu / x - mu
  * for half-lattice site ih of the given parity; wraps[mu*2 + 0/1] = 1 when

@@ -143,6 +143,8 @@ SIGNATURES = {
     "bridge_stats_reset": (c_int, [_h]),
     "bridge_profile": (c_int, [_h, c_int]),
     "bridge_launch_count": (c_long, []),
+    "bridge_device_alloc_count": (c_long, []),
+    "bridge_alu_peak": (c_int, [c_int, _dp]),
     "bridge_tune": (c_int, [_h, POINTER(bridge_op), c_int, c_int]),
     "bridge_tune_table": (c_int, [_h, c_char_p, c_int]),
     "bridge_tune_set": (c_int, [_h, c_char_p, c_int, c_int, c_int]),

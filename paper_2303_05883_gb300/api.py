@@ -317,6 +317,13 @@ def bridge_launch_count() -> int:
     return int(_abi.load().bridge_launch_count())
 
 
+def bridge_alu_peak(prec="f32") -> float:
+    """Measured FMA throughput of the device in flop/s (2 per FMA)."""
+    v = ctypes.c_double(0.0)
+    check(_abi.load().bridge_alu_peak(_prec(prec), ctypes.byref(v)), "bridge_alu_peak")
+    return v.value
+
+
 def bridge_debug_neighbours(dims, parity, ih):
     out = (c_long * 8)()
     wr = (c_int * 8)()

@@ -16,6 +16,7 @@ static constexpr int APPLY_DHAT_DAG = 100;
 namespace bridge {
 const char* last_error_text();
 extern std::atomic<long> g_launches;
+extern std::atomic<long> g_dev_allocs;
 void tune_cache_load(bridge_lattice_s* L);
 int engine_submit(bridge_lattice_s* L, const bridge_op& op, const bridge_solver& s, const double* b, int nrhs,
                   bridge_request_h* out);
@@ -578,6 +579,7 @@ int bridge_profile(bridge_lattice L, int enable) {
 }
 
 long bridge_launch_count(void) { return g_launches.load(); }
+long bridge_device_alloc_count(void) { return g_dev_allocs.load(); }
 
 int bridge_debug_neighbours(const int dims[4], int parity, long ih, long out[8], int wraps[8]) {
   BR_API_BEGIN

@@ -251,6 +251,21 @@ void launch_coarse(int red, int n2, const MgCoarseArgs& a, unsigned grid, cudaSt
   else launch_coarse_red<MG_CR_NONE>(n2, a, grid, st);
 }
 
+// Polls of each site-loop wait of the streamed kernel: the full bound, or
+// BRIDGE_MG_WAIT_POLLS from the environment (read at every launch), which
+// lets a test make those waits give up and exercise the error path.
+static int coarse_wait_polls() {
+  const char* e = std::getenv("BRIDGE_MG_WAIT_POLLS");
+  if (!e || !*e) return MG_WAIT_POLLS;
+  const long v = std::strtol(e, nullptr, 10);
+  return (int)std::max(0L, std::min<long>(v, MG_WAIT_POLLS));
+}
+
+// Clear the streamed kernel's error word before a coarse solve or apply.
+static void clear_coarse_err(bridge_mg_s* g) {
+  BR_CUDA(cudaMemsetAsync(g->cerr(), 0, sizeof(int), stream_of(g)));
+}
+
 // One streamed application of the FP16 tiles T (Dch: D_c; Deo: the even-odd
 // pieces): y = sum_{d0 <= d < d1} T[X][d] x_Y (or b - sum) at the coarse
 // sites of one colour (parity -1: every site), with an optional fused
@@ -264,6 +279,7 @@ void coarse_stream(bridge_mg_s* g, const DevBuf& tiles, int parity, int d0, int 
   a.Dch = reinterpret_cast<const __half2*>(tiles.ptr);
   a.nbr = reinterpret_cast<const int*>(g->cnbr->ptr);
   a.err = g->cerr();
+  a.wait_polls = coarse_wait_polls();
   a.x = x;
   a.b = b;
   a.y = y;
@@ -332,7 +348,11 @@ static_assert(sizeof(BiCGScalars) <= 192, "the coarse error word follows the sca
 // kernel's error word at byte 192.
 void check_coarse_err(bridge_mg_s* g) {
   const int e = *reinterpret_cast<const int*>(static_cast<const char*>(g->hcsc->ptr) + 192);
-  if (e != 0) throw Error{BRIDGE_ECUDA, "coarse operator: a tile copy did not complete within 1 s"};
+  if (e == 1) throw Error{BRIDGE_ECUDA, "coarse operator: a tile copy did not complete within its wait bound"};
+  if (e != 0)
+    throw Error{BRIDGE_ECUDA,
+                "coarse operator: a tile copy did not complete within its wait bound, and copies still in flight "
+                "did not land before the kernel returned; the CUDA context is no longer reliable"};
 }
 
 void cbicg_step(bridge_mg_s* g, int op, const float2* b = nullptr) {
@@ -376,6 +396,7 @@ int coarse_solve(bridge_mg_s* g, const float2* rhs) {
   init.max_iter = std::max(1, g->prm.coarse_maxiter);
   init.rho_r = init.alpha_r = init.omega_r = 1.0;
   BR_CUDA(cudaMemcpyAsync(g->csc->ptr, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  clear_coarse_err(g);
   const bool eo = g->Deo != nullptr;
   if (eo) {
     // even-odd: cv8 = A_O^-1 r_O; cv10 = A_E^-1 r_E - (A^-1 H)_EO cv8 (zero on O),
@@ -748,9 +769,12 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
         const int n2 = g->n2;
         DevBuf ainv(sizeof(float2) * (size_t)g->m.nblocks * n2 * n2), deo(sizeof(float2) * (size_t)n);
         const size_t inv_smem = sizeof(float2) * (size_t)(2 * n2 * n2 + n2);
+        DevBuf singular(sizeof(int));
+        BR_CUDA(cudaMemsetAsync(singular.ptr, 0, sizeof(int), st));
         note_launch(L, K_MG_SETUP, 0, 0, st, true);
         mg_invert_self_kernel<<<g->m.nblocks, 256, inv_smem, st>>>(reinterpret_cast<const float2*>(g->Dc->ptr),
-                                                                   reinterpret_cast<float2*>(ainv.ptr), n2);
+                                                                   reinterpret_cast<float2*>(ainv.ptr), n2,
+                                                                   reinterpret_cast<int*>(singular.ptr));
         mg_premul_kernel<<<g->m.nblocks, 256, sizeof(float2) * (size_t)n2 * n2, st>>>(
             reinterpret_cast<const float2*>(g->Dc->ptr), reinterpret_cast<const float2*>(ainv.ptr),
             reinterpret_cast<float2*>(deo.ptr), n2);
@@ -760,7 +784,10 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
                                                      n2, 1);
         note_launch(L, K_MG_SETUP, 0, 0, st, false);
         BR_CUDA(cudaGetLastError());
+        int sing = 0;
+        BR_CUDA(cudaMemcpyAsync(&sing, singular.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
         BR_CUDA(cudaStreamSynchronize(st));  // the temporaries are freed on return
+        if (sing) g->Deo.reset();  // a numerically singular self coupling: solve the full coarse system
       }
     }
     BR_CUDA(cudaStreamSynchronize(st));
@@ -954,6 +981,7 @@ void mg_apply(bridge_mg_s* g, int which, const double* in, double* out) {
       break;
     case BRIDGE_MG_COARSE_HALF:
       if (!g->Dch) throw Error{BRIDGE_EINVAL, "no FP16 coarse operator (coarse_half = 0)"};
+      clear_coarse_err(g);
       c64_to_32(in, reinterpret_cast<float2*>(cin.ptr));
       coarse_apply(g, reinterpret_cast<float2*>(cin.ptr), reinterpret_cast<float2*>(cout.ptr), nullptr, MG_CR_NONE,
                    nullptr, true);

@@ -306,7 +306,10 @@ struct MgCoarseArgs {
   float2* y;
   const float2* rhat;  // MG_CR_ALPHA: <rhat, y> -> FIN_ALPHA
   RedArgs red;
-  int* err;     // mg_coarse_tma_kernel: set to 1 if a tile copy did not arrive in time
+  int* err;     // mg_coarse_tma_kernel: 1 if a tile copy did not arrive in time, 2 if the copies
+                // still in flight then did not land within the drain's bound either
+  int wait_polls;  // mg_coarse_tma_kernel: polls of each site-loop wait before it gives up
+                   // (MG_WAIT_POLLS normally; 0 gives up at once, for tests of the error path)
   int stages;   // mg_coarse_tma_kernel: tile buffers in shared memory (2 .. 4)
   // mg_coarse_tma_kernel only: the coarse sites of one colour (parity 0 / 1,
   // -1 all sites), the couplings d0 .. d1 - 1 summed, and the vector of the
@@ -339,11 +342,13 @@ BR_D void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
                : "memory");
 }
 // Wait for the phase of the given parity to complete, giving up after about
-// a second (returns false then).
-BR_D bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// a second or max_polls polls (returns false then; max_polls = 0 gives up
+// without polling).
+constexpr int MG_WAIT_POLLS = 1 << 22;
+BR_D bool mbar_wait(uint64_t* bar, uint32_t parity, int max_polls = MG_WAIT_POLLS) {
   uint64_t t0;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-  for (int it = 0; it < (1 << 22); ++it) {
+  for (int it = 0; it < max_polls; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -511,7 +516,7 @@ __global__ void __launch_bounds__(256) mg_coarse_tma_kernel(const MgCoarseArgs a
       if (RED == MG_CR_ALPHA) ev = a.rhat[t];
       if (RED == MG_CR_OMEGA) ev = a.xin ? a.xin[t] : a.x[t];
     }
-    const bool ok = mbar_wait(&bar[buf], (uint32_t)((it / stages) & 1));
+    const bool ok = mbar_wait(&bar[buf], (uint32_t)((it / stages) & 1), a.wait_polls);
     if (!__syncthreads_and(ok)) {
       failed = true;
       break;
@@ -561,9 +566,15 @@ __global__ void __launch_bounds__(256) mg_coarse_tma_kernel(const MgCoarseArgs a
     }
   }
   if (failed) {
-    // let the copies still in flight land (bounded) before the CTA exits
-    for (int k = it; k < mine && k < it + stages; ++k) (void)mbar_wait(&bar[k % stages], (uint32_t)((k / stages) & 1));
-    if (tid == 0) atomicExch(a.err, 1);
+    // Let the copies still in flight land before the CTA exits and its
+    // shared memory is handed to another CTA: every copy this CTA issued is
+    // waited for with the full bound.  Should that run out as well (the copy
+    // engine stopped answering), the word says so and the host reports that
+    // the context is no longer reliable.
+    bool drained = true;
+    for (int k = it; k < mine && k < it + stages; ++k)
+      drained = mbar_wait(&bar[k % stages], (uint32_t)((k / stages) & 1)) && drained;
+    if (tid == 0) atomicMax(a.err, drained ? 1 : 2);
   }
   if (RED == MG_CR_ALPHA) reduce_finalize<2>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
   if (RED == MG_CR_OMEGA) reduce_finalize<3>(a.red, 0, blockIdx.x, gridDim.x, 1, rv);
@@ -581,11 +592,15 @@ __global__ void __launch_bounds__(256) mg_coarse_tma_kernel(const MgCoarseArgs a
 // A_X^-1 for every coarse site by Gauss-Jordan elimination with partial
 // pivoting on [A | 1] in shared memory (row-major, n x 2n), one CTA per site.
 // Dc and Ainv are column-major (entry (row, col) at col * n + row).
-__global__ void __launch_bounds__(256) mg_invert_self_kernel(const float2* Dc, float2* Ainv, int n) {
+// A pivot whose magnitude is below 1e-6 of the largest entry of A_X (or not
+// finite) marks A_X as numerically singular in FP32: *singular is set and
+// the host falls back to the full coarse system.
+__global__ void __launch_bounds__(256) mg_invert_self_kernel(const float2* Dc, float2* Ainv, int n, int* singular) {
   extern __shared__ __align__(16) unsigned char dsm_inv[];
   float2* M = reinterpret_cast<float2*>(dsm_inv);  // [n][2n]
   float2* f = M + 2L * n * n;                      // [n] elimination factors
   __shared__ int piv;
+  __shared__ float amax2;
   const int X = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, w = 2 * n;
   const float2* A = Dc + (long)X * 9 * n * n;  // coupling 0
   for (int i = tid; i < n * w; i += nt) {
@@ -593,6 +608,14 @@ __global__ void __launch_bounds__(256) mg_invert_self_kernel(const float2* Dc, f
     M[i] = c < n ? A[(long)c * n + r] : make_float2(c - n == r ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
+  if (tid == 0) {
+    float m = 0.f;
+    for (int i = 0; i < n * n; ++i) {
+      const float2 v = M[(i / n) * w + i % n];
+      m = fmaxf(m, v.x * v.x + v.y * v.y);
+    }
+    amax2 = m;
+  }
   for (int k = 0; k < n; ++k) {
     if (tid == 0) {
       int best = k;
@@ -606,6 +629,7 @@ __global__ void __launch_bounds__(256) mg_invert_self_kernel(const float2* Dc, f
         }
       }
       piv = best;
+      if (!(bv > 1e-12f * amax2) || !isfinite(bv)) atomicExch(singular, 1);
     }
     __syncthreads();
     const int pr = piv;

@@ -16,6 +16,7 @@ void set_error(int code, const std::string& msg) {
 const char* last_error_text() { return tl_last_error.c_str(); }
 
 std::atomic<long> g_launches{0};
+std::atomic<long> g_dev_allocs{0};
 
 const char* kclass_name(int k) {
   static const char* names[K_NCLASS] = {"hop_deo",      "dirac_full",    "schur_pass1", "schur_pass2",
@@ -64,6 +65,7 @@ DevBuf::DevBuf(size_t n, cudaStream_t stream, bool stream_ordered) : st(stream),
     throw Error{BRIDGE_ENOMEM, "device allocation of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e)};
   }
   bytes = n;
+  g_dev_allocs.fetch_add(1);
 }
 DevBuf::~DevBuf() {
   if (!ptr) return;

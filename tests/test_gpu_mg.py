@@ -140,6 +140,41 @@ def test_coarse_solve_even_odd(api, case, nv):
     assert rel(sols[1], sols[0]) < 2e-2
 
 
+@pytest.mark.parametrize("which", ["half", "solve"])
+def test_coarse_wait_gives_up_and_reports(api, case, monkeypatch, which):
+    """The bounded waits of the streamed coarse kernel.  With
+    BRIDGE_MG_WAIT_POLLS=0 every site-loop wait gives up at once; nothing is
+    faulted and no copy is lost (each CTA then waits, with the full bound, for
+    the copies it still has in flight before it exits).  The kernel raises its
+    error word and the call returns BRIDGE_ECUDA naming the wait; the next
+    call on the same multigrid object, with the normal bound, succeeds (the
+    word is cleared at the start of every coarse apply and solve) and agrees
+    with the oracle."""
+    from paper_2303_05883_gb300 import _abi
+
+    lat, U, op, L = case["lat"], case["U"], case["op"], case["L"]
+    nv = 4
+    gen = np.random.default_rng(300)
+    vs = gen.standard_normal((nv, lat.V, 4, 3)) + 1j * gen.standard_normal((nv, lat.V, 4, 3))
+    orc = multigrid.Multigrid(U, lat, 0.12, 1.0, (2, 2, 2, 2), vs)
+    mg = api.Multigrid(L, op, api.make_mg_params(block=(2, 2, 2, 2), nvec=nv, coarse_half=1, coarse_eo=1,
+                                                 coarse_tol=1e-5, coarse_maxiter=4000), null_vectors=vs)
+    x = gen.standard_normal((mg.nblocks, 2, nv)) + 1j * gen.standard_normal((mg.nblocks, 2, nv))
+    op_id = _abi.BRIDGE_MG_COARSE_HALF if which == "half" else _abi.BRIDGE_MG_COARSE_SOLVE
+    monkeypatch.setenv("BRIDGE_MG_WAIT_POLLS", "0")
+    with pytest.raises(_abi.BridgeError) as e:
+        mg.apply(op_id, x)
+    assert e.value.status == _abi.BRIDGE_ECUDA
+    assert "wait bound" in str(e.value) and "no longer reliable" not in str(e.value)
+    monkeypatch.delenv("BRIDGE_MG_WAIT_POLLS")
+    y = mg.apply(op_id, x)
+    if which == "half":
+        assert rel(y, orc.restrict(orc.D(orc.prolong(x)))) < 2e-3
+    else:
+        assert rel(orc.restrict(orc.D(orc.prolong(y))), x) < 2e-2
+    mg.close()
+
+
 def test_sap_smoother(api, case):
     from paper_2303_05883_gb300 import _abi
 

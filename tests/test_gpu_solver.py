@@ -276,3 +276,12 @@ def test_null_pointers_are_einval(clover_odd, api):
     assert lib.bridge_solve(h, ctypes.byref(op), ctypes.byref(s), None, None, 1, None) == _abi.BRIDGE_EINVAL
     assert lib.bridge_gauge_upload(h, None, None) == _abi.BRIDGE_EINVAL
     assert lib.bridge_apply(h, ctypes.byref(op), 9, None, None) == _abi.BRIDGE_EINVAL
+
+
+def test_alu_peak_is_measured(api):
+    """The FMA microbenchmark behind the arithmetic rooflines: FP32 well above
+    FP64 (the FP64 pipe runs at a small fraction of the FP32 rate) and both
+    within physical bounds (152 SMs x 128 FP32 lanes x 2 flops x 2.1 GHz)."""
+    f32, f64 = api.bridge_alu_peak("f32"), api.bridge_alu_peak("f64")
+    assert 1e12 < f32 < 1.2e14
+    assert 1e10 < f64 < f32 / 4

@@ -52,22 +52,46 @@ def _noalloc(api, L, op, prec, x_dev, out_dev, nrhs):
 
 @pytest.mark.parametrize("kind,prec", [("clover", "f32"), ("clover", "f64"), ("wilson", "f16")])
 def test_noalloc_matches_mult_dhat_twice(api, kind, prec):
+    """Two calls in a row on different inputs: the same kernels and launch
+    shapes as bridge_mult_Dhat, so the results agree to rounding-free
+    precision, and both agree with the FP64 oracle within the precision's
+    tolerance.  Across the calls the library makes no device allocation and
+    the device's free memory does not change."""
     import torch
+
+    from oracle import evenodd
+    from paper_2303_05883_gb300 import _abi
 
     dims = (8, 8, 8, 16)
     lat = Lattice(dims)
     L = api.Lattice(dims)
-    op = api.make_op(kind, 0.12, 1.0 if kind == "clover" else 0.0)
-    L.upload(synth.gauge_field(dims, 0.3, 21), op)
+    csw = 1.0 if kind == "clover" else 0.0
+    op = api.make_op(kind, 0.12, csw)
+    U = synth.gauge_field(dims, 0.3, 21)
+    L.upload(U, op)
+    eo = evenodd.EvenOdd(U, lat, 0.12, csw)
     nrhs = 2
+    xs = [synth.gaussian_spinor(dims, 300 + call, nrhs=nrhs)[:, lat.even] for call in range(2)]
+    wants = [L.Dhat(op, x, prec) for x in xs]  # the existing entry point (also builds the operator data)
+    x_devs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in xs]
+    out_devs = [torch.full_like(x_dev, float("nan")) for x_dev in x_devs]
+    lib = _abi.load()
+    # the first call on a device does its one-time set-up (the scratch
+    # array's address; lazy loading of the library's device code): make it
+    # before the measured calls, as a caller would during set-up
+    assert _noalloc(api, L, op, prec, x_devs[0], out_devs[0], nrhs) == 0
+    torch.cuda.synchronize()
+    allocs0, free0 = lib.bridge_device_alloc_count(), torch.cuda.mem_get_info()[0]
     for call in range(2):  # two calls in a row, different inputs
-        x = synth.gaussian_spinor(dims, 300 + call, nrhs=nrhs)[:, lat.even]
-        want = L.Dhat(op, x, prec)  # the existing entry point (also builds the operator data)
-        x_dev = torch.from_numpy(np.ascontiguousarray(x)).cuda()
-        out_dev = torch.full_like(x_dev, float("nan"))
-        assert _noalloc(api, L, op, prec, x_dev, out_dev, nrhs) == 0
-        got = out_dev.cpu().numpy()
-        assert rel(got, want) < TOL[prec], (call, rel(got, want))
+        assert _noalloc(api, L, op, prec, x_devs[call], out_devs[call], nrhs) == 0
+    torch.cuda.synchronize()
+    assert lib.bridge_device_alloc_count() == allocs0
+    assert torch.cuda.mem_get_info()[0] == free0
+    for call in range(2):
+        got = out_devs[call].cpu().numpy()
+        assert rel(got, wants[call]) < 1e-14, (call, rel(got, wants[call]))
+        oracle = np.stack([eo.schur(v) for v in xs[call]])
+        assert rel(got, oracle) < TOL[prec], (call, rel(got, oracle))
     L.close()
 
 
