@@ -136,7 +136,12 @@ typedef struct {
   int check_every;   /* iterations between host convergence polls (<= 0: 16) */
   int use_graph;     /* 1: replay iteration batches as CUDA graphs */
   int max_outer;     /* limit on defect-correction passes (<= 0: 50) */
+  int method;        /* WILSON/CLOVER inner solver: BRIDGE_METHOD_AUTO (0) BiCGStab, switching to CG on the
+                        normal equations of the Schur system for the remaining passes once a BiCGStab pass
+                        stagnates (1000 iterations with |r^| > 1e-2 |b^| at its end); BRIDGE_METHOD_BICGSTAB (1)
+                        BiCGStab only; BRIDGE_METHOD_CGNR (2) CG on D^dag D^ only.  Other kinds ignore it. */
 } bridge_solver;
+enum bridge_method { BRIDGE_METHOD_AUTO = 0, BRIDGE_METHOD_BICGSTAB = 1, BRIDGE_METHOD_CGNR = 2 };
 
 typedef struct {
   int status;               /* BRIDGE_OK, BRIDGE_ENOCONV or BRIDGE_EBREAKDOWN */
@@ -145,6 +150,8 @@ typedef struct {
   int restarts;             /* inner solves that ended in breakdown */
   double true_rel_residual; /* ||b - D x|| / ||b|| in FP64 on the GPU */
   double seconds;           /* wall time of the solve */
+  int cgnr_passes;          /* WILSON/CLOVER: defect-correction passes whose inner solve was CG on the
+                               normal equations (inner_iters then counts CG iterations for them) */
 } bridge_info;
 
 typedef struct {

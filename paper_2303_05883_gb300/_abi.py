@@ -24,6 +24,7 @@ BRIDGE_ECUDA = -6
 BRIDGE_ESTATE = -7
 
 BRIDGE_F64, BRIDGE_F32, BRIDGE_F16, BRIDGE_BF16 = 0, 1, 2, 3
+BRIDGE_METHOD_AUTO, BRIDGE_METHOD_BICGSTAB, BRIDGE_METHOD_CGNR = 0, 1, 2
 BRIDGE_WILSON, BRIDGE_CLOVER, BRIDGE_MOBIUS, BRIDGE_STAGGERED = 0, 1, 2, 3
 BRIDGE_EVEN, BRIDGE_ODD, BRIDGE_FULL = 0, 1, 2
 BRIDGE_APPLY_D, BRIDGE_APPLY_DEO, BRIDGE_APPLY_DOE, BRIDGE_APPLY_DHAT = 0, 1, 2, 3
@@ -55,6 +56,7 @@ class bridge_solver(ctypes.Structure):
         ("check_every", c_int),
         ("use_graph", c_int),
         ("max_outer", c_int),
+        ("method", c_int),
     ]
 
 
@@ -66,6 +68,7 @@ class bridge_info(ctypes.Structure):
         ("restarts", c_int),
         ("true_rel_residual", c_double),
         ("seconds", c_double),
+        ("cgnr_passes", c_int),
     ]
 
 

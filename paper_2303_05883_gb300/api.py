@@ -179,6 +179,7 @@ def _infos(arr, n):
             restarts=arr[k].restarts,
             true_rel_residual=arr[k].true_rel_residual,
             seconds=arr[k].seconds,
+            cgnr_passes=arr[k].cgnr_passes,
         )
         for k in range(n)
     ]

@@ -381,6 +381,7 @@ void bridge_solver_defaults(bridge_solver* s) {
   s->check_every = 16;
   s->use_graph = 1;
   s->max_outer = 50;
+  s->method = BRIDGE_METHOD_AUTO;
 }
 
 int bridge_solve(bridge_lattice L, const bridge_op* op, const bridge_solver* s, const double* b, double* x, int nrhs,

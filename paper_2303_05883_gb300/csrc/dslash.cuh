@@ -15,7 +15,8 @@
 //
 //   out = s1 * M(self) + E( beta * H(in) + caux * aux )
 //
-// with M in {1, T} (F_SELF, F_SELF_CLOV) and E in {1, T^-1} (F_E_CLOV); this
+// with M in {1, T} (F_SELF, F_SELF_CLOV) and E in {1, T^-1, gamma5}
+// (F_E_CLOV, F_G5: the second pass of the adjoint Schur operator); this
 // single kernel covers D_eo / D_oe, the full operator T - kappa H, both
 // passes of the Schur operator of Eq. 1, the even-odd source preparation and
 // solution reconstruction, and the FP64 residual b - D x.  Optional fused
@@ -27,7 +28,12 @@
 
 namespace bridge {
 
-enum HopFlags { F_SELF = 1, F_SELF_CLOV = 2, F_E_CLOV = 4, F_AUX = 8 };
+enum HopFlags { F_SELF = 1, F_SELF_CLOV = 2, F_E_CLOV = 4, F_AUX = 8, F_G5 = 16 };
+
+// A right-hand side whose solve has ended (BiCGStab or CG scalars) is skipped.
+BR_D bool rhs_finished(const RedArgs& r, int rhs) {
+  return r.check_done && ((r.sc != nullptr && r.sc[rhs].done != RUNNING) || (r.cg != nullptr && r.cg[rhs].done != RUNNING));
+}
 enum RedMode { R_NONE = 0, R_NORM = 1, R_DOT_A = 2, R_TS = 3 };
 
 struct HopArgs {
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
   constexpr int NV = RED == R_NORM ? 1 : RED == R_DOT_A ? 2 : 3;
   PartialSum<R> ps[NV];
   const R beta = pick<R>(a.beta, a.betaf), s1 = pick<R>(a.s1, a.s1f), ca = pick<R>(a.caux, a.cauxf);
-  const bool skip = a.red.check_done && a.red.sc != nullptr && a.red.sc[rhs].done != RUNNING;
+  const bool skip = rhs_finished(a.red, rhs);
   if (!skip) {
     const int p = a.out_parity;
     const long lbb = link_block_bytes(P, vh), cbb = clover_block_bytes(P, vh);
@@ -213,6 +219,10 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopArgs a) {
         load_spinor<P, true, ST>(a.aux + rhs * a.aux_rs, vh, ih, x);
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = acc[k] + ca * x[k];
+      }
+      if (FL & F_G5) {
+#pragma unroll
+        for (int k = 6; k < 12; ++k) acc[k] = cx<R>{-acc[k].r, -acc[k].i};
       }
       cx<R> v[12];
       if (FL & F_E_CLOV) {
@@ -348,8 +358,7 @@ __global__ void __launch_bounds__(256) hop_kernel_mr(const HopArgs a) {
   bool any = false;
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
-    live[r] = (r0 + r < a.nrhs) &&
-              !(a.red.check_done && a.red.sc != nullptr && a.red.sc[r0 + r].done != RUNNING);
+    live[r] = (r0 + r < a.nrhs) && !rhs_finished(a.red, r0 + r);
     any = any || live[r];
   }
   PartialSum<T> ps[NR][NV];

@@ -184,8 +184,7 @@ __global__ void __launch_bounds__(32 * TILE_MAX_RHS, 2) hop_kernel_tile(const Ho
   const int rhs = grp * G + w;  // warp-uniform
   const long vh = a.g.vh;
   constexpr int NV = RED == R_NORM ? 1 : RED == R_DOT_A ? 2 : 3;
-  const bool live = rhs < a.nrhs && w < G &&
-                    !(a.red.check_done && a.red.sc != nullptr && a.red.sc[rhs].done != RUNNING);
+  const bool live = rhs < a.nrhs && w < G && !rhs_finished(a.red, rhs);
   PartialSum<float> ps[NV];
   const int p = a.out_parity;
   const long lbb = link_block_bytes(P, vh), cbb = clover_block_bytes(P, vh);

@@ -22,7 +22,7 @@ bool launch_dwf_hop(int prec, bool m1, int m2, int epi, const DwfArgs& a, cudaSt
 bool launch_dwf_mix(int prec, int mode, const DwfMixArgs& a, cudaStream_t st, int variant = 0);
 
 // ----------------------------------------------------- BiCGStab vectors
-enum BlasOp { B_INIT = 0, B_S = 1, B_XR = 2, B_P = 3 };
+enum BlasOp { B_INIT = 0, B_S = 1, B_XR = 2, B_P = 3, B_CG_INIT = 4, B_CG_XR = 5, B_CG_P = 6 };
 struct BlasArgs {
   uint32_t vh;
   int nrhs, nblk;
@@ -38,6 +38,9 @@ struct BlasArgs {
 // B_S:    s = r - alpha v
 // B_XR:   x += alpha p + omega s, r = s - omega t, (<rhat, r>, |r|^2) -> FIN_RHO
 // B_P:    p = r + beta (p - omega v)
+// B_CG_INIT, B_CG_XR, B_CG_P: CG on the normal equations of the Schur system
+// (x = 0, p = r, |r|^2; x += alpha p, r -= alpha t, |r|^2; p = r + beta p),
+// scalars in red.cg
 bool launch_blas(int op, int prec, int px, const BlasArgs& a, int block, cudaStream_t st, int* occ = nullptr);
 
 // ------------------------------------------------------------ layout
@@ -63,6 +66,9 @@ bool launch_convert(int ps, int pd, const CopyArgs& a, int block, cudaStream_t s
 bool launch_accumulate64(int ps, const CopyArgs& a, int block, cudaStream_t st);      // dst(F64) += src
 bool launch_norm2(int prec, const CopyArgs& a, int block, cudaStream_t st);           // |src|^2 -> FIN_STORE
 bool launch_clover_site(int prec, const CopyArgs& a, const char* clov, int block, cudaStream_t st);  // dst = A src
+// dst = gamma5 A src (clov = null: gamma5 src); skips right-hand sides whose
+// CG solve ended (red.cg with check_done)
+bool launch_g5_site(int prec, const CopyArgs& a, const char* clov, int block, cudaStream_t st);
 
 // ------------------------------------------------------- gauge, clover
 // Canonical FP64 links (4, V, 3, 3) -> internal F64 blocks [parity][mu].

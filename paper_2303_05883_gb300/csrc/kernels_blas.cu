@@ -111,6 +111,83 @@ __global__ void __launch_bounds__(256) k_blas_p(const BlasArgs a) {
   }
 }
 
+// ----------------------------------------------------------- CG on D^dag D^
+// CG (Hestenes-Stiefel) on the normal equations of the Schur system, the
+// inner method where BiCGStab stagnates (a spectrum around the origin past
+// the critical kappa); real scalars from CGScalars (FIN_CG_* finalizers):
+// B_CG_INIT x = 0, p = r, |r|^2 -> FIN_CG_INIT
+// B_CG_XR   x += alpha p, r -= alpha t, |r|^2 -> FIN_CG_BETA
+// B_CG_P    p = r + beta p
+template <int P, int PX>
+__global__ void __launch_bounds__(256) k_cg_init(const BlasArgs a) {
+  using R = typename Tr<P>::R;
+  const int rhs = blockIdx.x % a.nrhs, sb = blockIdx.x / a.nrhs;
+  PartialSum<R> ps;
+  BR_SITE_LOOP(a.vh, a.nblk) {
+    cx<R> r[12], z[12];
+    load_spinor<P>(a.r + rhs * a.r_rs, a.vh, ih, r);
+    R n = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      n += r[k].r * r[k].r + r[k].i * r[k].i;
+      z[k] = czero<R>();
+    }
+    store_spinor<P>(a.p + rhs * a.p_rs, a.vh, ih, r);
+    store_spinor<PX>(a.x + rhs * a.x_rs, a.vh, ih, z);
+    ps.add(n);
+  }
+  double rv[1] = {ps.value()};
+  reduce_finalize<1>(a.red, rhs, sb, a.nblk, a.nrhs, rv);
+}
+
+template <int P, int PX>
+__global__ void __launch_bounds__(256) k_cg_xr(const BlasArgs a) {
+  using R = typename Tr<P>::R;
+  const int rhs = blockIdx.x % a.nrhs, sb = blockIdx.x / a.nrhs;
+  const CGScalars* q = a.red.cg + rhs;
+  PartialSum<R> ps;
+  if (q->done == RUNNING) {
+    const R al = (R)q->alpha;
+    BR_SITE_LOOP(a.vh, a.nblk) {
+      cx<R> x[12], p[12], r[12], t[12];
+      load_spinor<PX, false>(a.x + rhs * a.x_rs, a.vh, ih, x);
+      load_spinor<P, false>(a.p + rhs * a.p_rs, a.vh, ih, p);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) x[k] = caxpy(al, p[k], x[k]);
+      store_spinor<PX>(a.x + rhs * a.x_rs, a.vh, ih, x);
+      load_spinor<P, false>(a.r + rhs * a.r_rs, a.vh, ih, r);
+      load_spinor<P, false>(a.t + rhs * a.t_rs, a.vh, ih, t);
+      R n = 0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        r[k] = caxpy(-al, t[k], r[k]);
+        n += r[k].r * r[k].r + r[k].i * r[k].i;
+      }
+      store_spinor<P>(a.r + rhs * a.r_rs, a.vh, ih, r);
+      ps.add(n);
+    }
+  }
+  double rv[1] = {ps.value()};
+  reduce_finalize<1>(a.red, rhs, sb, a.nblk, a.nrhs, rv);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_cg_p(const BlasArgs a) {
+  using R = typename Tr<P>::R;
+  const int rhs = blockIdx.x % a.nrhs;
+  const CGScalars* q = a.red.cg + rhs;
+  if (q->done != RUNNING) return;
+  const R be = (R)q->beta;
+  BR_SITE_LOOP(a.vh, a.nblk) {
+    cx<R> r[12], p[12];
+    load_spinor<P, false>(a.r + rhs * a.r_rs, a.vh, ih, r);
+    load_spinor<P, false>(a.p + rhs * a.p_rs, a.vh, ih, p);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k] = caxpy(be, p[k], r[k]);
+    store_spinor<P>(a.p + rhs * a.p_rs, a.vh, ih, p);
+  }
+}
+
 template <int P, int PX>
 static bool blas_dispatch(int op, const BlasArgs& a, int block, cudaStream_t st, int* occ) {
   const dim3 grid((unsigned)(a.nblk * a.nrhs));
@@ -121,6 +198,9 @@ static bool blas_dispatch(int op, const BlasArgs& a, int block, cudaStream_t st,
       case B_S: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_blas_s<P>, block, 0); break;
       case B_XR: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_blas_xr<P, PX>, block, 0); break;
       case B_P: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_blas_p<P>, block, 0); break;
+      case B_CG_INIT: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_cg_init<P, PX>, block, 0); break;
+      case B_CG_XR: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_cg_xr<P, PX>, block, 0); break;
+      case B_CG_P: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_cg_p<P>, block, 0); break;
     }
     return e == cudaSuccess;
   }
@@ -129,6 +209,9 @@ static bool blas_dispatch(int op, const BlasArgs& a, int block, cudaStream_t st,
     case B_S: k_blas_s<P><<<grid, block, 0, st>>>(a); return true;
     case B_XR: k_blas_xr<P, PX><<<grid, block, 0, st>>>(a); return true;
     case B_P: k_blas_p<P><<<grid, block, 0, st>>>(a); return true;
+    case B_CG_INIT: k_cg_init<P, PX><<<grid, block, 0, st>>>(a); return true;
+    case B_CG_XR: k_cg_xr<P, PX><<<grid, block, 0, st>>>(a); return true;
+    case B_CG_P: k_cg_p<P><<<grid, block, 0, st>>>(a); return true;
   }
   return false;
 }
@@ -243,6 +326,28 @@ __global__ void __launch_bounds__(256) k_clover_site(const CopyArgs a, const cha
   }
 }
 
+// dst = gamma5 A src (A the site term at each site, or 1 with clov = null);
+// gamma5 = diag(1, 1, -1, -1) in the chiral basis commutes with A.
+template <int P>
+__global__ void __launch_bounds__(256) k_g5_site(const CopyArgs a, const char* clov) {
+  using R = typename Tr<P>::R;
+  const int rhs = blockIdx.x % a.nrhs;
+  if (a.red.cg != nullptr && a.red.check_done && a.red.cg[rhs].done != RUNNING) return;
+  BR_SITE_LOOP(a.vh, a.nblk) {
+    cx<R> s[12], d[12];
+    load_spinor<P>(a.src + rhs * a.src_rs, a.vh, ih, s);
+    if (clov) {
+      clover_apply<P>(clov, a.vh, ih, s, d);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) d[k] = s[k];
+    }
+#pragma unroll
+    for (int k = 6; k < 12; ++k) d[k] = cx<R>{-d[k].r, -d[k].i};
+    store_spinor<P>(a.dst + rhs * a.dst_rs, a.vh, ih, d);
+  }
+}
+
 #define BR_PREC_SWITCH(prec, KERNEL, ...)                                                    \
   switch (prec) {                                                                             \
     case P_F64: KERNEL<P_F64><<<grid, block, 0, st>>>(__VA_ARGS__); return true;             \
@@ -271,6 +376,10 @@ bool launch_norm2(int prec, const CopyArgs& a, int block, cudaStream_t st) {
 bool launch_clover_site(int prec, const CopyArgs& a, const char* clov, int block, cudaStream_t st) {
   const dim3 grid((unsigned)(a.nblk * a.nrhs));
   BR_PREC_SWITCH(prec, k_clover_site, a, clov)
+}
+bool launch_g5_site(int prec, const CopyArgs& a, const char* clov, int block, cudaStream_t st) {
+  const dim3 grid((unsigned)(a.nblk * a.nrhs));
+  BR_PREC_SWITCH(prec, k_g5_site, a, clov)
 }
 
 template <int PS>

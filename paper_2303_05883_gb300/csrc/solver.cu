@@ -67,6 +67,10 @@ PinnedBuf::~PinnedBuf() {
 }
 
 static int inner_prec(const bridge_solver& prm) { return prm.mixed ? prm.inner_prec : P_F64; }
+// Iterations a BiCGStab pass may take under BRIDGE_METHOD_AUTO before its
+// progress decides whether the following passes switch to CG on the normal
+// equations.
+static constexpr long kAutoPassCap = 1000;
 static int x_prec(int P) { return (P == P_F16 || P == P_BF16) ? P_F32 : P; }
 
 size_t solve_footprint(const bridge_lattice_s* L, const bridge_solver& prm, int nrhs) {
@@ -96,6 +100,7 @@ SolveState::SolveState(bridge_lattice_s* L, const bridge_op& op, const bridge_so
   if (prm_.max_outer <= 0) prm_.max_outer = 50;
   if (prm_.max_iter <= 0) prm_.max_iter = 20000;
   if (prm_.inner_tol <= 0) prm_.inner_tol = prm_.mixed ? (P_ == P_F32 ? 1e-5 : 2e-3) : std::max(prm_.tol * 0.25, 1e-15);
+  cgnr_ = prm_.method == BRIDGE_METHOD_CGNR;
   batch_iters_ = prm_.check_every;
   if (L_->stats.profiling) {
     // event-timed runs launch exactly the iterations that execute
@@ -124,6 +129,9 @@ SolveState::SolveState(bridge_lattice_s* L, const bridge_op& op, const bridge_so
   result_.reset(new DevBuf(sizeof(double) * 4 * 4 * nrhs, st_, true));
   mask_.reset(new DevBuf(sizeof(int) * nrhs, st_, true));
   for (int i = 0; i < 2; ++i) h_sc_[i].reset(new PinnedBuf(sizeof(BiCGScalars) * nrhs));
+  cgsc_.reset(new DevBuf(sizeof(CGScalars) * nrhs, st_, true));
+  for (int i = 0; i < 2; ++i) h_cg_[i].reset(new PinnedBuf(sizeof(CGScalars) * nrhs));
+  h_cginit_.reset(new PinnedBuf(sizeof(CGScalars) * nrhs));
   h_result_.reset(new PinnedBuf(sizeof(double) * 4 * 4 * nrhs));
   h_mask_.reset(new PinnedBuf(sizeof(int) * nrhs));
   h_init_.reset(new PinnedBuf(sizeof(BiCGScalars) * nrhs));
@@ -137,7 +145,7 @@ SolveState::SolveState(bridge_lattice_s* L, const bridge_op& op, const bridge_so
   failed_.assign(nrhs, 0);
   stall_.assign(nrhs, 0);
   info_.assign(nrhs, bridge_info{});
-  for (auto& k : graph_delta_) k = KStat{};
+
   // make the operator data for this precision before any graph capture
   gauge_ptr(L_, P_);
   gauge_ptr(L_, P_F64);
@@ -150,7 +158,8 @@ SolveState::SolveState(bridge_lattice_s* L, const bridge_op& op, const bridge_so
 }
 
 SolveState::~SolveState() {
-  if (graph_) cudaGraphExecDestroy(graph_);
+  for (auto& g : graphs_)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (auto& e : ev_)
     if (e) cudaEventDestroy(e);
   if (ev_misc_) cudaEventDestroy(ev_misc_);
@@ -280,9 +289,18 @@ void SolveState::begin_inner() {
     c.in_rs = rin_.rs;
   }
   run_hop(L_, c, st_);
+  if (cgnr_) {
+    begin_cgnr();
+    nvtxRangePop();
+    return;
+  }
   // stage the per-rhs tolerance and iteration budget, then x = 0, r = rhat = p = b^
   BiCGScalars* hi = reinterpret_cast<BiCGScalars*>(h_init_->ptr);
-  const long left = std::max<long>(1, (long)prm_.max_iter - inner_total_);
+  long left = std::max<long>(1, (long)prm_.max_iter - inner_total_);
+  // automatic method: a BiCGStab pass gets a bounded budget so that a
+  // stagnating one hands over to CG on the normal equations in time
+  if (prm_.method == BRIDGE_METHOD_AUTO && (op_.kind == BRIDGE_WILSON || op_.kind == BRIDGE_CLOVER))
+    left = std::min<long>(left, kAutoPassCap);
   for (int r = 0; r < nrhs_; ++r) {
     std::memset(&hi[r], 0, sizeof(BiCGScalars));
     hi[r].tol2 = prm_.inner_tol * prm_.inner_tol;
@@ -297,6 +315,10 @@ void SolveState::begin_inner() {
 }
 
 void SolveState::enqueue_iteration() {
+  if (cgnr_) {
+    enqueue_cg_iteration();
+    return;
+  }
   const double S = P_ == P_F64 ? 192 : P_ == P_F32 ? 96 : 52, SX = PX_ == P_F64 ? 192 : PX_ == P_F32 ? 96 : 52;
   HopCall c;
   c.prec = P_;
@@ -360,6 +382,214 @@ void SolveState::enqueue_iteration() {
   launch_blas(B_P, K_BLAS_P, 4 * S, 96, FIN_NONE, false);
 }
 
+// ---------------------------------------------------------------- CGNR
+// CG (Hestenes-Stiefel) on D^dag D^ e_e = D^dag b^_e, the normal equations of
+// the Eq. 1 Schur system.  Past the critical kappa the spectrum of D^ can
+// surround the origin, where BiCGStab (and any short-recurrence method on D^
+// itself) stagnates; D^dag D^ is Hermitian positive definite for any
+// non-singular D^, so CG converges, at a rate set by the condition number.
+// The adjoint follows from gamma5-hermiticity of the hopping term,
+// (H_oe)^dag = gamma5 H_eo gamma5, and T = T^dag commuting with gamma5:
+//   D^dag v = v - gamma5 D_eo T_oo^-1 D_oe gamma5 T_ee^-1 v,
+// three launches: s = gamma5 T_ee^-1 v; tmp = T_oo^-1 (-kappa H_oe s);
+// out = v + kappa gamma5 H_eo tmp.
+RedArgs SolveState::cg_red(int fin, bool check_done) {
+  RedArgs r = red(fin);
+  r.sc = nullptr;
+  r.cg = reinterpret_cast<CGScalars*>(cgsc_->ptr);
+  r.check_done = check_done ? 1 : 0;
+  return r;
+}
+
+void SolveState::cg_dhat_norm(const Field& in, const Field& out) {
+  HopCall c;
+  c.prec = P_;
+  c.nrhs = nrhs_;
+  c.kcsw = kcsw_;
+  c.clov = clov_.get();
+  for (int k = 0; k < 4; ++k) c.bc[k] = op_.bc[k];
+  c.count_work = false;
+  c.flags = clover_ ? F_E_CLOV : 0;
+  c.cls = K_DHAT1;
+  c.out_parity = 1;
+  c.beta = -op_.kappa;
+  c.in = in.ptr(0);
+  c.in_rs = in.rs;
+  c.out = tmp_.ptr(1);
+  c.out_rs = tmp_.rs;
+  c.redargs = cg_red(FIN_NONE, true);
+  c.redargs.partials = nullptr;  // no reduction, but skip finished right-hand sides
+  run_hop(L_, c, st_);
+  c.flags = F_SELF | (clover_ ? F_E_CLOV : 0);
+  c.red = R_NORM;
+  c.cls = K_DHAT2A;
+  c.out_parity = 0;
+  c.beta = op_.kappa;
+  c.s1 = 1.0;
+  c.in = tmp_.ptr(1);
+  c.in_rs = tmp_.rs;
+  c.self = in.ptr(0);
+  c.self_rs = in.rs;
+  c.out = out.ptr(0);
+  c.out_rs = out.rs;
+  c.redargs = cg_red(FIN_CG_ALPHA, true);
+  run_hop(L_, c, st_);
+}
+
+void SolveState::cg_dhat_dag(const Field& in, const Field& out, bool check_done) {
+  CopyArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.vh = (uint32_t)L_->vh;
+  a.nrhs = nrhs_;
+  a.g = L_->g;
+  a.V = L_->V;
+  a.nblk = (int)((L_->vh + 255) / 256);
+  a.src = in.ptr(0);
+  a.src_rs = in.rs;
+  a.dst = s_.ptr(0);
+  a.dst_rs = s_.rs;
+  a.red = cg_red(FIN_NONE, check_done);
+  const char* cl = clover_ ? clover_ptr(L_, *clov_, P_, true) : nullptr;  // parity 0 block first
+  note_launch(L_, K_CLOVER, 0, 0, st_, true);
+  BR_CHECK(launch_g5_site(P_, a, cl, 256, st_), BRIDGE_EINVAL, "precision");
+  note_launch(L_, K_CLOVER, 0, 0, st_, false);
+  BR_CUDA(cudaGetLastError());
+  HopCall c;
+  c.prec = P_;
+  c.nrhs = nrhs_;
+  c.kcsw = kcsw_;
+  c.clov = clov_.get();
+  for (int k = 0; k < 4; ++k) c.bc[k] = op_.bc[k];
+  c.count_work = false;
+  c.flags = clover_ ? F_E_CLOV : 0;
+  c.cls = K_DHAT1;
+  c.out_parity = 1;
+  c.beta = -op_.kappa;
+  c.in = s_.ptr(0);
+  c.in_rs = s_.rs;
+  c.out = tmp_.ptr(1);
+  c.out_rs = tmp_.rs;
+  c.redargs = cg_red(FIN_NONE, check_done);
+  c.redargs.partials = nullptr;
+  run_hop(L_, c, st_);
+  c.flags = F_SELF | F_G5;
+  c.cls = K_DHAT2;
+  c.out_parity = 0;
+  c.beta = op_.kappa;
+  c.s1 = 1.0;
+  c.in = tmp_.ptr(1);
+  c.in_rs = tmp_.rs;
+  c.self = in.ptr(0);
+  c.self_rs = in.rs;
+  c.out = out.ptr(0);
+  c.out_rs = out.rs;
+  run_hop(L_, c, st_);
+}
+
+void SolveState::begin_cgnr() {
+  // r = D^dag b^ (the CG scalars of the previous pass are stale: no skipping)
+  cg_dhat_dag(bh_, r_, false);
+  CGScalars* hi = reinterpret_cast<CGScalars*>(h_cginit_->ptr);
+  const long left = std::max<long>(1, (long)prm_.max_iter - inner_total_);
+  for (int r = 0; r < nrhs_; ++r) {
+    std::memset(&hi[r], 0, sizeof(CGScalars));
+    hi[r].tol2 = prm_.inner_tol * prm_.inner_tol;
+    hi[r].max_iter = (int)std::min<long>(left, 1L << 30);
+  }
+  BR_CUDA(cudaMemcpyAsync(cgsc_->ptr, hi, sizeof(CGScalars) * nrhs_, cudaMemcpyHostToDevice, st_));
+  const double S = P_ == P_F64 ? 192 : P_ == P_F32 ? 96 : 52, SX = PX_ == P_F64 ? 192 : PX_ == P_F32 ? 96 : 52;
+  {
+    BlasArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.vh = (uint32_t)L_->vh;
+    a.nrhs = nrhs_;
+    a.x = xin_.ptr(0);
+    a.x_rs = xin_.rs;
+    a.r = r_.ptr(0);
+    a.r_rs = r_.rs;
+    a.p = p_.ptr(0);
+    a.p_rs = p_.rs;
+    a.red = cg_red(FIN_CG_INIT, false);
+    const std::string key = "blas/" + std::to_string(B_CG_INIT) + "/" + std::to_string(P_) + "/" +
+                            std::to_string(L_->vh) + "/" + std::to_string(nrhs_);
+    LaunchShape sh = shape_for(L_, key, L_->vh, nrhs_, [&](int block) {
+      int n = 0;
+      bridge::launch_blas(B_CG_INIT, P_, PX_, a, block, st_, &n);
+      return n;
+    });
+    a.nblk = sh.nblk;
+    note_launch(L_, K_BLAS_INIT, (double)L_->vh * nrhs_ * (2 * S + SX), (double)L_->vh * nrhs_ * 24, st_, true);
+    BR_CHECK(bridge::launch_blas(B_CG_INIT, P_, PX_, a, sh.block, st_), BRIDGE_EINVAL, "blas variant");
+    note_launch(L_, K_BLAS_INIT, 0, 0, st_, false);
+    BR_CUDA(cudaGetLastError());
+  }
+  batches_launched_ = batches_checked_ = 0;
+  for (int k = 0; k < inflight_; ++k) enqueue_batch();
+}
+
+void SolveState::enqueue_cg_iteration() {
+  // q = D^ p (v), alpha = |r|^2 / |q|^2
+  cg_dhat_norm(p_, v_);
+  // w = D^dag q (t)
+  cg_dhat_dag(v_, t_, true);
+  for (int op : {B_CG_XR, B_CG_P}) {
+    BlasArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.vh = (uint32_t)L_->vh;
+    a.nrhs = nrhs_;
+    a.x = xin_.ptr(0);
+    a.x_rs = xin_.rs;
+    a.r = r_.ptr(0);
+    a.r_rs = r_.rs;
+    a.p = p_.ptr(0);
+    a.p_rs = p_.rs;
+    a.t = t_.ptr(0);
+    a.t_rs = t_.rs;
+    a.red = cg_red(op == B_CG_XR ? FIN_CG_BETA : FIN_NONE, true);
+    const std::string key = "blas/" + std::to_string(op) + "/" + std::to_string(P_) + "/" + std::to_string(L_->vh) +
+                            "/" + std::to_string(nrhs_);
+    LaunchShape sh = shape_for(L_, key, L_->vh, nrhs_, [&](int block) {
+      int n = 0;
+      bridge::launch_blas(op, P_, PX_, a, block, st_, &n);
+      return n;
+    });
+    a.nblk = sh.nblk;
+    const int cls = op == B_CG_XR ? K_BLAS_XR : K_BLAS_P;
+    note_launch(L_, cls, 0, 0, st_, true);
+    BR_CHECK(bridge::launch_blas(op, P_, PX_, a, sh.block, st_), BRIDGE_EINVAL, "blas variant");
+    note_launch(L_, cls, 0, 0, st_, false);
+    BR_CUDA(cudaGetLastError());
+  }
+}
+
+// Algorithmic work of the CG iterations that ran: per iteration two Schur
+// first passes, the second pass with |q|^2, the adjoint's gamma5 T^-1 and
+// second pass, and the two vector updates.
+void SolveState::credit_cg_iterations(const std::vector<long>& iters) {
+  long most = 0, sum = 0;
+  for (long n : iters) {
+    most = std::max(most, n);
+    sum += n;
+  }
+  if (most == 0) return;
+  const double vh = (double)L_->vh;
+  const double S = P_ == P_F64 ? 192 : P_ == P_F32 ? 96 : 52, SX = PX_ == P_F64 ? 192 : PX_ == P_F32 ? 96 : 52;
+  const double C = P_ == P_F64 ? 576 : P_ == P_F32 ? 288 : 144;
+  const int f1 = clover_ ? F_E_CLOV : 0, f2 = F_SELF | (clover_ ? F_E_CLOV : 0);
+  const HopCost h1 = hop_cost(P_, f1, R_NONE), hn = hop_cost(P_, f2, R_NORM), hd = hop_cost(P_, F_SELF, R_NONE);
+  std::lock_guard<std::mutex> lk(L_->stats.mu);
+  auto add = [&](int cls, double rhs_bytes, double shared_bytes, double rhs_flops) {
+    L_->stats.k[cls].bytes += vh * (rhs_bytes * sum + shared_bytes * most);
+    L_->stats.k[cls].flops += vh * rhs_flops * sum;
+  };
+  add(K_DHAT1, 2 * h1.rhs_bytes, 2 * h1.shared_bytes, 2 * h1.rhs_flops);
+  add(K_DHAT2A, hn.rhs_bytes, hn.shared_bytes, hn.rhs_flops);
+  add(K_DHAT2, hd.rhs_bytes, hd.shared_bytes, hd.rhs_flops);
+  add(K_CLOVER, 2 * S, clover_ ? C : 0.0, clover_ ? 504 : 0);
+  add(K_BLAS_XR, 4 * S + 2 * SX, 0, 96);
+  add(K_BLAS_P, 3 * S, 0, 48);
+}
+
 void SolveState::capture_batch() {
   KStat before[K_NCLASS];
   {
@@ -377,41 +607,46 @@ void SolveState::capture_batch() {
     throw;
   }
   BR_CUDA(cudaStreamEndCapture(st_, &g));
-  cudaError_t e = cudaGraphInstantiate(&graph_, g, 0);
+  GraphRec& gr = graphs_[cgnr_ ? 1 : 0];
+  cudaError_t e = cudaGraphInstantiate(&gr.exec, g, 0);
   cudaGraphDestroy(g);
   BR_CUDA(e);
   // nothing ran during capture: move the counted work into the per-replay delta
   std::lock_guard<std::mutex> lk(L_->stats.mu);
   for (int k = 0; k < K_NCLASS; ++k) {
-    graph_delta_[k].launches = L_->stats.k[k].launches - before[k].launches;
-    graph_delta_[k].bytes = L_->stats.k[k].bytes - before[k].bytes;
-    graph_delta_[k].flops = L_->stats.k[k].flops - before[k].flops;
+    gr.delta[k].launches = L_->stats.k[k].launches - before[k].launches;
+    gr.delta[k].bytes = L_->stats.k[k].bytes - before[k].bytes;
+    gr.delta[k].flops = L_->stats.k[k].flops - before[k].flops;
     L_->stats.k[k] = before[k];
   }
-  graph_launches_ = g_launches.load() - l0;
-  g_launches.fetch_sub(graph_launches_);
+  gr.launches = g_launches.load() - l0;
+  g_launches.fetch_sub(gr.launches);
 }
 
 void SolveState::enqueue_batch() {
   nvtxRangePushA("bridge: BiCGStab batch");
   const bool use_graph = prm_.use_graph && !L_->stats.profiling;
   if (use_graph) {
-    if (!graph_) capture_batch();
-    BR_CUDA(cudaGraphLaunch(graph_, st_));
+    GraphRec& gr = graphs_[cgnr_ ? 1 : 0];
+    if (!gr.exec) capture_batch();
+    BR_CUDA(cudaGraphLaunch(gr.exec, st_));
     {
       std::lock_guard<std::mutex> lk(L_->stats.mu);
       for (int k = 0; k < K_NCLASS; ++k) {
-        L_->stats.k[k].launches += graph_delta_[k].launches;
-        L_->stats.k[k].bytes += graph_delta_[k].bytes;
-        L_->stats.k[k].flops += graph_delta_[k].flops;
+        L_->stats.k[k].launches += gr.delta[k].launches;
+        L_->stats.k[k].bytes += gr.delta[k].bytes;
+        L_->stats.k[k].flops += gr.delta[k].flops;
       }
     }
-    g_launches.fetch_add(graph_launches_);
+    g_launches.fetch_add(gr.launches);
   } else {
     for (int it = 0; it < batch_iters_; ++it) enqueue_iteration();
   }
   const int slot = (int)(batches_launched_ & 1);
-  BR_CUDA(cudaMemcpyAsync(h_sc_[slot]->ptr, scal_->ptr, sizeof(BiCGScalars) * nrhs_, cudaMemcpyDeviceToHost, st_));
+  if (cgnr_)
+    BR_CUDA(cudaMemcpyAsync(h_cg_[slot]->ptr, cgsc_->ptr, sizeof(CGScalars) * nrhs_, cudaMemcpyDeviceToHost, st_));
+  else
+    BR_CUDA(cudaMemcpyAsync(h_sc_[slot]->ptr, scal_->ptr, sizeof(BiCGScalars) * nrhs_, cudaMemcpyDeviceToHost, st_));
   BR_CUDA(cudaEventRecord(ev_[slot], st_));
   ++batches_launched_;
   nvtxRangePop();
@@ -448,19 +683,38 @@ void SolveState::finish_inner() {
   struct Pop {
     ~Pop() { nvtxRangePop(); }
   } pop;
-  const BiCGScalars* sc = reinterpret_cast<const BiCGScalars*>(h_sc_[(batches_checked_ - 1) & 1]->ptr);
   long most = 0;
   std::vector<long> iters(nrhs_, 0);
-  for (int r = 0; r < nrhs_; ++r) {
-    if (!active_[r]) continue;
-    info_[r].inner_iters += sc[r].iter;
-    iters[r] = sc[r].iter;
-    most = std::max<long>(most, sc[r].iter);
-    if (sc[r].done == BREAKDOWN) info_[r].restarts += 1;
-    stall_[r] = (sc[r].iter == 0) ? stall_[r] + 1 : 0;
+  bool stagnated = false;
+  if (cgnr_) {
+    const CGScalars* cg = reinterpret_cast<const CGScalars*>(h_cg_[(batches_checked_ - 1) & 1]->ptr);
+    for (int r = 0; r < nrhs_; ++r) {
+      if (!active_[r]) continue;
+      info_[r].inner_iters += cg[r].iter;
+      info_[r].cgnr_passes += 1;
+      iters[r] = cg[r].iter;
+      most = std::max<long>(most, cg[r].iter);
+      if (cg[r].done == BREAKDOWN) info_[r].restarts += 1;
+      stall_[r] = (cg[r].iter == 0) ? stall_[r] + 1 : 0;
+    }
+    inner_total_ += most;
+    credit_cg_iterations(iters);
+  } else {
+    const BiCGScalars* sc = reinterpret_cast<const BiCGScalars*>(h_sc_[(batches_checked_ - 1) & 1]->ptr);
+    for (int r = 0; r < nrhs_; ++r) {
+      if (!active_[r]) continue;
+      info_[r].inner_iters += sc[r].iter;
+      iters[r] = sc[r].iter;
+      most = std::max<long>(most, sc[r].iter);
+      if (sc[r].done == BREAKDOWN) info_[r].restarts += 1;
+      stall_[r] = (sc[r].iter == 0) ? stall_[r] + 1 : 0;
+      // a pass that ended without reaching 1e-2 of its source: BiCGStab is
+      // not converging on this spectrum
+      if ((sc[r].done == MAXITER || sc[r].done == BREAKDOWN) && sc[r].r2 > 1e-4 * sc[r].b2) stagnated = true;
+    }
+    inner_total_ += most;
+    credit_iterations(iters);
   }
-  inner_total_ += most;
-  credit_iterations(iters);
   const int* mask = reinterpret_cast<const int*>(mask_->ptr);
   // e_o = T_oo^-1 (r_o + kappa H_oe e_e)
   const Field* xe = &xin_;
@@ -488,6 +742,11 @@ void SolveState::finish_inner() {
   run_hop(L_, c, st_);
   accumulate64(L_, xin_, 0, x64_, 0, st_, mask);
   accumulate64(L_, eo_, 1, x64_, 1, st_, mask);
+  // the remaining passes run CG on the normal equations
+  if (stagnated && prm_.method == BRIDGE_METHOD_AUTO) {
+    cgnr_ = true;
+    for (int r = 0; r < nrhs_; ++r) stall_[r] = 0;
+  }
 }
 
 bool SolveState::advance() {
@@ -579,11 +838,17 @@ bool SolveState::advance() {
         break;
       }
       case ST_INNER: {
-        const BiCGScalars* sc = reinterpret_cast<const BiCGScalars*>(h_sc_[batches_checked_ & 1]->ptr);
-        ++batches_checked_;
         bool all = true;
-        for (int r = 0; r < nrhs_; ++r)
-          if (sc[r].done == RUNNING) all = false;
+        if (cgnr_) {
+          const CGScalars* cg = reinterpret_cast<const CGScalars*>(h_cg_[batches_checked_ & 1]->ptr);
+          for (int r = 0; r < nrhs_; ++r)
+            if (cg[r].done == RUNNING) all = false;
+        } else {
+          const BiCGScalars* sc = reinterpret_cast<const BiCGScalars*>(h_sc_[batches_checked_ & 1]->ptr);
+          for (int r = 0; r < nrhs_; ++r)
+            if (sc[r].done == RUNNING) all = false;
+        }
+        ++batches_checked_;
         if (all) {
           finish_inner();
           enqueue_residual();

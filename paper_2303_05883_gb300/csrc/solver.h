@@ -68,6 +68,15 @@ class SolveState {
   void credit_iterations(const std::vector<long>& iters);
   void capture_batch();
   RedArgs red(int fin, int slot = 0);
+  // CG on the normal equations of the Schur system (the inner method where
+  // BiCGStab stagnates): D^ and its adjoint on even fields, the CG start
+  // from the prepared source and one CG iteration.
+  RedArgs cg_red(int fin, bool check_done);
+  void cg_dhat_norm(const Field& in, const Field& out);
+  void cg_dhat_dag(const Field& in, const Field& out, bool check_done);
+  void begin_cgnr();
+  void enqueue_cg_iteration();
+  void credit_cg_iterations(const std::vector<long>& iters);
 
   bridge_lattice_s* L_;
   bridge_op op_;
@@ -88,9 +97,15 @@ class SolveState {
   cudaEvent_t ev_misc_ = nullptr;
   cudaEvent_t pending_ = nullptr;
 
-  cudaGraphExec_t graph_ = nullptr;
-  KStat graph_delta_[K_NCLASS];
-  long graph_launches_ = 0;
+  // one captured batch per inner method (0 BiCGStab, 1 CG on the normal equations)
+  struct GraphRec {
+    cudaGraphExec_t exec = nullptr;
+    KStat delta[K_NCLASS];
+    long launches = 0;
+  } graphs_[2];
+  bool cgnr_ = false;                      // the current inner pass runs CG on D^dag D^
+  std::unique_ptr<DevBuf> cgsc_;           // CGScalars per right-hand side
+  std::unique_ptr<PinnedBuf> h_cg_[2], h_cginit_;
 
   State state_ = ST_START;
   int outer_ = 0;

@@ -70,12 +70,19 @@ def test_alone_equals_in_mix(api, lattices):
         alone.append(x)
     # all at once: the engine overlaps them on the GPU
     hs = [api.bridge_submit(lattices[dims][0].handle, op, s, b) for dims, op, b, s in reqs]
+    spans = []
     for (dims, op, b, s), h, xa in zip(reqs, hs, alone):
         st, x, info = api.bridge_wait(h)
+        _, t_admit, t_done = api.bridge_request_times(h)
+        spans.append((t_admit, t_done))
         api.bridge_request_release(h)
         assert st == 0 and all(i["true_rel_residual"] <= 1e-11 for i in info)
         assert rel(x, xa) <= 1e-10
         assert np.array_equal(x, xa)  # deterministic reductions: identical bits
+    # the mix really ran concurrently: some requests were on the GPU together
+    overlaps = sum(1 for i in range(len(spans)) for j in range(i + 1, len(spans))
+                   if spans[i][0] < spans[j][1] and spans[j][0] < spans[i][1])
+    assert overlaps >= 1, spans
 
 
 def test_engine_results_match_oracle(api, lattices):

@@ -285,3 +285,56 @@ def test_alu_peak_is_measured(api):
     f32, f64 = api.bridge_alu_peak("f32"), api.bridge_alu_peak("f64")
     assert 1e12 < f32 < 1.2e14
     assert 1e10 < f64 < f32 / 4
+
+
+@pytest.mark.parametrize("kind,prec", [("clover", "f64"), ("clover", "f32"), ("wilson", "f32"), ("clover", "f16")])
+def test_cgnr_inner_method_matches_oracle(api, kind, prec):
+    """CG on the normal equations of the Schur system (the inner method the
+    solver switches to where BiCGStab stagnates), forced for every pass, on a
+    lattice with several site blocks: the solution agrees with the oracle's
+    even-odd BiCGStab solution of the same system."""
+    from paper_2303_05883_gb300 import _abi
+
+    dims, kappa, nrhs = (4, 6, 8, 10), 0.125, 2
+    csw = 1.0 if kind == "clover" else 0.0
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, 0.3, 23)
+    B = synth.gaussian_spinor(dims, 23, nrhs=nrhs)
+    L = api.Lattice(dims)
+    op = api.make_op(kind, kappa, csw)
+    L.upload(U, op)
+    X, info = L.solve(op, B, api.make_solver(tol=1e-11, inner_prec=prec, method=_abi.BRIDGE_METHOD_CGNR,
+                                             max_iter=40000))
+    eo = evenodd.EvenOdd(U, lat, kappa, csw)
+    for k in range(nrhs):
+        xe, _ = solvers.bicgstab(eo.schur, eo.prepare(B[k]), tol=1e-14)
+        assert info[k]["status"] == 0 and info[k]["cgnr_passes"] == info[k]["outer_iters"], info[k]
+        assert rel(X[k], eo.reconstruct(xe, B[k])) < 1e-9, (k, rel(X[k], eo.reconstruct(xe, B[k])))
+    L.close()
+
+
+def test_auto_method_switches_to_cgnr_past_critical_kappa(api):
+    """kappa = 0.15 on a smooth field (links exp(0.1 i A)) is far past the
+    critical kappa: the eigenvalues of D surround the origin and BiCGStab
+    stagnates (alone it ends at the iteration limit), while D^dag D stays well
+    conditioned.  The automatic method switches to CG on the normal equations
+    after one stagnating BiCGStab pass and meets the tolerance; the oracle's
+    residual b - D x over the whole lattice confirms it."""
+    from paper_2303_05883_gb300 import _abi
+
+    dims, kappa = (8, 8, 8, 8), 0.15
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, 0.1, 11)
+    b = synth.gaussian_spinor(dims, 5)
+    L = api.Lattice(dims)
+    op = api.make_op("wilson", kappa)
+    L.upload(U, op)
+    _, info = L.solve(op, b, api.make_solver(tol=1e-10, method=_abi.BRIDGE_METHOD_BICGSTAB, max_iter=4000),
+                      raise_on_fail=False)
+    assert info[0]["status"] == _abi.BRIDGE_ENOCONV and info[0]["cgnr_passes"] == 0
+    x, info = L.solve(op, b, api.make_solver(tol=1e-10, max_iter=40000))
+    assert info[0]["status"] == 0 and info[0]["cgnr_passes"] >= 1, info[0]
+    assert info[0]["true_rel_residual"] <= 1e-10
+    r = b - dirac.dirac(U, x, lat, kappa, 0.0)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 2e-10
+    L.close()
