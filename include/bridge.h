@@ -243,6 +243,63 @@ int bridge_mult_Dhat_dag_dev(bridge_lattice lat, const bridge_op* op, int prec, 
 int bridge_mult_Dhat_noalloc(bridge_lattice lat, const bridge_op* op, int prec, const double* in_dev, double* out_dev,
                              int nrhs);
 
+/* ---- domain decomposition with halo exchange ------------------------------------ */
+
+/* The lattice cut into nparts slabs along t, each a sub-lattice with its own
+ * links, clover term, fields and stream, joined by a halo exchange on every
+ * application of the hopping term -- the decomposition the paper runs over
+ * MPI processes (Sec. 2: sub-lattices per process, boundary data exchanged
+ * with the neighbours by persistent communication while the bulk is
+ * computed; Sec. 3: weak and strong scaling).  Per hop term: the interior
+ * stencil of every slab (t hops leaving the slab left out) overlaps, on a
+ * second stream per slab, the packing of the two faces -- (1 - gamma_t) psi
+ * of the first time slice and U_t^dagger (1 + gamma_t) psi of the last, six
+ * complex numbers per face site -- and their copy into the neighbours'
+ * receive buffers; a boundary kernel then adds the crossing hops
+ * (reconstructed to four spin components, times beta, the global boundary
+ * phase where the hop wraps, and T^-1 for a T^-1 epilogue).  Dot products
+ * are per-slab partial sums added over all slabs.  Here the slabs share the
+ * caller's GPU and the exchange is a device-to-device copy. */
+typedef struct bridge_dd_s* bridge_dd;
+
+/* The face schedule of one slab (host arithmetic only, no device needed). */
+typedef struct {
+  int local_dims[4];       /* Lx, Ly, Lz, Lt / nparts */
+  int t0;                  /* first global time slice of the slab */
+  int rank_up;             /* slab holding time slice t0 + Lt / nparts (mod Lt): receives this slab's
+                              last-slice face, sends its first-slice face here */
+  int rank_down;           /* slab holding time slice t0 - 1 (mod Lt) */
+  long face_sites;         /* sites per parity of one time slice, Lx Ly Lz / 2; face site f of a slice is
+                              the site of that parity whose spatial lexicographic index s has s / 2 = f */
+  int up_wraps;            /* 1: forward t hops out of this slab cross the lattice boundary (phase bc[3]) */
+  int down_wraps;          /* 1: backward t hops out of this slab cross the lattice boundary */
+  long canon_offset_sites; /* lexicographic index of the slab's first site in the global lattice */
+} bridge_dd_plan;
+
+/* Face schedule of slab `rank` for global extents dims cut into nparts slabs.
+ * EINVAL unless every extent is even and >= 2 and Lt / nparts is even. */
+int bridge_dd_plan_of(const int dims[4], int nparts, int rank, bridge_dd_plan* plan);
+/* Decompose lattice lat (gauge field uploaded) for operator op (WILSON or
+ * CLOVER; the clover term is taken from the whole field) into nparts slabs.
+ * The handle refers to lat, which must outlive it.  Synchronous.  Errors:
+ * EINVAL (kind, bc, nparts), ESTATE (no gauge field), ENOMEM. */
+int bridge_dd_create(bridge_lattice lat, const bridge_op* op, int nparts, bridge_dd* out);
+int bridge_dd_destroy(bridge_dd dd);
+/* The operators of bridge_mult_D_dev / _Deo_dev / _Dhat_dev (same canonical
+ * device layouts, nrhs right-hand sides, any precision) through the
+ * decomposition.  Synchronous. */
+int bridge_dd_mult_D_dev(bridge_dd dd, int prec, const double* in_dev, double* out_dev, int nrhs);
+int bridge_dd_mult_Deo_dev(bridge_dd dd, int prec, int out_parity, const double* in_dev, double* out_dev, int nrhs);
+int bridge_dd_mult_Dhat_dev(bridge_dd dd, int prec, const double* in_dev, double* out_dev, int nrhs);
+/* Plain FP64 BiCGStab on the even-odd system of Eq. 1 over the slabs (every
+ * dot product summed over all slabs), solved to 0.1 s->tol in the Schur
+ * residual, then x_o reconstructed and the FP64 true residual ||b - D x|| /
+ * ||b|| of the whole lattice reported in info (status OK when it is <=
+ * s->tol).  b_dev / x_dev: canonical full fields on the device; x starts
+ * from zero.  Uses s->tol and s->max_iter only.  Synchronous. */
+int bridge_dd_solve_dev(bridge_dd dd, const bridge_solver* s, const double* b_dev, double* x_dev, int nrhs,
+                        bridge_info* info);
+
 /* ---- solver ------------------------------------------------------------------ */
 
 /* Solve D x = b for nrhs right-hand sides (Sec. 3: BiCGStab for the clover

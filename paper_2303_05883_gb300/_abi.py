@@ -60,6 +60,19 @@ class bridge_solver(ctypes.Structure):
     ]
 
 
+class bridge_dd_plan(ctypes.Structure):
+    _fields_ = [
+        ("local_dims", c_int * 4),
+        ("t0", c_int),
+        ("rank_up", c_int),
+        ("rank_down", c_int),
+        ("face_sites", c_long),
+        ("up_wraps", c_int),
+        ("down_wraps", c_int),
+        ("canon_offset_sites", c_long),
+    ]
+
+
 class bridge_info(ctypes.Structure):
     _fields_ = [
         ("status", c_int),
@@ -146,6 +159,13 @@ SIGNATURES = {
     "bridge_stats_reset": (c_int, [_h]),
     "bridge_profile": (c_int, [_h, c_int]),
     "bridge_launch_count": (c_long, []),
+    "bridge_dd_plan_of": (c_int, [POINTER(c_int), c_int, c_int, POINTER(bridge_dd_plan)]),
+    "bridge_dd_create": (c_int, [_h, POINTER(bridge_op), c_int, POINTER(_h)]),
+    "bridge_dd_destroy": (c_int, [_h]),
+    "bridge_dd_mult_D_dev": (c_int, [_h, c_int, c_void_p, c_void_p, c_int]),
+    "bridge_dd_mult_Deo_dev": (c_int, [_h, c_int, c_int, c_void_p, c_void_p, c_int]),
+    "bridge_dd_mult_Dhat_dev": (c_int, [_h, c_int, c_void_p, c_void_p, c_int]),
+    "bridge_dd_solve_dev": (c_int, [_h, POINTER(bridge_solver), c_void_p, c_void_p, c_int, POINTER(bridge_info)]),
     "bridge_device_alloc_count": (c_long, []),
     "bridge_alu_peak": (c_int, [c_int, _dp]),
     "bridge_tune": (c_int, [_h, POINTER(bridge_op), c_int, c_int]),

@@ -477,3 +477,79 @@ class Lattice:
         import torch
 
         return torch.cuda.ExternalStream(bridge_lattice_stream(self.handle))
+
+
+# --- domain decomposition with halo exchange ---------------------------------------------
+
+
+def bridge_dd_plan_of(dims, nparts, rank) -> dict:
+    """Face schedule of one slab (host arithmetic only)."""
+    pl = _abi.bridge_dd_plan()
+    d = (c_int * 4)(*[int(x) for x in dims])
+    check(_abi.load().bridge_dd_plan_of(d, int(nparts), int(rank), byref(pl)), "bridge_dd_plan_of")
+    return dict(local_dims=tuple(pl.local_dims), t0=pl.t0, rank_up=pl.rank_up, rank_down=pl.rank_down,
+                face_sites=pl.face_sites, up_wraps=pl.up_wraps, down_wraps=pl.down_wraps,
+                canon_offset_sites=pl.canon_offset_sites)
+
+
+class Decomposition:
+    """A lattice cut into nparts slabs along t, joined by a halo exchange
+    (bridge_dd_*).  Inputs may be host arrays or CUDA tensors; results come
+    back in the same kind."""
+
+    def __init__(self, lattice, op, nparts):
+        self.lattice, self.op, self.nparts = lattice, op, int(nparts)
+        h = c_void_p()
+        check(_abi.load().bridge_dd_create(lattice.handle, byref(op), self.nparts, byref(h)), "bridge_dd_create")
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            check(_abi.load().bridge_dd_destroy(self.handle), "bridge_dd_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _dev(a):
+        import torch
+
+        if _is_torch_cuda(a):
+            return a.contiguous(), True
+        return torch.from_numpy(np.ascontiguousarray(_host(a))).cuda(), False
+
+    def _mult(self, name, prec, psi, *extra):
+        src, on_dev = self._dev(psi)
+        out = src.new_empty(src.shape)
+        nrhs = 1 if src.dim() == 3 else src.shape[0]
+        _torch_sync()
+        check(getattr(_abi.load(), name)(self.handle, _prec(prec), *extra, c_void_p(src.data_ptr()),
+                                         c_void_p(out.data_ptr()), nrhs), name)
+        return out if on_dev else out.cpu().numpy()
+
+    def D(self, psi, prec="f64"):
+        return self._mult("bridge_dd_mult_D_dev", prec, psi)
+
+    def Deo(self, psi, out_parity=0, prec="f64"):
+        return self._mult("bridge_dd_mult_Deo_dev", prec, psi, int(out_parity))
+
+    def Dhat(self, psi, prec="f64"):
+        return self._mult("bridge_dd_mult_Dhat_dev", prec, psi)
+
+    def solve(self, b, solver=None, raise_on_fail=True):
+        solver = solver or make_solver()
+        src, on_dev = self._dev(b)
+        x = src.new_zeros(src.shape)
+        nrhs = 1 if src.dim() == 3 else src.shape[0]
+        info = (bridge_info * nrhs)()
+        _torch_sync()
+        check(_abi.load().bridge_dd_solve_dev(self.handle, byref(solver), c_void_p(src.data_ptr()),
+                                              c_void_p(x.data_ptr()), nrhs, info), "bridge_dd_solve_dev")
+        infos = _infos(info, nrhs)
+        if raise_on_fail and any(i["status"] != 0 for i in infos):
+            raise _abi.BridgeError(infos[0]["status"], "bridge_dd_solve_dev")
+        return (x if on_dev else x.cpu().numpy()), infos

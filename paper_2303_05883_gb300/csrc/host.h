@@ -252,8 +252,11 @@ void apply_dhat(bridge_lattice_s* L, const bridge_op& op, const Field& out, cons
                 cudaStream_t st);
 
 // Canonical FP64 (device) <-> field.  full: canonical holds whole lattices.
-void canon_to_field(bridge_lattice_s* L, const double* canon, const Field& f, cudaStream_t st, const int* mask = nullptr);
-void field_to_canon(bridge_lattice_s* L, const Field& f, double* canon, cudaStream_t st);
+// canon_rs: doubles between right-hand sides of the canonical array (0: the
+// field's own site count x 24, i.e. contiguous right-hand sides).
+void canon_to_field(bridge_lattice_s* L, const double* canon, const Field& f, cudaStream_t st, const int* mask = nullptr,
+                    long canon_rs = 0);
+void field_to_canon(bridge_lattice_s* L, const Field& f, double* canon, cudaStream_t st, long canon_rs = 0);
 void convert_field(bridge_lattice_s* L, const Field& src, const Field& dst, int parity, cudaStream_t st, const int* mask);
 void accumulate64(bridge_lattice_s* L, const Field& src, int src_parity, const Field& dst64, int dst_parity, cudaStream_t st,
                   const int* mask);

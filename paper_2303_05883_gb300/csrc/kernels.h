@@ -53,6 +53,7 @@ struct CopyArgs {
   const double* canon;  // canonical FP64 (re, im) pairs
   double* canon_out;
   int canon_full;       // 1: canonical is a full-lattice field, 0: a half-lattice one
+  long canon_rs;        // double2 entries between right-hand sides of canon / canon_out (0: 12 x sites)
   const char* src;
   long src_rs;
   char* dst;

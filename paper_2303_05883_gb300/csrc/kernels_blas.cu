@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(256) k_canon_to_field(const CopyArgs a) {
   const bool on = a.mask == nullptr || a.mask[rhs] != 0;
   const long n_sites = a.canon_full ? a.V : (long)a.vh;
   BR_SITE_LOOP(a.vh, a.nblk) {
-    const double2* src = reinterpret_cast<const double2*>(a.canon) + ((long)rhs * n_sites + canon_site(a, ih)) * 12;
+    const long crs = a.canon_rs ? a.canon_rs : n_sites * 12;
+    const double2* src = reinterpret_cast<const double2*>(a.canon) + (long)rhs * crs + canon_site(a, ih) * 12;
     cx<R> s[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -259,7 +260,8 @@ __global__ void __launch_bounds__(256) k_field_to_canon(const CopyArgs a) {
   BR_SITE_LOOP(a.vh, a.nblk) {
     cx<R> s[12];
     load_spinor<P>(a.src + rhs * a.src_rs, a.vh, ih, s);
-    double2* dst = reinterpret_cast<double2*>(a.canon_out) + ((long)rhs * n_sites + canon_site(a, ih)) * 12;
+    const long crs = a.canon_rs ? a.canon_rs : n_sites * 12;
+    double2* dst = reinterpret_cast<double2*>(a.canon_out) + (long)rhs * crs + canon_site(a, ih) * 12;
 #pragma unroll
     for (int k = 0; k < 12; ++k) dst[k] = make_double2((double)s[k].r, (double)s[k].i);
   }

@@ -395,11 +395,13 @@ static CopyArgs copy_args(bridge_lattice_s* L, const Field& f, int parity) {
   return a;
 }
 
-void canon_to_field(bridge_lattice_s* L, const double* canon, const Field& f, cudaStream_t st, const int* mask) {
+void canon_to_field(bridge_lattice_s* L, const double* canon, const Field& f, cudaStream_t st, const int* mask,
+                    long canon_rs) {
   const int lo = f.subset == BRIDGE_FULL ? 0 : f.subset, hi = f.subset == BRIDGE_FULL ? 1 : f.subset;
   for (int p = lo; p <= hi; ++p) {
     CopyArgs a = copy_args(L, f, p);
     a.canon = canon;
+    a.canon_rs = canon_rs / 2;
     a.canon_full = f.subset == BRIDGE_FULL;
     a.dst = f.ptr(p);
     a.dst_rs = f.rs;
@@ -412,11 +414,12 @@ void canon_to_field(bridge_lattice_s* L, const double* canon, const Field& f, cu
   BR_CUDA(cudaGetLastError());
 }
 
-void field_to_canon(bridge_lattice_s* L, const Field& f, double* canon, cudaStream_t st) {
+void field_to_canon(bridge_lattice_s* L, const Field& f, double* canon, cudaStream_t st, long canon_rs) {
   const int lo = f.subset == BRIDGE_FULL ? 0 : f.subset, hi = f.subset == BRIDGE_FULL ? 1 : f.subset;
   for (int p = lo; p <= hi; ++p) {
     CopyArgs a = copy_args(L, f, p);
     a.canon_out = canon;
+    a.canon_rs = canon_rs / 2;
     a.canon_full = f.subset == BRIDGE_FULL;
     a.src = f.ptr(p);
     a.src_rs = f.rs;
