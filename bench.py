@@ -161,7 +161,7 @@ def traffic_for(kernel: str, workload: str):
 
 def kernel_source_hash(kernel: str = "") -> str:
     d = hashlib.sha256()
-    files = ["common.cuh", "dslash.cuh", "reduce.cuh"] + (["dwf.cuh"] if kernel.startswith("dwf") else []) + (
+    files = ["common.cuh", "dslash.cuh", "dslash_tile.cuh", "reduce.cuh"] + (["dwf.cuh"] if kernel.startswith("dwf") else []) + (
         ["stag.cuh"] if kernel.startswith("stag") else []) + (["mg.cuh"] if kernel.startswith("mg") else [])
     for f in files:
         d.update(open(os.path.join(ROOT, "paper_2303_05883_gb300", "csrc", f), "rb").read())
@@ -524,6 +524,7 @@ def multi_rhs_leg(args, api, local, peak, alu):
         ach = d["bytes"] / d["launches"] / (us * 1e-6) / 1e9
         tf = site_rhs * fl / (us * 1e-6) / 1e12
         kernels[k] = {"avg_launch_us": us, "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                      "traffic": traffic_for(k, w.name),
                       "gbs": ach, "hbm_frac": ach / peak, "tflops": tf,
                       "fp32_frac": tf / alu["f32_tflops"] if alu else None,
                       "share_of_step": d["ms"] / step_ms if step_ms else None}
