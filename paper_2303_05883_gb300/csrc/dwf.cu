@@ -267,7 +267,9 @@ void run_dwf_hop(bridge_lattice_s* L, const DwfSet& set, const bridge_op& op, co
   a.out_parity = c.out_parity;
   a.Ls = c.Ls;
   a.nrhs = c.nrhs;
-  a.ns = sites_per_block(sh.block, c.Ls, c.prec);
+  // with two slices per thread a block of sh.block threads covers twice the sites
+  const int spt = c.prec == P_F64 ? 1 : dwf_variant_spt(sh.variant, c.Ls);
+  a.ns = sites_per_block(sh.block * spt, c.Ls, c.prec);
   a.nsb = (int)((L->vh + a.ns - 1) / a.ns);
   a.scale = c.scale;
   a.scalef = (float)c.scale;

@@ -244,6 +244,46 @@ BR_D void hop_shared(const char* in, long vh, uint32_t nbw, const cx<typename Tr
   reconstruct<R, MU, FWD>(u, acc);
 }
 
+// The same hop for SPT slices of one site (slices q0 + j * qstep): the link,
+// the neighbour index and its address arithmetic are read once and shared.
+template <int P, int MU, bool FWD, int SPT>
+BR_D void hop_shared_multi(const char* in, long in_bs, long qstep, long vh, uint32_t nbw,
+                           const cx<typename Tr<P>::R>* lk, int ns, typename Tr<P>::R bc,
+                           cx<typename Tr<P>::R> acc[SPT][12]) {
+  using R = typename Tr<P>::R;
+  const uint32_t nb = nbw & 0x7fffffffu;
+  const bool wraps = (nbw >> 31) != 0;
+  cx<R> U[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) U[k] = lk[k * ns];
+#pragma unroll
+  for (int j = 0; j < SPT; ++j) {
+    cx<R> h[2][3];
+    {
+      cx<R> psi[12];
+      load_spinor<P>(in + j * qstep * in_bs, vh, nb, psi);
+      project<R, MU, FWD>(psi, h);
+    }
+    if (wraps) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[k][c] = bc * h[k][c];
+    }
+    cx<R> u[2][3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        if (FWD)
+          u[k][r] = crow3(U[3 * r], U[3 * r + 1], U[3 * r + 2], h[k]);
+        else
+          u[k][r] = crow3_conj(U[r], U[3 + r], U[6 + r], h[k]);
+      }
+    reconstruct<R, MU, FWD>(u, acc[j]);
+  }
+}
+
 // Stage the links and neighbour indices of the block's ns sites: entry
 // d = 2 mu + (0 forward, 1 backward) holds U_mu(x) or U_mu(x - mu) with all 9
 // entries (row 2 rebuilt for 12-real storage) at shl[(d * 9 + k) * ns + site].
@@ -279,13 +319,17 @@ BR_D void stage_links(const DwfArgs& a, int sb, cx<typename Tr<P>::R>* shl, uint
 }
 
 // MINB: resident 256-thread blocks per SM the register allocation must allow
-// (2: <= 128 registers, 3: <= 85, 4: <= 64); picked per kernel by the tuner.
-template <int P, bool M1, int M2, int EPI, int MINB = 2>
+// (1: no cap, 2: <= 128 registers, 3: <= 85, 4: <= 64); SPT: slices per
+// thread (1, or 2 for even Ls: slices s and s + Ls / 2 of one site share the
+// link reads, neighbour index and address arithmetic of every hop, and give
+// the thread two independent FMA chains).  Picked per kernel by the tuner.
+template <int P, bool M1, int M2, int EPI, int MINB = 2, int SPT = 1>
 __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
   using R = typename Tr<P>::R;
   extern __shared__ __align__(16) unsigned char dsm[];
   const int Ls = a.Ls, ns = a.ns;
   const int nm = 2 * Ls * Ls;
+  const int lss = Ls / SPT;  // slice groups
   cx<R>* shl = reinterpret_cast<cx<R>*>(dsm);                 // [8][9][ns] links
   uint32_t* shn = reinterpret_cast<uint32_t*>(shl + 72L * ns);  // [8][ns] neighbours
   const bool fact = a.fact != 0;
@@ -296,13 +340,13 @@ __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
 
   const int rhs = blockIdx.x % a.nrhs;
   const int sb = blockIdx.x / a.nrhs;
-  const int sl = threadIdx.x % ns, s = threadIdx.x / ns;
+  const int sl = threadIdx.x % ns, s0 = threadIdx.x / ns;
   const uint32_t ih = (uint32_t)sb * ns + sl;
   const long vh = a.g.vh;
-  const bool live = s < Ls;
+  const bool live = s0 < lss;
   const bool skip = a.red.check_done && a.red.cg != nullptr && a.red.cg[rhs].done != RUNNING;
   const bool valid = live && ih < (uint32_t)vh && !skip;
-  const long q = (long)rhs * Ls + s;
+  const long q0 = (long)rhs * Ls + s0;  // slice j of this thread: q0 + j * lss
 
   if (M1 && !fact)
     for (int i = threadIdx.x; i < nm; i += blockDim.x) mat1[i] = reinterpret_cast<const R*>(a.m1)[i];
@@ -311,35 +355,44 @@ __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
   if (!skip) stage_links<P>(a, sb, shl, shn);
   __syncthreads();
 
-  cx<R> acc[12];
+  cx<R> acc[SPT][12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) acc[k] = czero<R>();
+  for (int j = 0; j < SPT; ++j)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[j][k] = czero<R>();
   if (valid) {
-    const char* in = a.in + q * a.in_bs;
+    const char* in = a.in + q0 * a.in_bs;
     const cx<R>* lk = shl + sl;
     const uint32_t* nw = shn + sl;
-    hop_shared<P, 0, true>(in, vh, nw[0 * ns], lk + 0 * 9 * ns, ns, pick<R>(a.bc[0], a.bcf[0]), acc);
-    hop_shared<P, 0, false>(in, vh, nw[1 * ns], lk + 1 * 9 * ns, ns, pick<R>(a.bc[0], a.bcf[0]), acc);
-    hop_shared<P, 1, true>(in, vh, nw[2 * ns], lk + 2 * 9 * ns, ns, pick<R>(a.bc[1], a.bcf[1]), acc);
-    hop_shared<P, 1, false>(in, vh, nw[3 * ns], lk + 3 * 9 * ns, ns, pick<R>(a.bc[1], a.bcf[1]), acc);
-    hop_shared<P, 2, true>(in, vh, nw[4 * ns], lk + 4 * 9 * ns, ns, pick<R>(a.bc[2], a.bcf[2]), acc);
-    hop_shared<P, 2, false>(in, vh, nw[5 * ns], lk + 5 * 9 * ns, ns, pick<R>(a.bc[2], a.bcf[2]), acc);
-    hop_shared<P, 3, true>(in, vh, nw[6 * ns], lk + 6 * 9 * ns, ns, pick<R>(a.bc[3], a.bcf[3]), acc);
-    hop_shared<P, 3, false>(in, vh, nw[7 * ns], lk + 7 * 9 * ns, ns, pick<R>(a.bc[3], a.bcf[3]), acc);
+    hop_shared_multi<P, 0, true, SPT>(in, a.in_bs, lss, vh, nw[0 * ns], lk + 0 * 9 * ns, ns, pick<R>(a.bc[0], a.bcf[0]), acc);
+    hop_shared_multi<P, 0, false, SPT>(in, a.in_bs, lss, vh, nw[1 * ns], lk + 1 * 9 * ns, ns, pick<R>(a.bc[0], a.bcf[0]), acc);
+    hop_shared_multi<P, 1, true, SPT>(in, a.in_bs, lss, vh, nw[2 * ns], lk + 2 * 9 * ns, ns, pick<R>(a.bc[1], a.bcf[1]), acc);
+    hop_shared_multi<P, 1, false, SPT>(in, a.in_bs, lss, vh, nw[3 * ns], lk + 3 * 9 * ns, ns, pick<R>(a.bc[1], a.bcf[1]), acc);
+    hop_shared_multi<P, 2, true, SPT>(in, a.in_bs, lss, vh, nw[4 * ns], lk + 4 * 9 * ns, ns, pick<R>(a.bc[2], a.bcf[2]), acc);
+    hop_shared_multi<P, 2, false, SPT>(in, a.in_bs, lss, vh, nw[5 * ns], lk + 5 * 9 * ns, ns, pick<R>(a.bc[2], a.bcf[2]), acc);
+    hop_shared_multi<P, 3, true, SPT>(in, a.in_bs, lss, vh, nw[6 * ns], lk + 6 * 9 * ns, ns, pick<R>(a.bc[3], a.bcf[3]), acc);
+    hop_shared_multi<P, 3, false, SPT>(in, a.in_bs, lss, vh, nw[7 * ns], lk + 7 * 9 * ns, ns, pick<R>(a.bc[3], a.bcf[3]), acc);
     const R sc = pick<R>(a.scale, a.scalef);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = sc * acc[k];
-  }
-  if (M1 && live) stage_row(shh, ns, s, sl, acc);
-  if (M2 == DM2_DENSE && live) {
-    cx<R> v[12];
-    if (valid) {
-      load_spinor<P>(a.self + q * a.self_bs, vh, ih, v);
-    } else {
+    for (int j = 0; j < SPT; ++j)
 #pragma unroll
-      for (int k = 0; k < 12; ++k) v[k] = czero<R>();
+      for (int k = 0; k < 12; ++k) acc[j][k] = sc * acc[j][k];
+  }
+  if (M1 && live)
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) stage_row(shh, ns, s0 + j * lss, sl, acc[j]);
+  if (M2 == DM2_DENSE && live) {
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+      cx<R> v[12];
+      if (valid) {
+        load_spinor<P>(a.self + (q0 + j * lss) * a.self_bs, vh, ih, v);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = czero<R>();
+      }
+      stage_row(shs, ns, s0 + j * lss, sl, v);
     }
-    stage_row(shs, ns, s, sl, v);
   }
   if (M1 || M2 == DM2_DENSE) __syncthreads();
   if (fact) {
@@ -349,59 +402,64 @@ __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
 
   R nrm = R(0);
   if (valid) {
-    cx<R> v[12];
-    if (M1 && fact) {
 #pragma unroll
-      for (int k = 0; k < 12; ++k) v[k] = shh[((long)s * 12 + k) * ns + sl];
-    } else if (M1) {
-      smix_row(mat1, shh, Ls, ns, s, sl, v);
-    } else {
+    for (int j = 0; j < SPT; ++j) {
+      const int s = s0 + j * lss;
+      const long q = q0 + (long)j * lss;
+      cx<R> v[12];
+      if (M1 && fact) {
 #pragma unroll
-      for (int k = 0; k < 12; ++k) v[k] = acc[k];
-    }
-    if (M2 == DM2_PLAIN) {
-      cx<R> w[12];
-      load_spinor<P>(a.self + q * a.self_bs, vh, ih, w);
-      const R s2 = pick<R>(a.s2, a.s2f);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) v[k] = v[k] + s2 * w[k];
-    } else if (M2 == DM2_DENSE) {
-      cx<R> w[12];
-      if (fact) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) w[k] = shs[((long)s * 12 + k) * ns + sl];
+        for (int k = 0; k < 12; ++k) v[k] = shh[((long)s * 12 + k) * ns + sl];
+      } else if (M1) {
+        smix_row(mat1, shh, Ls, ns, s, sl, v);
       } else {
-        smix_row(mat2, shs, Ls, ns, s, sl, w);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = acc[j][k];
       }
+      if (M2 == DM2_PLAIN) {
+        cx<R> w[12];
+        load_spinor<P>(a.self + q * a.self_bs, vh, ih, w);
+        const R s2 = pick<R>(a.s2, a.s2f);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) v[k] = v[k] + w[k];
-    }
-    if (a.aux != nullptr) {
-      cx<R> w[12];
-      load_spinor<P>(a.aux + q * a.aux_bs, vh, ih, w);
-      const R ca = pick<R>(a.caux, a.cauxf);
+        for (int k = 0; k < 12; ++k) v[k] = v[k] + s2 * w[k];
+      } else if (M2 == DM2_DENSE) {
+        cx<R> w[12];
+        if (fact) {
 #pragma unroll
-      for (int k = 0; k < 12; ++k) v[k] = v[k] + ca * w[k];
-    }
-    if (EPI == DE_CGUPD) {
-      const R alpha = (R)a.red.cg[rhs].alpha;
-      cx<R> xv[12], rv[12], pv[12];
-      load_spinor<P, false>(a.x + q * a.cg_bs, vh, ih, xv);
-      load_spinor<P, false>(a.r + q * a.cg_bs, vh, ih, rv);
-      load_spinor<P>(a.p + q * a.cg_bs, vh, ih, pv);
+          for (int k = 0; k < 12; ++k) w[k] = shs[((long)s * 12 + k) * ns + sl];
+        } else {
+          smix_row(mat2, shs, Ls, ns, s, sl, w);
+        }
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        xv[k] = xv[k] + alpha * pv[k];
-        rv[k] = rv[k] - alpha * v[k];
-        nrm += rv[k].r * rv[k].r + rv[k].i * rv[k].i;
+        for (int k = 0; k < 12; ++k) v[k] = v[k] + w[k];
       }
-      store_spinor<P>(a.x + q * a.cg_bs, vh, ih, xv);
-      store_spinor<P>(a.r + q * a.cg_bs, vh, ih, rv);
-    } else {
-      store_spinor<P>(a.out + q * a.out_bs, vh, ih, v);
-      if (EPI == DE_NORM)
+      if (a.aux != nullptr) {
+        cx<R> w[12];
+        load_spinor<P>(a.aux + q * a.aux_bs, vh, ih, w);
+        const R ca = pick<R>(a.caux, a.cauxf);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) nrm += v[k].r * v[k].r + v[k].i * v[k].i;
+        for (int k = 0; k < 12; ++k) v[k] = v[k] + ca * w[k];
+      }
+      if (EPI == DE_CGUPD) {
+        const R alpha = (R)a.red.cg[rhs].alpha;
+        cx<R> xv[12], rv[12], pv[12];
+        load_spinor<P, false>(a.x + q * a.cg_bs, vh, ih, xv);
+        load_spinor<P, false>(a.r + q * a.cg_bs, vh, ih, rv);
+        load_spinor<P>(a.p + q * a.cg_bs, vh, ih, pv);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          xv[k] = xv[k] + alpha * pv[k];
+          rv[k] = rv[k] - alpha * v[k];
+          nrm += rv[k].r * rv[k].r + rv[k].i * rv[k].i;
+        }
+        store_spinor<P>(a.x + q * a.cg_bs, vh, ih, xv);
+        store_spinor<P>(a.r + q * a.cg_bs, vh, ih, rv);
+      } else {
+        store_spinor<P>(a.out + q * a.out_bs, vh, ih, v);
+        if (EPI == DE_NORM)
+#pragma unroll
+          for (int k = 0; k < 12; ++k) nrm += v[k].r * v[k].r + v[k].i * v[k].i;
+      }
     }
   }
   if (EPI != DE_NONE) {

@@ -18,25 +18,28 @@ static void allow_smem(K kernel, long need, long (&limit)[64]) {
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) == cudaSuccess) cur = need;
 }
 
-template <int P, bool M1, int M2, int EPI, int MINB>
+template <int P, bool M1, int M2, int EPI, int MINB, int SPT>
 static bool go_hop1(const DwfArgs& a, cudaStream_t st) {
   static long limit[64] = {};
-  auto k = dwf_hop_kernel<P, M1, M2, EPI, MINB>;
+  auto k = dwf_hop_kernel<P, M1, M2, EPI, MINB, SPT>;
   const long smem = dwf_hop_smem(P, a.Ls, a.ns, M1, M2 == DM2_DENSE, a.fact != 0);
   allow_smem(k, smem, limit);
-  k<<<a.nsb * a.nrhs, dwf_threads(a.ns, a.Ls), smem, st>>>(a);
+  k<<<a.nsb * a.nrhs, dwf_threads(a.ns, a.Ls / SPT), smem, st>>>(a);
   return true;
 }
 
-// Register-budget variant v -> MINB 2, 3, 4 (FP32); FP64 has only v = 0.
+// Variant v -> (register budget MINB, slices per thread): 0 (2, 1), 1 (3, 1),
+// 2 (4, 1), 3 (1, 2), 4 (2, 2) for FP32 (two slices per thread need an even
+// Ls); FP64 has only v = 0.
 template <int P, bool M1, int M2, int EPI>
 static bool go_hop(const DwfArgs& a, cudaStream_t st, int v) {
   if constexpr (P == P_F64) {
-    return go_hop1<P, M1, M2, EPI, 1>(a, st);
+    return go_hop1<P, M1, M2, EPI, 1, 1>(a, st);
   } else {
-    if (v == 1) return go_hop1<P, M1, M2, EPI, 3>(a, st);
-    if (v == 2) return go_hop1<P, M1, M2, EPI, 4>(a, st);
-    return go_hop1<P, M1, M2, EPI, 2>(a, st);
+    if (dwf_variant_spt(v, a.Ls) == 2) return v == 3 ? go_hop1<P, M1, M2, EPI, 1, 2>(a, st) : go_hop1<P, M1, M2, EPI, 2, 2>(a, st);
+    if (v == 1) return go_hop1<P, M1, M2, EPI, 3, 1>(a, st);
+    if (v == 2) return go_hop1<P, M1, M2, EPI, 4, 1>(a, st);
+    return go_hop1<P, M1, M2, EPI, 2, 1>(a, st);
   }
 }
 

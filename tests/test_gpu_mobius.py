@@ -213,3 +213,42 @@ def test_dense_fifth_dimension_path(api, monkeypatch, how):
         assert info[0]["status"] == 0
         assert np.linalg.norm(psi - orc.full(x)) / np.linalg.norm(psi) < 1.5e-10
     L.close()
+
+
+# every (fifth-dimension matrix, self term, epilogue) combination of the hop kernel
+_DWF_COMBOS = [(1, 0, 0), (1, 1, 0), (1, 1, 1), (1, 1, 2), (1, 2, 0), (0, 0, 0), (0, 2, 0), (0, 2, 1)]
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+@pytest.mark.parametrize("dims,Ls", [((4, 2, 4, 6), 16), ((6, 6, 2, 4), 7), ((4, 4, 4, 8), 8)],
+                         ids=["4x2x4x6_Ls16", "6x6x2x4_Ls7", "4x4x4x8_Ls8"])
+def test_two_slices_per_thread_variants(api, dims, Ls, variant):
+    """The hop kernels with two fifth-dimension slices per thread (links,
+    neighbour indices and addresses shared by the slices s and s + Ls/2),
+    pinned for every kernel of the operators and of the CG solve, against the
+    oracle; an odd Ls runs the same variant with one slice per thread."""
+    lat, U, orc, op, L = _setup(api, dims, Ls, 0.4, 40 + Ls)
+    key = "x".join(map(str, dims))
+    for nrhs in (1, 2):
+        for m1, m2, epi in _DWF_COMBOS:
+            api.bridge_tune_set(L.handle, f"dwf/1/{m1}/{m2}/{epi}/Ls{Ls}/{key}/{nrhs}", 128, 1, variant)
+    nrhs = 2
+    psi = synth.gaussian_spinor(dims, 9, nrhs=nrhs * Ls).reshape(nrhs, Ls, lat.V, 4, 3)
+    got = L.D(op, psi, "f32")
+    for r in range(nrhs):
+        assert rel(got[r], orc.full(psi[r])) < TOL["f32"], ("D", r)
+    for q in (0, 1):
+        half = np.ascontiguousarray(psi[:, :, lat.sites_of(1 - q)])
+        got = L.Deo(op, half, q, "f32")
+        for r in range(nrhs):
+            assert rel(got[r], orc.D_hop(q, half[r])) < TOL["f32"], ("Deo", q, r)
+    xe = np.ascontiguousarray(psi[:, :, lat.even])
+    got, got_dag = L.Dhat(op, xe, "f32"), L.Dhat_dag(op, xe, "f32")
+    for r in range(nrhs):
+        assert rel(got[r], orc.schur(xe[r])) < TOL["f32"], ("Dhat", r)
+        assert rel(got_dag[r], orc.schur_dag(xe[r])) < TOL["f32"], ("Dhat_dag", r)
+    b = psi[0]
+    x, info = L.solve(op, b, api.make_solver(tol=1e-10, inner_prec="f32"))
+    assert info[0]["status"] == 0
+    assert np.linalg.norm(b - orc.full(x)) / np.linalg.norm(b) <= 1.5e-10
+    L.close()
