@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--multi-rhs", default="clover_48x48x48x96_12rhs",
                     help="clover workload: the multi-RHS workload measured beside it ('' to skip)")
     ap.add_argument("--multi-rhs-steps", type=int, default=2, help="timed solves of the multi-RHS workload")
+    ap.add_argument("--oracle-solves", action="store_true",
+                    help="reference arm: also time the oracle's even-odd BiCGStab on the 8^4 Wilson and a 16^4 clover system")
     ap.add_argument("--deo-only", action="store_true",
                     help="Moebius workload: only the operator legs (one Schur operator, then D_eo), for profiler captures")
     return ap.parse_args()
@@ -497,7 +499,34 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": max(cores_all), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    if args.oracle_solves:
+        line["oracle_solves"] = oracle_solves()
     print(json.dumps(line), flush=True)
+
+
+def oracle_solves():
+    """The oracle's even-odd BiCGStab, as it stands, on two whole systems: the
+    8^4 Wilson workload (kappa 0.12, tol 1e-12) and a 16^4 clover system
+    (kappa 0.125, c_sw 1, links exp(0.2 i A), tol 1e-10); one process."""
+    import synth
+    from oracle import evenodd, solvers
+    from oracle.lattice import Lattice
+
+    out = {}
+    for name, dims, kappa, csw, eps, seed, tol in [("wilson_8x8x8x8", (8, 8, 8, 8), 0.12, 0.0, 0.3, 1, 1e-12),
+                                                    ("clover_16x16x16x16", (16, 16, 16, 16), 0.125, 1.0, 0.2, 2, 1e-10)]:
+        lat = Lattice(dims)
+        U = synth.gauge_field(dims, eps, seed)
+        b = synth.gaussian_spinor(dims, seed)
+        t0 = time.perf_counter()
+        eo = evenodd.EvenOdd(U, lat, kappa, csw)
+        xe, info = solvers.bicgstab(eo.schur, eo.prepare(b), tol=tol)
+        x = eo.reconstruct(xe, b)
+        secs = time.perf_counter() - t0
+        out[name] = {"seconds": secs, "iterations": info["iters"], "true_rel_residual": info["true_rel_residual"],
+                     "cores": 1, "includes": "clover term setup, preparation, BiCGStab, reconstruction"}
+        del x
+    return out
 
 
 def alu_peaks(api):

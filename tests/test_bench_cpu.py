@@ -28,3 +28,17 @@ def test_reference_arm_prints_contract_line(workload):
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == workload
+
+
+def test_oracle_sample_on_all_cores_matches_work():
+    """The all-cores oracle baseline: the sampled sites split over spawned
+    workers reading the fields from shared memory; every site is computed."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+
+    w = synth.WORKLOADS["wilson_8x8x8x8"]
+    U = w.gauge()
+    b = synth.gaussian_spinor(w.dims, 1)
+    v, secs, procs = bench.oracle_sample_pool(w, U, b, 1024, seed=3, procs=2)
+    assert procs == 2 and secs > 0 and v == pytest.approx(1024 * bench.FP64_D_BYTES_PER_SITE / secs / 1e9)
