@@ -314,17 +314,31 @@ def serving_sample(api, n_requests, main_lattice, main_U, seed=5, rate_factor=0.
     results = []
 
     def collect():
-        # wait for requests in submission order and release them at once, so
-        # finished results do not pile up in host memory
-        while True:
-            item = pending.get()
-            if item is None:
-                return
-            h, nr, size = item
-            st, _, info = api.bridge_wait(h, want_x=False)
-            cg = any(i["cgnr_passes"] > 0 for i in info)
-            results.append((st, nr, size, api.bridge_request_times(h), cg))
-            api.bridge_request_release(h)
+        # release requests in the order they finish (a finished request holds
+        # its result on the host until it is released), polling without a wait
+        live, more = [], True
+        while more or live:
+            try:
+                while True:
+                    item = pending.get_nowait()
+                    if item is None:
+                        more = False
+                        break
+                    live.append(item)
+            except queue.Empty:
+                pass
+            still = []
+            for h, nr, size in live:
+                r = api.bridge_wait(h, 0, want_x=False)
+                if r is None:
+                    still.append((h, nr, size))
+                    continue
+                st, _, info = r
+                cg = any(i["cgnr_passes"] > 0 for i in info)
+                results.append((st, nr, size, api.bridge_request_times(h), cg))
+                api.bridge_request_release(h)
+            live = still
+            time.sleep(0.001)
 
     waiter = threading.Thread(target=collect)
     waiter.start()
