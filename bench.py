@@ -1475,6 +1475,76 @@ def run_mg(args):
         dist.destroy_process_group()
 
 
+def run_dd(args):
+    """The decomposed Schur operator (slabs along t joined by a halo exchange)
+    against the single-lattice one on the 32^3 x 64 clover workload, through
+    the device-pointer entry points (canonical FP64 in and out, so the layout
+    conversions are inside both timings), for 1, 2, 4 and 8 slabs; and the
+    decomposed FP64 BiCGStab solve beside the plain FP64 one."""
+    import torch
+
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+
+    g.build()
+    import synth
+    from paper_2303_05883_gb300 import _abi, api
+
+    w = synth.WORKLOADS["clover_32x32x32x64"]
+    op = api.make_op("clover", w.kappa, w.csw, w.bc)
+    L = api.Lattice(w.dims)
+    L.upload(w.gauge(), op)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    xe = torch.randn((w.volume // 2, 4, 3), dtype=torch.complex128, device="cuda", generator=gen)
+    reps = max(3, args.steps)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t0) / reps
+
+    out = {"plain": {}}
+    for prec in ("f32", "f16"):
+        out["plain"][prec] = timed(lambda: L.Dhat(op, xe, prec))
+    ref = L.Dhat(op, xe, "f32")
+    for n in (1, 2, 4, 8):
+        dd = api.Decomposition(L, op, n)
+        e = {prec: timed(lambda: dd.Dhat(xe, prec)) for prec in ("f32", "f16")}
+        got = dd.Dhat(xe, "f32")
+        e["rel_diff_f32"] = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
+        out[f"slabs_{n}"] = e
+        dd.close()
+    b = torch.from_numpy(w.sources()[0]).cuda()
+    s64 = api.make_solver(tol=w.tol, mixed=0)
+    t0 = time.perf_counter()
+    _, info = L.solve(op, b, s64)
+    t_plain = time.perf_counter() - t0
+    dd = api.Decomposition(L, op, 4)
+    t0 = time.perf_counter()
+    _, dinfo = dd.solve(b, api.make_solver(tol=w.tol))
+    t_dd = time.perf_counter() - t0
+    dd.close()
+    L.close()
+    line = {
+        "metric": "decomposed Schur operator and FP64 solve time (halo exchange between slabs on one GPU)",
+        "value": out["slabs_4"]["f32"], "unit": "ms per D^ application (4 slabs, f32, canonical FP64 in/out)",
+        "n_gpus": 1, "steps": reps, "warmup": 2, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 / f16 storage, f32 math; f64 solve", "data": "synthetic",
+        "config": {"workload": "dd_clover_32x32x32x64", "lattice": "x".join(map(str, w.dims)),
+                   "decomposition": "slabs along t", "transport": "device-to-device copies on one GPU"},
+        "dhat_ms": out,
+        "fp64_solve": {"plain_s": t_plain, "plain_iters": info[0]["inner_iters"],
+                       "decomposed_4_slabs_s": t_dd, "decomposed_iters": dinfo[0]["inner_iters"],
+                       "decomposed_true_rel_residual": dinfo[0]["true_rel_residual"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args):
     """The request stream alone: lattices {8^4, 16^4, 24^3x48, 32^3x64},
     kappa in [0.11, 0.13], 1-12 right-hand sides, Wilson or clover."""
@@ -1526,6 +1596,8 @@ def main():
         run_staggered(args)
     elif args.workload.startswith("mg_"):
         run_mg(args)
+    elif args.workload.startswith("dd_"):
+        run_dd(args)
     else:
         run_ours(args)
 
