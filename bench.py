@@ -985,7 +985,11 @@ def run_mobius(args):
     nrhs = w.nrhs
     api.bridge_tune(h, op, "f32", nrhs)
     if args.deo_only:
-        print(json.dumps({"workload": args.workload, "deo": mobius_operator_leg(api, h, op, w, b_dev, stream),
+        torch.cuda.nvtx.range_push("operator_legs")
+        leg = mobius_operator_leg(api, h, op, w, b_dev, stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"workload": args.workload, "deo": leg,
                           "launch_shapes": {k: {"threads": v[0], "variant": v[2]}
                                             for k, v in api.bridge_tune_table(h).items() if k.startswith("dwf")}}),
               flush=True)
@@ -1188,7 +1192,11 @@ def run_staggered(args):
     solver = api.make_solver(tol=w.tol, inner_prec=w.inner, mixed=1)
     peak, peak_kind = peaks()
     if args.deo_only:
-        print(json.dumps({"workload": args.workload, "deo": staggered_operator_leg(api, h, op, w, b_dev)}), flush=True)
+        torch.cuda.nvtx.range_push("operator_legs")
+        leg = staggered_operator_leg(api, h, op, w, b_dev)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"workload": args.workload, "deo": leg}), flush=True)
         L.close()
         return
 
