@@ -794,10 +794,11 @@ extern "C" int bridge_dd_solve_dev(bridge_dd d, const bridge_solver* prm, const 
       alpha = zdivd(rho, rv);
       lincomb(d, vs, {{one, vr}, {cx<double>{-alpha.r, -alpha.i}, vv}});
       dd_dhat(d, P_F64, t, sv, TO);
-      cx<double> ts;
+      // omega = <t, s> / |t|^2: dots(a, b) gives <a, b> and |b|^2, so take <s, t> and conjugate
+      cx<double> st;
       double tt;
-      dots(d, vt, vs, ts, tt);
-      omega = tt > 0 ? cx<double>{ts.r / tt, ts.i / tt} : zero;
+      dots(d, vs, vt, st, tt);
+      omega = tt > 0 ? cx<double>{st.r / tt, -st.i / tt} : zero;
       lincomb(d, vx, {{one, vx}, {alpha, vp_}, {omega, vs}});
       lincomb(d, vr, {{one, vs}, {cx<double>{-omega.r, -omega.i}, vt}});
       cx<double> rho_new;
