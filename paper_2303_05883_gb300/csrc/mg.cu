@@ -112,6 +112,7 @@ struct bridge_mg_s {
   int last_coarse_iters = 0;  // iterations of the previous coarse solve (sizes the first batch)
   Field r32, x32, res32;  // fine FP32 work fields of the cycle
   int sap_clover_smem = 1;  // SAP kernel variant (picked by timing at setup)
+  bool sap_fused = true;    // residual formed inside the SAP sweep (BRIDGE_MG_SAP_FUSED=0: separate pass)
   // half-lattice sites of parity p in blocks of colour c: smap[soff[p][c] .. + sn[p][c])
   std::unique_ptr<DevBuf> smap;
   long soff[2][2] = {{0, 0}, {0, 0}}, sn[2][2] = {{0, 0}, {0, 0}};
@@ -496,13 +497,17 @@ void allow_sap_smem(long smem) {
   done[dev] = smem;
 }
 
-void sap_half_sweep(bridge_mg_s* g, const Field& r, const Field& x, int colour) {
+// fused: r is the right-hand side b and each block forms b - D x itself;
+// otherwise r is the residual at the colour's sites.
+void sap_half_sweep(bridge_mg_s* g, const Field& r, const Field& x, int colour, bool fused = false) {
   MgSapArgs a;
   std::memset(static_cast<void*>(&a), 0, sizeof(a));
   a.m = g->m;
   a.colour = colour;
   a.steps = g->prm.mr_steps;
   a.kappa = (float)g->op.kappa;
+  a.fused = fused ? 1 : 0;
+  for (int k = 0; k < 4; ++k) a.bcf[k] = (float)g->op.bc[k];
   a.r = r.ptr(0);
   a.x = x.ptr(0);
   a.field_block = r.block;
@@ -518,8 +523,17 @@ void sap_half_sweep(bridge_mg_s* g, const Field& r, const Field& x, int colour) 
   // r, x in and out, the clover term, and the forward links of the hops that stay in the block
   double inner = 0;
   for (int k = 0; k < 4; ++k) inner += (double)(g->m.b[k] - 1) / g->m.b[k];
-  const double bytes = sites * (96 + 2 * 96 + 288 + 48 * inner);
-  note_launch(g->L, K_MG_SAP, bytes, sites * g->prm.mr_steps * 1900.0, stream_of(g), true);
+  double bytes = sites * (96 + 2 * 96 + 288 + 48 * inner);
+  double flops = sites * g->prm.mr_steps * 1900.0;
+  if (fused) {
+    // the residual adds the forward links the block's own hops skip, the backward links across the
+    // block faces and x at the neighbours in the other colour's blocks
+    double faces = 0;
+    for (int k = 0; k < 4; ++k) faces += 1.0 / g->m.b[k];
+    bytes += sites * (48 * (4 - inner) + 48 * faces + 96 * 2 * faces);
+    flops += sites * hop_cost(P_F32, F_AUX | F_SELF | F_SELF_CLOV, R_NONE).rhs_flops;
+  }
+  note_launch(g->L, K_MG_SAP, bytes, flops, stream_of(g), true);
   if (cs)
     mg_sap_kernel<true><<<g->m.nblocks / 2, block_threads(g), (size_t)smem, stream_of(g)>>>(a);
   else
@@ -571,6 +585,8 @@ void sap(bridge_mg_s* g, const Field& r, const Field& x, int cycles, bool x_zero
     for (int colour = 0; colour < 2; ++colour) {
       if (cyc == 0 && colour == 0 && x_zero) {
         sap_half_sweep(g, r, x, colour);  // residual = r while x = 0
+      } else if (g->sap_fused) {
+        sap_half_sweep(g, r, x, colour, true);
       } else {
         fine_residual32(g, r, x, g->res32, colour);
         sap_half_sweep(g, g->res32, x, colour);
@@ -793,6 +809,7 @@ int bridge::mg_setup(bridge_lattice_s* L, const bridge_op& op, const bridge_mg_p
     BR_CUDA(cudaStreamSynchronize(st));
   }
   pick_sap_variant(g.get());
+  if (const char* e = std::getenv("BRIDGE_MG_SAP_FUSED")) g->sap_fused = e[0] != '0';
   *out = g.release();
   return BRIDGE_OK;
 }

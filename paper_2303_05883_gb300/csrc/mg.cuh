@@ -749,12 +749,26 @@ struct MgSapArgs {
   MgGeom m;
   int colour, steps;
   float kappa;
-  const char* r;  // full FP32 field (the current residual)
+  const char* r;  // full FP32 field: the current residual, or with `fused` the right-hand side
   char* x;        // full FP32 field, updated
   long field_block;
   const char* gauge;
   const char* clov;
+  int fused;      // 1: the block residual r - D x is formed at the start of the sweep
+  float bcf[4];   // boundary phases (fused residual)
 };
+
+// The two hops of direction MU of the full operator at one site (x of the
+// opposite parity in `in`), added to acc: the fused residual of the SAP sweep.
+template <int MU>
+BR_D void mg_sap_hops(const MgSapArgs& a, const char* in, const char* g_out, const char* g_in, long lbb, uint32_t ih,
+                      const int c[4], cx<float> acc[12]) {
+  uint32_t f, b;
+  bool wf, wb;
+  neighbours<MU>(a.m.g, ih, c, (uint32_t)c[0] >> 1, f, b, wf, wb);
+  hop_one<P_F32, MU, true, false>(in, g_out + MU * lbb, a.m.g.vh, f, ih, wf, a.bcf[MU], acc);
+  hop_one<P_F32, MU, false, false>(in, g_in + MU * lbb, a.m.g.vh, b, b, wb, a.bcf[MU], acc);
+}
 
 // Dynamic shared memory of mg_sap_kernel: rho, the 4 forward links (all 18
 // reals) and, with CS, the clover term (72 reals) of every site of the block.
@@ -762,7 +776,11 @@ BR_HD long mg_sap_smem(int bsites, bool cs) { return (long)bsites * (12 * 8 + 4 
 
 // One SAP half sweep: every block of one colour solves D_B e = r_B by
 // `steps` MR steps from e = 0 and adds e to x.  One CTA per block, one
-// thread per site.  The links of the block are staged in shared memory once,
+// thread per site.  With `fused` the kernel first forms the residual
+// r_B = b - D x at its own sites (full operator, all eight hops): x inside
+// the block is changed only by this CTA, after that, and every site outside
+// the block that a hop reaches belongs to a block of the other colour, which
+// this sweep does not touch -- so no separate residual pass is needed.  The links of the block are staged in shared memory once,
 // so the MR steps read them there: a hop inside the block in -mu uses
 // U_mu(x - mu), the forward link of the neighbour site.  CS: the clover term
 // is staged as well (up to 168 KB, one CTA per SM); otherwise each step
@@ -796,12 +814,29 @@ __global__ void __launch_bounds__(256, CS ? 1 : 2) mg_sap_kernel(const MgSapArgs
     }
     cx<float> rr[12];
     load_spinor<P_F32>(a.r + p * a.field_block, vh, ih, rr);
+    const char* g_out = a.gauge + (long)p * 4 * lbb;
+    if (a.fused) {
+      // rr = b - T x + kappa H x at this site
+      const char* xin = a.x + (1 - p) * a.field_block;
+      const char* g_in = a.gauge + (long)(1 - p) * 4 * lbb;
+      cx<float> hx[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) hx[k] = czero<float>();
+      mg_sap_hops<0>(a, xin, g_out, g_in, lbb, ih, c, hx);
+      mg_sap_hops<1>(a, xin, g_out, g_in, lbb, ih, c, hx);
+      mg_sap_hops<2>(a, xin, g_out, g_in, lbb, ih, c, hx);
+      mg_sap_hops<3>(a, xin, g_out, g_in, lbb, ih, c, hx);
+      cx<float> xs[12], tx[12];
+      load_spinor<P_F32>(a.x + p * a.field_block, vh, ih, xs);
+      clover_apply<P_F32>(a.clov + p * clover_block_bytes(P_F32, vh), vh, ih, xs, tx);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) rr[k] = caxpy(a.kappa, hx[k], rr[k] - tx[k]);
+    }
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       rho[k * nsite + j] = rr[k];
       e[k] = czero<float>();
     }
-    const char* g_out = a.gauge + (long)p * 4 * lbb;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       if (nbf[mu] < 0) continue;  // no hop of the block uses it

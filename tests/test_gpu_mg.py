@@ -183,6 +183,34 @@ def test_sap_smoother(api, case):
     assert rel(mg.apply(_abi.BRIDGE_MG_SAP, r), orc.sap(r, 2, 4)) < TOL32
 
 
+@pytest.mark.parametrize("fused", ["1", "0"])
+def test_sap_residual_inside_sweep_or_separate(api, monkeypatch, fused):
+    """The SAP sweep with the block residual r - D x formed inside the sweep
+    kernel (default) and with the separate residual pass, on 4x2x2x2 blocks
+    with a negative phase in y and t, against the oracle's smoother (three
+    cycles: every half sweep after the first forms its residual from a
+    nonzero x)."""
+    from paper_2303_05883_gb300 import _abi
+
+    dims, block, nv, kappa, csw, bc = (8, 4, 4, 8), (4, 2, 2, 2), 2, 0.115, 1.0, (1, -1, 1, -1)
+    lat = Lattice(dims)
+    U = synth.gauge_field(dims, 0.35, 77)
+    gen = np.random.default_rng(78)
+    vs = gen.standard_normal((nv, lat.V, 4, 3)) + 1j * gen.standard_normal((nv, lat.V, 4, 3))
+    orc = multigrid.Multigrid(U, lat, kappa, csw, block, vs, bc=bc)
+    op = api.make_op("clover", kappa, csw, bc)
+    L = api.Lattice(dims)
+    L.upload(U, op)
+    monkeypatch.setenv("BRIDGE_MG_SAP_FUSED", fused)
+    mg = api.Multigrid(L, op, api.make_mg_params(block=block, nvec=nv, sap_cycles=3, mr_steps=5, coarse_half=0),
+                       null_vectors=vs)
+    monkeypatch.delenv("BRIDGE_MG_SAP_FUSED")
+    r = gen.standard_normal((lat.V, 4, 3)) + 1j * gen.standard_normal((lat.V, 4, 3))
+    assert rel(mg.apply(_abi.BRIDGE_MG_SAP, r), orc.sap(r, 3, 5)) < TOL32
+    mg.close()
+    L.close()
+
+
 def test_cycle(api, case):
     """The preconditioner with a tight coarse tolerance against the oracle's
     cycle with a tight coarse BiCGStab."""
