@@ -330,10 +330,12 @@ int bridge_tune(bridge_lattice lat, const bridge_op* op, int prec, int nrhs);
 int bridge_tune_table(bridge_lattice lat, char* out, int n);
 /* Set one entry of the shape table (key as printed by bridge_tune_table):
  * block in [64, 256] (multiple of 32), nblk >= 1 site blocks per
- * right-hand-side group, variant in [0, 8] (register budget / read-once
- * loads for 0-5, 2-4 right-hand sides per thread for 6-8; a variant a
- * kernel does not have falls back to 0).  Lets tests and users pin a launch
- * shape; EINVAL for values out of range. */
+ * right-hand-side group, variant in [0, 12] (register budget / read-once
+ * loads for 0-5, 2-4 right-hand sides per thread for 6-8, the shared-link
+ * tile kernel for 9-10, the same with pipelined neighbour loads for 11-12,
+ * FP16/BF16 storage only; a variant a kernel does not have falls back to
+ * 0).  Lets tests and users pin a launch shape; EINVAL for values out of
+ * range. */
 int bridge_tune_set(bridge_lattice lat, const char* key, int block, int nblk, int variant);
 
 /* ---- fields in the GPU layout (resident data) ------------------------------- */
@@ -442,6 +444,13 @@ int bridge_engine_config(size_t memory_budget_bytes, int max_active);
  * larger than the whole budget). */
 int bridge_submit(bridge_lattice lat, const bridge_op* op, const bridge_solver* s, const double* b, int nrhs,
                   bridge_request_h* out);
+/* As bridge_submit, but b is borrowed, not copied: the caller keeps it valid
+ * and unchanged until the request has finished (bridge_poll / bridge_wait
+ * returned its final status) or has been released (bridge_request_release
+ * returns only once a borrowed b is no longer read).  A queue of waiting
+ * requests then holds no host copies of its right-hand sides. */
+int bridge_submit_borrowed(bridge_lattice lat, const bridge_op* op, const bridge_solver* s, const double* b,
+                           int nrhs, bridge_request_h* out);
 /* PENDING while running; else the request's final status, with x_out
  * (nrhs*V*24 doubles, may be NULL) and info[nrhs] (may be NULL) filled. */
 int bridge_poll(bridge_request_h h, double* x_out, bridge_info* info);

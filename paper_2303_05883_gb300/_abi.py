@@ -140,6 +140,7 @@ SIGNATURES = {
     "bridge_apply": (c_int, [_h, POINTER(bridge_op), c_int, _h, _h]),
     "bridge_engine_config": (c_int, [c_size_t, c_int]),
     "bridge_submit": (c_int, [_h, POINTER(bridge_op), POINTER(bridge_solver), _dp, c_int, POINTER(_h)]),
+    "bridge_submit_borrowed": (c_int, [_h, POINTER(bridge_op), POINTER(bridge_solver), _dp, c_int, POINTER(_h)]),
     "bridge_mg_defaults": (None, [POINTER(bridge_mg_params)]),
     "bridge_mg_setup": (c_int, [_h, POINTER(bridge_op), POINTER(bridge_mg_params), _dp, POINTER(_h)]),
     "bridge_mg_destroy": (c_int, [_h]),

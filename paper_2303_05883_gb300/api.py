@@ -255,12 +255,16 @@ class Request:
     _b: np.ndarray = field(repr=False, default=None)
 
 
-def bridge_submit(lat, op, solver, b) -> Request:
+def bridge_submit(lat, op, solver, b, borrow=False) -> Request:
+    """Queue a solve.  borrow=True: the library reads b in place at admission
+    (no host copy); the returned Request keeps the array alive."""
     bb = _host(b)
     nrhs = 1 if bb.ndim == 3 else bb.shape[0]
     h = c_void_p()
-    check(_abi.load().bridge_submit(lat, byref(op), byref(solver), _dptr(bb), nrhs, byref(h)), "bridge_submit")
-    return Request(h.value, bb.shape, nrhs)  # the library keeps its own copy of b
+    fn = _abi.load().bridge_submit_borrowed if borrow else _abi.load().bridge_submit
+    check(fn(lat, byref(op), byref(solver), _dptr(bb), nrhs, byref(h)), "bridge_submit")
+    # without borrow the library keeps its own copy of b
+    return Request(h.value, bb.shape, nrhs, bb if borrow else None)
 
 
 def bridge_poll(req: Request):

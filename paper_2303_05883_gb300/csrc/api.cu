@@ -19,7 +19,7 @@ extern std::atomic<long> g_launches;
 extern std::atomic<long> g_dev_allocs;
 void tune_cache_load(bridge_lattice_s* L);
 int engine_submit(bridge_lattice_s* L, const bridge_op& op, const bridge_solver& s, const double* b, int nrhs,
-                  bridge_request_h* out);
+                  bool borrow, bridge_request_h* out);
 
 Field& workspace(bridge_lattice_s* L, const std::string& name, int prec, int subset, int nrhs) {
   const std::string key = name + "/" + std::to_string(prec) + "/" + std::to_string(subset) + "/" + std::to_string(nrhs);
@@ -604,8 +604,8 @@ int bridge_debug_neighbours(const int dims[4], int parity, long ih, long out[8],
   BR_API_END
 }
 
-int bridge_submit(bridge_lattice L, const bridge_op* op, const bridge_solver* s, const double* b, int nrhs,
-                  bridge_request_h* out) {
+static int submit(bridge_lattice L, const bridge_op* op, const bridge_solver* s, const double* b, int nrhs,
+                  bool borrow, bridge_request_h* out) {
   BR_API_BEGIN
   check_lat(L, true);
   check_op(op);
@@ -615,8 +615,18 @@ int bridge_submit(bridge_lattice L, const bridge_op* op, const bridge_solver* s,
   BR_CHECK(s->tol > 0, BRIDGE_EINVAL, "tol must be > 0");
   if (s->mixed) check_prec(s->inner_prec);
   BR_CHECK(nrhs >= 1, BRIDGE_EINVAL, "nrhs must be >= 1");
-  return engine_submit(L, *op, *s, b, nrhs, out);
+  return engine_submit(L, *op, *s, b, nrhs, borrow, out);
   BR_API_END
+}
+
+int bridge_submit(bridge_lattice L, const bridge_op* op, const bridge_solver* s, const double* b, int nrhs,
+                  bridge_request_h* out) {
+  return submit(L, op, s, b, nrhs, false, out);
+}
+
+int bridge_submit_borrowed(bridge_lattice L, const bridge_op* op, const bridge_solver* s, const double* b, int nrhs,
+                           bridge_request_h* out) {
+  return submit(L, op, s, b, nrhs, true, out);
 }
 
 }  // extern "C"

@@ -48,6 +48,7 @@ struct bridge_request_s {
   size_t bytes = 0;
   size_t nvals = 0;  // doubles per field (nrhs * V * 24)
   std::vector<double> b_host;
+  const double* b_ref = nullptr;  // borrowed b (bridge_submit_borrowed): the caller's buffer, not copied
   // set by the engine thread
   int state = RQ_QUEUED;
   std::atomic<int> phase{PH_UPLOAD};
@@ -108,7 +109,9 @@ struct Engine {
       }
       const size_t n = r->nvals * sizeof(double);
       if (r->phase.load() == PH_UPLOAD) {
-        cudaError_t e = cudaMemcpyAsync(r->b_dev->ptr, r->b_host.data(), n, cudaMemcpyHostToDevice, r->st);
+        const double* src = r->b_ref ? r->b_ref : r->b_host.data();
+        cudaError_t e = cudaMemcpyAsync(r->b_dev->ptr, src, n, cudaMemcpyHostToDevice, r->st);
+        if (e == cudaSuccess && r->b_ref) e = cudaStreamSynchronize(r->st);  // the caller may reuse b after this
         if (e != cudaSuccess) {
           cudaGetLastError();
           r->error = std::string("upload: ") + cudaGetErrorString(e);
@@ -276,7 +279,7 @@ Engine& engine() {
 
 namespace bridge {
 int engine_submit(bridge_lattice_s* L, const bridge_op& op, const bridge_solver& s, const double* b, int nrhs,
-                  bridge_request_h* out) {
+                  bool borrow, bridge_request_h* out) {
   Engine& E = engine();
   auto* r = new bridge_request_s();
   r->L = L;
@@ -285,7 +288,10 @@ int engine_submit(bridge_lattice_s* L, const bridge_op& op, const bridge_solver&
   r->nrhs = nrhs;
   r->nvals = (size_t)nrhs * L->V * 24;
   r->bytes = solve_footprint(L, s, nrhs);
-  r->b_host.assign(b, b + r->nvals);
+  if (borrow)
+    r->b_ref = b;
+  else
+    r->b_host.assign(b, b + r->nvals);
   r->t_submit = now_seconds();
   std::lock_guard<std::mutex> lk(E.mu);
   E.start(L->device);
@@ -341,7 +347,13 @@ int bridge_wait(bridge_request_h h, int timeout_ms, double* x_out, bridge_info* 
 int bridge_request_release(bridge_request_h h) {
   if (!h) return BRIDGE_OK;
   Engine& E = engine();
-  std::lock_guard<std::mutex> lk(E.mu);
+  std::unique_lock<std::mutex> lk(E.mu);
+  // a borrowed b may still be read by the upload of an admitted request: let that finish first
+  while (h->b_ref && h->state == RQ_ACTIVE && h->phase.load() == PH_UPLOAD) {
+    lk.unlock();
+    std::this_thread::sleep_for(std::chrono::microseconds(100));
+    lk.lock();
+  }
   if (h->state == RQ_QUEUED) {
     auto it = std::find(E.queue.begin(), E.queue.end(), h);
     if (it != E.queue.end()) E.queue.erase(it);

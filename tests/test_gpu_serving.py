@@ -168,6 +168,37 @@ def test_wait_timeout_and_release_of_running_request(api, lattices):
     assert st == 0
 
 
+def test_borrowed_rhs_equals_copied_and_release_while_queued(api, lattices):
+    """A borrowed b (read in place at admission) gives the bit-identical result
+    of a copied one.  Borrowed requests released at once -- queued ones
+    withdrawn, admitted ones cancelled after their upload -- leave the engine
+    serving, and their arrays can then be freed."""
+    L, _ = lattices[(8, 8, 8, 8)]
+    op = api.make_op("clover", 0.12, 1.0)
+    s = api.make_solver(tol=1e-10)
+    b = synth.gaussian_spinor((8, 8, 8, 8), 31, nrhs=3)
+    h1 = api.bridge_submit(L.handle, op, s, b)
+    h2 = api.bridge_submit(L.handle, op, s, b.copy(), borrow=True)
+    st1, x1, _ = api.bridge_wait(h1, timeout_ms=60000)
+    st2, x2, _ = api.bridge_wait(h2, timeout_ms=60000)
+    api.bridge_request_release(h1)
+    api.bridge_request_release(h2)
+    assert st1 == 0 and st2 == 0 and np.array_equal(x1, x2)
+    api.bridge_engine_config(budget_bytes=64 << 30, max_active=2)
+    try:
+        hs = [api.bridge_submit(L.handle, op, s, synth.gaussian_spinor((8, 8, 8, 8), 40 + i, nrhs=2), borrow=True)
+              for i in range(12)]
+        for h in hs:
+            api.bridge_request_release(h)
+        del hs
+        h = api.bridge_submit(L.handle, op, s, b, borrow=True)
+        st, x, _ = api.bridge_wait(h, timeout_ms=60000)
+        api.bridge_request_release(h)
+        assert st == 0 and np.array_equal(x, x1)
+    finally:
+        api.bridge_engine_config(budget_bytes=64 << 30, max_active=16)
+
+
 def test_gauge_reupload_refused_while_requests_run(api):
     from paper_2303_05883_gb300 import _abi
 
