@@ -486,9 +486,11 @@ bool launch_hop<P_BF16>(int flags, int red, const HopArgs& a, int block, cudaStr
 bool hop_has_variants(int flags, int red);
 // Right-hand sides covered by one block group of a variant: 1 for v < 6, NR
 // for the NR-per-thread kernels (v = 6, 7, 8) and up to 12 for the
-// shared-link tile kernels (v = 9, 10; dslash_tile.cuh).
+// shared-link tile kernels (v = 9, 10; with pipelined neighbour loads, 16-bit
+// storage only, v = 11, 12; dslash_tile.cuh).
 inline int hop_variant_rpt(int variant) { return variant >= 9 ? 12 : variant >= 6 ? variant - 4 : 1; }
-constexpr int HOP_NVARIANT = 11;
+constexpr int HOP_NVARIANT = 13;
+inline bool hop_variant_for_prec(int variant, int prec) { return variant < 11 || prec == P_F16 || prec == P_BF16; }
 inline bool hop_variant_is_tile(int variant) { return variant >= 9; }
 
 }  // namespace bridge

@@ -26,12 +26,17 @@ namespace bridge {
 
 constexpr int TILE_SITES = 32;
 constexpr int TILE_MAX_RHS = 12;
+constexpr int TILE_THREADS = 32 * TILE_MAX_RHS;
 // Staged per chunk of S = NT x 32 sites (NT tiles between two barriers), in
 // float4 units: links [8 hops][5][S] (nine complex entries in five float4),
 // clover [2 blocks][9][S], then the neighbour indices [8][S] as uint32.
-BR_HD size_t tile_smem_bytes(bool clov, int nt) {
+// With pipelined neighbour loads (pf) each thread also owns two slots of
+// four uint4 (three for the 16-bit spinor, one for its scale):
+// [2 stages][4][TILE_THREADS] uint4.
+BR_HD size_t tile_smem_bytes(bool clov, int nt, bool pf = false) {
   const int S = nt * TILE_SITES;
-  return (size_t)(8 * 5 * S + (clov ? 2 * 9 * S : 0)) * 16 + (size_t)8 * S * 4;
+  return (size_t)(8 * 5 * S + (clov ? 2 * 9 * S : 0)) * 16 + (size_t)8 * S * 4 +
+         (pf ? (size_t)2 * 4 * TILE_THREADS * 16 : 0);
 }
 // Right-hand sides per block for nrhs (groups of equal size, at most TILE_MAX_RHS).
 BR_HD int tile_groups(int nrhs) { return (nrhs + TILE_MAX_RHS - 1) / TILE_MAX_RHS; }
@@ -167,16 +172,104 @@ BR_D void tile_hop(const char* in, long vh, const float4* sl, const uint32_t* sn
     reconstruct<float, MU, FWD>(u, acc);
 }
 
+// Pipelined neighbour loads (16-bit storage): the neighbour spinor and scale
+// of the next hop are copied into the thread's own shared-memory slot by
+// cp.async while the current hop computes, so the load latency is hidden
+// without holding the next hop's data in registers.  Each thread reads only
+// the slot it filled itself, after waiting for its own copies: no barrier.
+BR_D void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+BR_D void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+BR_D void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+BR_D void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Slot k (0..2 spinor planes, 3 scale) of stage st of thread t.
+BR_D uint4* tile_pf_slot(uint4* pf, int st, int k, int t) { return pf + (st * 4 + k) * TILE_THREADS + t; }
+
+// Start the copy of the neighbour of hop H (16-bit spinor: three uint4 planes and the scale).
+template <int H, int S>
+BR_D void tile_fetch(const char* in, long vh, const uint32_t* snb, int s, uint4* pf, int t) {
+  const uint32_t nb = snb[H * S + s];
+  const uint4* pl = reinterpret_cast<const uint4*>(in);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    cp_async16((uint32_t)__cvta_generic_to_shared(tile_pf_slot(pf, H & 1, k, t)), pl + k * vh + nb);
+  cp_async4((uint32_t)__cvta_generic_to_shared(tile_pf_slot(pf, H & 1, 3, t)),
+            reinterpret_cast<const float*>(in + 48 * vh) + nb);
+  cp_async_commit();
+}
+
+// Hop H from the staged neighbour: projection, link product, reconstruction.
+template <int P, int H, int S>
+BR_D void tile_hop_staged(const float4* sl, int s, const uint4* pf, int t, cx<float> acc[12]) {
+  constexpr int MU = H / 2;
+  constexpr bool FWD = (H & 1) == 0;
+  const uint4 v0 = *tile_pf_slot(const_cast<uint4*>(pf), H & 1, 0, t);
+  const uint4 v1 = *tile_pf_slot(const_cast<uint4*>(pf), H & 1, 1, t);
+  const uint4 v2 = *tile_pf_slot(const_cast<uint4*>(pf), H & 1, 2, t);
+  const float sc = __uint_as_float(tile_pf_slot(const_cast<uint4*>(pf), H & 1, 3, t)->x);
+  cx<float> hh[2][3];
+  if constexpr (P == P_F16) {
+    const uint32_t w[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
+    project_f16<MU, FWD>(w, hh);
+  } else {
+    H16<P> h;
+    const uint32_t w[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
+    cx<float> psi[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const float2 f = h.to2(w[k]);
+      psi[k] = {f.x, f.y};
+    }
+    project<float, MU, FWD>(psi, hh);
+  }
+  const float4* q = sl + H * 5 * S + s;
+  const float4 q0 = q[0], q1 = q[S], q2 = q[2 * S], q3 = q[3 * S], q4 = q[4 * S];
+  const cx<float> m00 = {q0.x, q0.y}, m01 = {q0.z, q0.w}, m02 = {q1.x, q1.y};
+  const cx<float> m10 = {q1.z, q1.w}, m11 = {q2.x, q2.y}, m12 = {q2.z, q2.w};
+  const cx<float> m20 = {q3.x, q3.y}, m21 = {q3.z, q3.w}, m22 = {q4.x, q4.y};
+  cx<float> u[2][3];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    u[k][0] = crow3(m00, m01, m02, hh[k]);
+    u[k][1] = crow3(m10, m11, m12, hh[k]);
+    u[k][2] = crow3(m20, m21, m22, hh[k]);
+  }
+  reconstruct_scaled<MU, FWD>(u, sc, acc);
+}
+
+// One pipeline step: start hop H + 1's copy, wait for hop H's, compute hop H.
+template <int P, int H, int S>
+BR_D void tile_pf_step(const char* in, long vh, const float4* sl, const uint32_t* snb, int s, uint4* pf, int t,
+                       cx<float> acc[12]) {
+  if constexpr (H < 7) {
+    tile_fetch<H + 1, S>(in, vh, snb, s, pf, t);
+    cp_async_wait<1>();
+  } else {
+    cp_async_wait<0>();
+  }
+  tile_hop_staged<P, H, S>(sl, s, pf, t, acc);
+}
+
 // NT tiles (NT x 32 sites) are staged between two barriers; the register
-// budget allows two resident 384-thread blocks per SM.
-template <int P, int FL, int RED, int NT>
+// budget allows two resident 384-thread blocks per SM.  PF: pipelined
+// neighbour loads (16-bit storage only).
+template <int P, int FL, int RED, int NT, bool PF = false>
 __global__ void __launch_bounds__(32 * TILE_MAX_RHS, 2) hop_kernel_tile(const HopArgs a) {
+  static_assert(!PF || Tr<P>::half, "pipelined neighbour loads: 16-bit storage");
   static_assert(P != P_F64, "FP32 arithmetic kernels only");
   constexpr int S = NT * TILE_SITES;
   extern __shared__ float4 tile_smem[];
   float4* sl = tile_smem;
   float4* sc_clov = tile_smem + 8 * 5 * S;
   uint32_t* snb = reinterpret_cast<uint32_t*>(tile_smem + 8 * 5 * S + ((FL & F_E_CLOV) ? 2 * 9 * S : 0));
+  uint4* pf = reinterpret_cast<uint4*>(snb + 8 * S);  // PF slots
   const int ng = tile_groups(a.nrhs), G = tile_group_size(a.nrhs);
   const int grp = blockIdx.x % ng;
   const int sb = blockIdx.x / ng;
@@ -231,14 +324,27 @@ __global__ void __launch_bounds__(32 * TILE_MAX_RHS, 2) hop_kernel_tile(const Ho
       cx<float> acc[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = czero<float>();
-      tile_hop<P, 0, true, S>(in, vh, sl, snb, s, acc);
-      tile_hop<P, 0, false, S>(in, vh, sl, snb, s, acc);
-      tile_hop<P, 1, true, S>(in, vh, sl, snb, s, acc);
-      tile_hop<P, 1, false, S>(in, vh, sl, snb, s, acc);
-      tile_hop<P, 2, true, S>(in, vh, sl, snb, s, acc);
-      tile_hop<P, 2, false, S>(in, vh, sl, snb, s, acc);
-      tile_hop<P, 3, true, S>(in, vh, sl, snb, s, acc);
-      tile_hop<P, 3, false, S>(in, vh, sl, snb, s, acc);
+      if constexpr (PF) {
+        const int t = threadIdx.x;
+        tile_fetch<0, S>(in, vh, snb, s, pf, t);
+        tile_pf_step<P, 0, S>(in, vh, sl, snb, s, pf, t, acc);
+        tile_pf_step<P, 1, S>(in, vh, sl, snb, s, pf, t, acc);
+        tile_pf_step<P, 2, S>(in, vh, sl, snb, s, pf, t, acc);
+        tile_pf_step<P, 3, S>(in, vh, sl, snb, s, pf, t, acc);
+        tile_pf_step<P, 4, S>(in, vh, sl, snb, s, pf, t, acc);
+        tile_pf_step<P, 5, S>(in, vh, sl, snb, s, pf, t, acc);
+        tile_pf_step<P, 6, S>(in, vh, sl, snb, s, pf, t, acc);
+        tile_pf_step<P, 7, S>(in, vh, sl, snb, s, pf, t, acc);
+      } else {
+        tile_hop<P, 0, true, S>(in, vh, sl, snb, s, acc);
+        tile_hop<P, 0, false, S>(in, vh, sl, snb, s, acc);
+        tile_hop<P, 1, true, S>(in, vh, sl, snb, s, acc);
+        tile_hop<P, 1, false, S>(in, vh, sl, snb, s, acc);
+        tile_hop<P, 2, true, S>(in, vh, sl, snb, s, acc);
+        tile_hop<P, 2, false, S>(in, vh, sl, snb, s, acc);
+        tile_hop<P, 3, true, S>(in, vh, sl, snb, s, acc);
+        tile_hop<P, 3, false, S>(in, vh, sl, snb, s, acc);
+      }
       cx<float> v[12];
       if constexpr ((FL & F_E_CLOV) != 0) {
 #pragma unroll

@@ -132,7 +132,8 @@ static std::vector<int> hop_variants(int prec, int flags, int red, int nrhs) {
     for (int k = 6; k < 9; ++k)
       if (hop_variant_rpt(k) <= nrhs) v.push_back(k);
     if (nrhs >= 2)
-      for (int k = 9; k < HOP_NVARIANT; ++k) v.push_back(k);
+      for (int k = 9; k < HOP_NVARIANT; ++k)
+        if (hop_variant_for_prec(k, prec)) v.push_back(k);
   }
   return v;
 }

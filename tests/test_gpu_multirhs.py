@@ -5,7 +5,10 @@ configuration, Sec. 3) go through the stencil kernels with a pinned launch
 shape: the per-thread kernel (variant 0), the shared-link tile kernel with
 and without a register cap (variants 9, 10: the eight links and T^-1 of a
 site staged once in shared memory for all right-hand sides of a 32-site
-tile), and the 2-4 right-hand-sides-per-thread kernels (6-8).  The lattice
+tile), the same with the neighbour spinors of the next hop copied into
+shared memory while the current hop computes (variants 11, 12; 16-bit
+storage, FP32 falls back to variant 0), and the 2-4
+right-hand-sides-per-thread kernels (6-8).  The lattice
 has a ragged last tile (720 sites per parity = 22.5 tiles) and several site
 blocks; 13 right-hand sides make two tile groups (7 + 6) with one idle warp.
 Each comparison bounds the relative L2 error over the whole output and the
@@ -80,7 +83,7 @@ def pin(api, L, prec, flags, red, nrhs, variant, nblk=3):
 
 
 @pytest.mark.parametrize("nrhs", [12, 13])
-@pytest.mark.parametrize("variant", [0, 9, 10, 8])
+@pytest.mark.parametrize("variant", [0, 9, 10, 11, 12, 8])
 @pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
 def test_deo_and_schur_multi_rhs(api, mr, prec, variant, nrhs):
     lat, L, op = mr["lat"], mr["L"], mr["op"]
@@ -92,16 +95,17 @@ def test_deo_and_schur_multi_rhs(api, mr, prec, variant, nrhs):
     check(L.Dhat(op, np.ascontiguousarray(psi[:, lat.even]), prec), mr["want"]["Dhat"][:nrhs], prec, "D^")
 
 
+@pytest.mark.parametrize("prec,variant", [("f32", 9), ("f16", 11), ("f16", 12)])
 @pytest.mark.parametrize("nblk", [1, 2, 7, 1000])
-def test_tile_kernel_grid_sizes(api, mr, nblk):
+def test_tile_kernel_grid_sizes(api, mr, nblk, prec, variant):
     """One block looping over every tile, a few, and more blocks than tiles."""
     lat, L, op = mr["lat"], mr["L"], mr["op"]
     psi = mr["psi"][:12]
-    pin(api, L, "f32", 0, 0, 12, 9, nblk=nblk)
-    check(L.Deo(op, np.ascontiguousarray(psi[:, lat.odd]), 0, "f32"), mr["want"]["Deo"][:12], "f32", "D_eo")
+    pin(api, L, prec, 0, 0, 12, variant, nblk=nblk)
+    check(L.Deo(op, np.ascontiguousarray(psi[:, lat.odd]), 0, prec), mr["want"]["Deo"][:12], prec, "D_eo")
 
 
-@pytest.mark.parametrize("variant", [0, 9, 10])
+@pytest.mark.parametrize("variant", [0, 9, 10, 11])
 @pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
 def test_twelve_rhs_solve_with_pinned_kernels(api, mr, prec, variant):
     """A 12-RHS mixed solve whose Schur passes (with their fused <rhat, v> and
@@ -123,12 +127,13 @@ def test_twelve_rhs_solve_with_pinned_kernels(api, mr, prec, variant):
         assert rel(X[k], mr["x"][k]) < 1e-10, (k, rel(X[k], mr["x"][k]))
 
 
-def test_tile_kernel_repeat_is_bit_identical(api, mr):
+@pytest.mark.parametrize("variant", [9, 11])
+def test_tile_kernel_repeat_is_bit_identical(api, mr, variant):
     """The tile kernel's fused reductions sum in a fixed order."""
     lat, L, op = mr["lat"], mr["L"], mr["op"]
     B = mr["psi"][:12]
     for flags, red in [(0, 0), (4, 0), (5, 2), (5, 3)]:
-        pin(api, L, "f16", flags, red, 12, 9)
+        pin(api, L, "f16", flags, red, 12, variant)
     s = api.make_solver(tol=1e-11, inner_prec="f16")
     a, _ = L.solve(op, B, s)
     b, _ = L.solve(op, B, s)

@@ -220,10 +220,11 @@ def test_autotuned_shapes_keep_parity(clover_odd, api):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
-@pytest.mark.parametrize("variant", [3, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("variant", [3, 5, 6, 7, 8, 9, 10, 11, 12])
 def test_forced_kernel_variants_keep_parity(api, prec, variant):
     """Every stencil variant (read-once loads, 2/3/4 right-hand sides per
-    thread, the shared-link tile kernel) inside a 5-RHS solve -- ragged
+    thread, the shared-link tile kernel with and without pipelined
+    neighbour loads) inside a 5-RHS solve -- ragged
     right-hand-side groups -- against
     the oracle, with the launch shape pinned by bridge_tune_set."""
     dims, kappa, csw, nrhs = (4, 6, 8, 10), 0.125, 1.0, 5
