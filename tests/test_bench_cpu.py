@@ -42,3 +42,18 @@ def test_oracle_sample_on_all_cores_matches_work():
     b = synth.gaussian_spinor(w.dims, 1)
     v, secs, procs = bench.oracle_sample_pool(w, U, b, 1024, seed=3, procs=2)
     assert procs == 2 and secs > 0 and v == pytest.approx(1024 * bench.FP64_D_BYTES_PER_SITE / secs / 1e9)
+
+
+def test_oracle_samples_never_exceed_the_lattice():
+    """A sample asked for more sites than the lattice has takes every site once."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+
+    w = synth.WORKLOADS["wilson_8x8x8x8"]
+    U = w.gauge()
+    b = synth.gaussian_spinor(w.dims, 1)
+    v, secs, _ = bench.oracle_sample(w, U, b, 10 * 4096, seed=0)
+    assert v == pytest.approx(4096 * bench.FP64_D_BYTES_PER_SITE / secs / 1e9)
+    v, secs, _ = bench.oracle_sample_pool(w, U, b, 10 * 4096, seed=0, procs=2)
+    assert v == pytest.approx(4096 * bench.FP64_D_BYTES_PER_SITE / secs / 1e9)
