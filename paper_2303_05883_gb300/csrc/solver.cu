@@ -254,6 +254,20 @@ void SolveState::launch_blas(int op, int cls, double bytes_per_site, double flop
   BR_CUDA(cudaGetLastError());
 }
 
+// Inner tolerance of the next pass of right-hand side r.  When the reduction
+// still needed, tol / (current true relative residual), lies within a factor
+// of ten below to four above the inner tolerance, this pass can be the last
+// one: aim at half the needed reduction (at most the inner tolerance, at
+// least a tenth of it), so that a small remainder does not cost one more
+// pass with its FP64 residual.  Otherwise the inner tolerance.
+double SolveState::pass_target(int r) const {
+  const double t = prm_.inner_tol;
+  if (outer_ == 0 || !(b2_[r] > 0.0) || !(r2_[r] > 0.0)) return t;
+  const double need = prm_.tol / std::sqrt(r2_[r] / b2_[r]);
+  if (need < 0.1 * t || need > 4.0 * t) return t;
+  return std::min(t, std::max(0.5 * need, 0.1 * t));
+}
+
 void SolveState::begin_inner() {
   nvtxRangePushA("bridge: even-odd prepare + inner start");
   // mask: right-hand sides still above tolerance
@@ -303,7 +317,8 @@ void SolveState::begin_inner() {
     left = std::min<long>(left, kAutoPassCap);
   for (int r = 0; r < nrhs_; ++r) {
     std::memset(&hi[r], 0, sizeof(BiCGScalars));
-    hi[r].tol2 = prm_.inner_tol * prm_.inner_tol;
+    const double t = pass_target(r);
+    hi[r].tol2 = t * t;
     hi[r].max_iter = (int)std::min<long>(left, 1L << 30);
   }
   BR_CUDA(cudaMemcpyAsync(scal_->ptr, hi, sizeof(BiCGScalars) * nrhs_, cudaMemcpyHostToDevice, st_));

@@ -114,6 +114,7 @@ class SolveState {
   int inflight_ = 2;  // batches kept queued ahead of the host check
   long inner_total_ = 0;
   std::vector<double> b2_, r2_;
+  double pass_target(int r) const;
   std::vector<int> active_, failed_, stall_;
   std::vector<bridge_info> info_;
   std::chrono::steady_clock::time_point t0_;
