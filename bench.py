@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg through host buffers")
     ap.add_argument("--inner", default=None, help="override the workload's inner storage precision (f32, f16, bf16)")
-    ap.add_argument("--rate-factors", type=float, nargs="+", default=[0.5, 0.9],
+    ap.add_argument("--rate-factors", type=float, nargs="+", default=[0.5, 0.7, 0.9],
                     help="serving workload: arrival rates as fractions of the saturated rate")
     ap.add_argument("--oracle-sites", type=int, default=16384, help="sites per oracle sample")
     ap.add_argument("--multi-rhs", default="clover_48x48x48x96_12rhs",
@@ -261,7 +261,7 @@ def oracle_sample_pool(w, U, b, nsites, seed, procs=None):
 # ------------------------------------------------------------------- serving
 
 
-def serving_sample(api, n_requests, main_lattice, main_U, seed=5, rate_factor=0.9):
+def serving_sample(api, n_requests, main_lattice, main_U, seed=5, rate_factor=0.7):
     """Poisson stream through the request engine; returns latency stats."""
     import synth
 
