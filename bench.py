@@ -639,6 +639,8 @@ def multi_rhs_leg(args, api, local, peak, alu):
            "mixed_ms": ms, "mixed_steps": K, "gbs": gbs, "inner_iters": max(i.inner_iters for i in infos),
            "outer_iters": max(i.outer_iters for i in infos), "true_rel_residual": res,
            "status": sorted({i.status for i in infos}), "kernels": kernels, "kernel_shares": shares,
+           "launch_shapes": {k: {"block": v[0], "site_blocks": v[1], "variant": v[2]}
+                             for k, v in api.bridge_tune_table(h).items() if k.startswith("hop/")},
            "clocks": clk.summary(), "setup_s": setup_s}
     if not args.no_fp64:
         api.bridge_tune(h, op, "f64", 1)
