@@ -123,6 +123,98 @@ BR_D void prog_columns(const SProg& pg, cx<R>* sh, int Ls, int ns, R mf) {
   __syncthreads();
 }
 
+// The same programs with a whole column in registers (FP32, compile-time
+// Ls): one shared-memory load and one store per element instead of a load,
+// a dependent FMA and a store per step of each factor, so the sweep is no
+// longer a chain of shared-memory round trips.  Same operations in the same
+// order as col_mul / col_solve.
+template <class R, int LS>
+BR_D void col_mul_reg(cx<R> v[LS], R d, R e, int dir, R mf) {
+  if (dir < 0) {
+    const cx<R> last = v[LS - 1];
+#pragma unroll
+    for (int s = LS - 1; s >= 1; --s) v[s] = d * v[s] + e * v[s - 1];
+    v[0] = d * v[0] + (-mf * e) * last;
+  } else {
+    const cx<R> first = v[0];
+#pragma unroll
+    for (int s = 0; s < LS - 1; ++s) v[s] = d * v[s] + e * v[s + 1];
+    v[LS - 1] = d * v[LS - 1] + (-mf * e) * first;
+  }
+}
+
+template <class R, int LS>
+BR_D void col_solve_reg(cx<R> v[LS], R d, R e, int dir, R mf) {
+  const R r = -e / d, inv_d = R(1) / d;
+  cx<R> acc = czero<R>();
+  R w = R(1);
+  if (dir < 0) {
+#pragma unroll
+    for (int t = LS - 1; t >= 1; --t) {
+      acc = acc + w * v[t];
+      w *= r;
+    }
+    cx<R> y = (R(1) / (d - e * mf * w)) * (v[0] + (e * mf * inv_d) * acc);
+    v[0] = y;
+#pragma unroll
+    for (int s = 1; s < LS; ++s) {
+      y = inv_d * v[s] + r * y;
+      v[s] = y;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t <= LS - 2; ++t) {
+      acc = acc + w * v[t];
+      w *= r;
+    }
+    cx<R> y = (R(1) / (d - e * mf * w)) * (v[LS - 1] + (e * mf * inv_d) * acc);
+    v[LS - 1] = y;
+#pragma unroll
+    for (int s = LS - 2; s >= 0; --s) {
+      y = inv_d * v[s] + r * y;
+      v[s] = y;
+    }
+  }
+}
+
+template <class R, int LS>
+BR_D void prog_columns_reg(const SProg& pg, cx<R>* sh, int ns, R mf) {
+  for (int cidx = threadIdx.x; cidx < 12 * ns; cidx += blockDim.x) {
+    const int sl = cidx % ns, k = cidx / ns, chi = k < 6 ? 0 : 1;
+    cx<R>* col = sh + (long)k * ns + sl;
+    const long stride = 12L * ns;
+    cx<R> v[LS];
+#pragma unroll
+    for (int s = 0; s < LS; ++s) v[s] = col[s * stride];
+    for (int f = 0; f < pg.nf[chi]; ++f) {
+      if (pg.kind[chi][f] == SF_MUL)
+        col_mul_reg<R, LS>(v, (R)pg.d[chi][f], (R)pg.e[chi][f], pg.dir[chi][f], mf);
+      else
+        col_solve_reg<R, LS>(v, (R)pg.d[chi][f], (R)pg.e[chi][f], pg.dir[chi][f], mf);
+    }
+    const R sg = (R)pg.sign[chi];
+#pragma unroll
+    for (int s = 0; s < LS; ++s) col[s * stride] = sg != R(1) ? sg * v[s] : v[s];
+  }
+  __syncthreads();
+}
+
+// The register form for FP32 and the usual Ls, else the shared-memory one.
+template <class R>
+BR_D void prog_columns_any(const SProg& pg, cx<R>* sh, int Ls, int ns, R mf) {
+  if constexpr (sizeof(R) == 4) {
+    if (Ls == 16) {
+      prog_columns_reg<R, 16>(pg, sh, ns, mf);
+      return;
+    }
+    if (Ls == 8) {
+      prog_columns_reg<R, 8>(pg, sh, ns, mf);
+      return;
+    }
+  }
+  prog_columns<R>(pg, sh, Ls, ns, mf);
+}
+
 struct DwfArgs {
   Geom g;
   int out_parity;
@@ -340,7 +432,17 @@ __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
 
   const int rhs = blockIdx.x % a.nrhs;
   const int sb = blockIdx.x / a.nrhs;
-  const int sl = threadIdx.x % ns, s0 = threadIdx.x / ns;
+  // site and slice group of this thread: with two slices per thread a warp
+  // takes 16 sites x 2 slice groups (when the block's shape allows), so that
+  // each 8-byte link read from shared memory touches 16 sites -- one
+  // 128-byte wavefront -- while serving four slices of each; otherwise
+  // consecutive threads take consecutive sites
+  int sl = threadIdx.x % ns, s0 = threadIdx.x / ns;
+  if (SPT == 2 && ns % 16 == 0 && lss % 2 == 0 && ns * lss == (int)blockDim.x) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nst = ns / 16;
+    sl = 16 * (w % nst) + (lane & 15);
+    s0 = 2 * (w / nst) + (lane >> 4);
+  }
   const uint32_t ih = (uint32_t)sb * ns + sl;
   const long vh = a.g.vh;
   const bool live = s0 < lss;
@@ -396,8 +498,8 @@ __global__ void __launch_bounds__(256, MINB) dwf_hop_kernel(const DwfArgs a) {
   }
   if (M1 || M2 == DM2_DENSE) __syncthreads();
   if (fact) {
-    if (M1) prog_columns<R>(a.p1, shh, Ls, ns, (R)a.mf);
-    if (M2 == DM2_DENSE) prog_columns<R>(a.p2, shs, Ls, ns, (R)a.mf);
+    if (M1) prog_columns_any<R>(a.p1, shh, Ls, ns, (R)a.mf);
+    if (M2 == DM2_DENSE) prog_columns_any<R>(a.p2, shs, Ls, ns, (R)a.mf);
   }
 
   R nrm = R(0);
@@ -508,7 +610,7 @@ __global__ void __launch_bounds__(256, MINB) dwf_mix_kernel(const DwfMixArgs a) 
   }
   if (live) stage_row(sh, ns, s, sl, v);
   __syncthreads();
-  if (fact) prog_columns<R>(a.pm, sh, Ls, ns, (R)a.mf);
+  if (fact) prog_columns_any<R>(a.pm, sh, Ls, ns, (R)a.mf);
   if (valid) {
     cx<R> w[12];
     if (fact) {

@@ -29,14 +29,18 @@ static bool go_hop1(const DwfArgs& a, cudaStream_t st) {
 }
 
 // Variant v -> (register budget MINB, slices per thread): 0 (2, 1), 1 (3, 1),
-// 2 (4, 1), 3 (1, 2), 4 (2, 2) for FP32 (two slices per thread need an even
-// Ls); FP64 has only v = 0.
+// 2 (4, 1), 3 (1, 2), 4 (2, 2), 5 (3, 2) for FP32 (two slices per thread need
+// an even Ls); FP64 has only v = 0.
 template <int P, bool M1, int M2, int EPI>
 static bool go_hop(const DwfArgs& a, cudaStream_t st, int v) {
   if constexpr (P == P_F64) {
     return go_hop1<P, M1, M2, EPI, 1, 1>(a, st);
   } else {
-    if (dwf_variant_spt(v, a.Ls) == 2) return v == 3 ? go_hop1<P, M1, M2, EPI, 1, 2>(a, st) : go_hop1<P, M1, M2, EPI, 2, 2>(a, st);
+    if (dwf_variant_spt(v, a.Ls) == 2) {
+      if (v == 3) return go_hop1<P, M1, M2, EPI, 1, 2>(a, st);
+      if (v == 5) return go_hop1<P, M1, M2, EPI, 3, 2>(a, st);
+      return go_hop1<P, M1, M2, EPI, 2, 2>(a, st);
+    }
     if (v == 1) return go_hop1<P, M1, M2, EPI, 3, 1>(a, st);
     if (v == 2) return go_hop1<P, M1, M2, EPI, 4, 1>(a, st);
     return go_hop1<P, M1, M2, EPI, 2, 1>(a, st);

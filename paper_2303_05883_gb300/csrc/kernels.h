@@ -16,11 +16,11 @@ bool launch_hop_any(int prec, int flags, int red, const HopArgs& a, int block, c
 // (1, PLAIN, NORM), (1, PLAIN, CGUPD), (1, DENSE, NONE), (0, NONE, NONE),
 // (0, DENSE, NONE), (0, DENSE, NORM); F64 and F32.  false for any other.
 // variant: register budget of the FP32 kernels, 0/1/2 = at most 128/85/64
-// registers per thread, 3/4 = two slices per thread with no cap / <= 128
-// registers (FP64: one variant).
-// Variants 3 and 4: two fifth-dimension slices per thread (even Ls; an odd
-// Ls runs them as one slice per thread).
-constexpr int DWF_NVARIANT = 5;
+// registers per thread, 3/4/5 = two slices per thread with no cap / <= 128 /
+// <= 85 registers (FP64: one variant).
+// Variants 3-5: two fifth-dimension slices per thread (even Ls; an odd Ls
+// runs them as one slice per thread).
+constexpr int DWF_NVARIANT = 6;
 inline int dwf_variant_spt(int variant, int Ls) { return (variant >= 3 && Ls % 2 == 0) ? 2 : 1; }
 bool launch_dwf_hop(int prec, bool m1, int m2, int epi, const DwfArgs& a, cudaStream_t st, int variant = 0);
 bool launch_dwf_mix(int prec, int mode, const DwfMixArgs& a, cudaStream_t st, int variant = 0);

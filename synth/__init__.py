@@ -282,6 +282,11 @@ class MobiusWorkload:
 WORKLOADS["mobius_24x24x24x48x16"] = MobiusWorkload(
     "mobius_24x24x24x48x16", (24, 24, 24, 48), 16, 1.8, 1.5, 0.5, 0.01, 0.2, 5, 1, 1e-10
 )
+# The same on 16^3x32 (each five-dimensional FP32 field 201 MB, above L2; a
+# few GB in all) for profiler captures.
+WORKLOADS["mobius_16x16x16x32x16"] = MobiusWorkload(
+    "mobius_16x16x16x32x16", (16, 16, 16, 32), 16, 1.8, 1.5, 0.5, 0.01, 0.2, 5, 1, 1e-10
+)
 
 
 @dataclass(frozen=True)

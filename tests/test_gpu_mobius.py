@@ -219,19 +219,22 @@ def test_dense_fifth_dimension_path(api, monkeypatch, how):
 _DWF_COMBOS = [(1, 0, 0), (1, 1, 0), (1, 1, 1), (1, 1, 2), (1, 2, 0), (0, 0, 0), (0, 2, 0), (0, 2, 1)]
 
 
-@pytest.mark.parametrize("variant", [3, 4])
+@pytest.mark.parametrize("block", [128, 256])
+@pytest.mark.parametrize("variant", [3, 4, 5])
 @pytest.mark.parametrize("dims,Ls", [((4, 2, 4, 6), 16), ((6, 6, 2, 4), 7), ((4, 4, 4, 8), 8)],
                          ids=["4x2x4x6_Ls16", "6x6x2x4_Ls7", "4x4x4x8_Ls8"])
-def test_two_slices_per_thread_variants(api, dims, Ls, variant):
+def test_two_slices_per_thread_variants(api, dims, Ls, variant, block):
     """The hop kernels with two fifth-dimension slices per thread (links,
-    neighbour indices and addresses shared by the slices s and s + Ls/2),
-    pinned for every kernel of the operators and of the CG solve, against the
-    oracle; an odd Ls runs the same variant with one slice per thread."""
+    neighbour indices and addresses shared by the slices s and s + Ls/2; a
+    warp takes 16 sites x 2 slice groups, one or two such site tiles per
+    block), pinned for every kernel of the operators and of the CG solve,
+    against the oracle; an odd Ls runs the same variant with one slice per
+    thread."""
     lat, U, orc, op, L = _setup(api, dims, Ls, 0.4, 40 + Ls)
     key = "x".join(map(str, dims))
     for nrhs in (1, 2):
         for m1, m2, epi in _DWF_COMBOS:
-            api.bridge_tune_set(L.handle, f"dwf/1/{m1}/{m2}/{epi}/Ls{Ls}/{key}/{nrhs}", 128, 1, variant)
+            api.bridge_tune_set(L.handle, f"dwf/1/{m1}/{m2}/{epi}/Ls{Ls}/{key}/{nrhs}", block, 1, variant)
     nrhs = 2
     psi = synth.gaussian_spinor(dims, 9, nrhs=nrhs * Ls).reshape(nrhs, Ls, lat.V, 4, 3)
     got = L.D(op, psi, "f32")
